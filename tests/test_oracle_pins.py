@@ -1,0 +1,448 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage it checks. None of them compares the oracle with itself: the
+expected values come from hand-derived worked examples (tests/golden), closed forms, library
+routines on dense matrices, or invariants the paper states.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle.kernels as K
+from oracle.gmres import gmres_mgs, gmres_onereduce
+from oracle.vcycle import vcycle
+from workloads import build_hierarchy, poisson2d_5pt, pressure3d_7pt, rhs_uniform
+from workloads.hierarchy import ilu0
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def tridiag(n):
+    return sp.csr_matrix(sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]))
+
+
+def random_spd(n, seed, density=0.3):
+    rng = np.random.default_rng(seed)
+    B = sp.random(n, n, density=density, random_state=rng, data_rvs=lambda k: -rng.uniform(0.1, 1.0, k))
+    B = sp.triu(B, 1)
+    A = B + B.T
+    d = np.asarray(abs(A).sum(axis=1)).ravel() + rng.uniform(0.5, 1.5, n)
+    return sp.csr_matrix(A + sp.diags(d))
+
+
+# ----------------------------------------------------------------------------------------------
+# Polynomial Gauss-Seidel (Sec. 5.2)
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", _read_golden("poly_gs_tridiag4.txt"), ids=lambda r: r[0])
+def test_poly_gs_golden(row):
+    _, terms, direction, *vals = row
+    A = tridiag(4)
+    x = K.poly_gs_sweep(A, np.ones(4), np.zeros(4), int(terms), backward=(direction == "bwd"))
+    np.testing.assert_allclose(x, np.array(vals, float), rtol=0, atol=1e-15)
+
+
+def test_poly_gs_direct_golden():
+    A = tridiag(4)
+    x = K.poly_gs_sweep(A, np.ones(4), np.zeros(4), 2, backward=False, mode="direct")
+    np.testing.assert_allclose(x, [0.5, 0.75, 0.875, 0.9375], atol=1e-15)
+
+
+@pytest.mark.parametrize("backward", [False, True])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_poly_gs_full_series_is_gauss_seidel(seed, backward):
+    """A strictly triangular D^-1 L is nilpotent, so n terms of the series are exact (Sec. 5.2,
+    last paragraph): the sweep equals x + (D+L)^-1 r from a dense library solve."""
+    n = 24
+    A = random_spd(n, seed)
+    rng = np.random.default_rng(seed + 10)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    got = K.poly_gs_sweep(A, b, x0, n, backward=backward)
+    Ad = A.toarray()
+    M = np.triu(Ad) if backward else np.tril(Ad)
+    want = x0 + np.linalg.solve(M, b - Ad @ x0)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    direct = K.poly_gs_sweep(A, b, x0, 2, backward=backward, mode="direct")
+    np.testing.assert_allclose(direct, want, rtol=1e-12, atol=1e-12)
+
+
+def test_poly_gs_one_term_is_jacobi():
+    """Zero inner sweeps reduce polynomial GS to Jacobi (Sec. 5.2)."""
+    A = random_spd(30, 5)
+    rng = np.random.default_rng(3)
+    b, x0 = rng.uniform(-1, 1, 30), rng.uniform(-1, 1, 30)
+    Ad = A.toarray()
+    want = x0 + (b - Ad @ x0) / np.diag(Ad)
+    np.testing.assert_allclose(K.poly_gs_sweep(A, b, x0, 1), want, rtol=1e-14, atol=1e-14)
+
+
+def test_poly_gs_partial_series_matches_dense_powers():
+    """k terms equal sum_{j<k} (-D^-1 L)^j D^-1 r formed with dense matrix powers."""
+    A = random_spd(20, 7)
+    Ad = A.toarray()
+    D = np.diag(np.diag(Ad))
+    G = -np.linalg.solve(D, np.tril(Ad, -1))
+    rng = np.random.default_rng(8)
+    b = rng.uniform(-1, 1, 20)
+    for k in (2, 3, 5):
+        S = sum(np.linalg.matrix_power(G, j) for j in range(k)) @ np.linalg.inv(D)
+        np.testing.assert_allclose(K.poly_gs_sweep(A, b, np.zeros(20), k), S @ b, rtol=1e-13, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------------------------
+# ILU(0) with Neumann triangular solves (Sec. 5.3.2) and the factorisation input
+# ----------------------------------------------------------------------------------------------
+
+def _tridiag3_factors():
+    Ls = sp.csr_matrix(np.array([[0, 0, 0], [-0.5, 0, 0], [0, -2 / 3, 0]]))
+    Us = sp.csr_matrix(np.array([[0, -0.5, 0], [0, 0, -2 / 3], [0, 0, 0]]))
+    return Ls, Us, np.array([0.5, 2 / 3, 0.75])
+
+
+@pytest.mark.parametrize("row", _read_golden("ilu_tridiag3.txt"), ids=lambda r: r[0])
+def test_ilu_golden(row):
+    _, tl, tu, *vals = row
+    Ls, Us, dinv = _tridiag3_factors()
+    x = K.ilu0_sweep(Ls, Us, dinv, tridiag(3), np.ones(3), np.zeros(3), int(tl), int(tu))
+    np.testing.assert_allclose(x, np.array(vals, float), atol=1e-15)
+
+
+def test_ilu0_generator_matches_hand_factors():
+    Ls, Us, dinv = ilu0(tridiag(3))
+    L0, U0, d0 = _tridiag3_factors()
+    np.testing.assert_allclose(Ls.toarray(), L0.toarray(), atol=1e-15)
+    np.testing.assert_allclose(Us.toarray(), U0.toarray(), atol=1e-15)
+    np.testing.assert_allclose(dinv, d0, atol=1e-15)
+
+
+def test_ilu0_reproduces_A_on_its_pattern():
+    """ILU(0): (L U)_ij = a_ij for (i, j) in pattern(A)."""
+    A = pressure3d_7pt(6, seed=3)
+    Ls, Us, dinv = ilu0(A)
+    n = A.shape[0]
+    I = sp.identity(n)
+    LU = ((I + Ls) @ sp.diags(1.0 / dinv) @ (I + Us)).toarray()
+    Ad = A.toarray()
+    mask = Ad != 0
+    np.testing.assert_allclose(LU[mask], Ad[mask], rtol=1e-13, atol=1e-13)
+
+
+def test_ilu_full_series_is_exact_substitution():
+    """With n terms both Neumann series are exact (L_s, U_s nilpotent; Sec. 1 and eq. Neumann)."""
+    A = pressure3d_7pt(4, seed=1)
+    n = A.shape[0]
+    Ls, Us, dinv = ilu0(A)
+    rng = np.random.default_rng(0)
+    b = rng.uniform(-1, 1, n)
+    I = np.eye(n)
+    LU = (I + Ls.toarray()) @ np.diag(1.0 / dinv) @ (I + Us.toarray())
+    want = np.linalg.solve(LU, b)
+    got = K.ilu0_sweep(Ls, Us, dinv, A, b, np.zeros(n), n, n)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
+    got_d = K.ilu0_sweep(Ls, Us, dinv, A, b, np.zeros(n), 1, 1, mode="direct")
+    np.testing.assert_allclose(got_d, want, rtol=1e-11, atol=1e-12)
+
+
+def test_l1_jacobi_dense():
+    A = random_spd(16, 4)
+    Ad = A.toarray()
+    rng = np.random.default_rng(1)
+    b, x0 = rng.uniform(-1, 1, 16), rng.uniform(-1, 1, 16)
+    want = x0 + (b - Ad @ x0) / np.abs(Ad).sum(axis=1)
+    np.testing.assert_allclose(K.l1_jacobi_sweep(A, b, x0), want, rtol=1e-14, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------------------------
+# V-cycle (Sec. 5): brute force against the closed-form error propagation operator
+# ----------------------------------------------------------------------------------------------
+
+def _dense_smoother(A, kind, p, backward, lev):
+    """Dense approximate inverse B of one sweep x <- x + B (b - A x)."""
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    if kind == "jacobi":
+        return np.diag(1.0 / np.abs(Ad).sum(axis=1))
+    if kind == "ilu":
+        Ls, Us = lev.ilu_L.toarray(), lev.ilu_U.toarray()
+        SL = sum(np.linalg.matrix_power(-Ls, j) for j in range(p.ilu_terms_L))
+        SU = sum(np.linalg.matrix_power(-Us, j) for j in range(p.ilu_terms_U))
+        return SU @ np.diag(lev.ilu_dinv) @ SL
+    Dinv = np.diag(1.0 / np.diag(Ad))
+    T = np.triu(Ad, 1) if backward else np.tril(Ad, -1)
+    G = -Dinv @ T
+    return sum(np.linalg.matrix_power(G, j) for j in range(p.neumann_terms)) @ Dinv
+
+
+def _dense_vcycle_operator(H, p, l=0):
+    """M_l^-1 = (I - E_l) A_l^-1 with E_l = S_post^nu2 (I - P M_{l+1}^-1 R A) S_pre^nu1 and
+    S = I - B A; the coarsest level uses A_L^-1."""
+    from oracle.vcycle import level_smoother
+    lev = H.levels[l]
+    Ad = lev.A.toarray()
+    n = Ad.shape[0]
+    I = np.eye(n)
+    if l == H.nlevels - 1:
+        return np.linalg.inv(Ad)
+    kind = level_smoother(H, l, p)
+    Bpre = _dense_smoother(lev.A, kind, p, False, lev)
+    Bpost = _dense_smoother(lev.A, kind, p, True, lev)
+    Mc = _dense_vcycle_operator(H, p, l + 1)
+    E = np.linalg.matrix_power(I - Bpost @ Ad, p.post_sweeps) @ (I - lev.P.toarray() @ Mc @ lev.R.toarray() @ Ad) \
+        @ np.linalg.matrix_power(I - Bpre @ Ad, p.pre_sweeps)
+    return (I - E) @ np.linalg.inv(Ad)
+
+
+@pytest.mark.parametrize("smoother,terms,sweeps", [(K.POLY_GS, 2, 1), (K.POLY_GS, 3, 2), (K.JACOBI_L1, 1, 2),
+                                                   (K.HYBRID_ILU0, 2, 1), (K.ILU0, 2, 1)])
+def test_vcycle_matches_closed_form_operator(smoother, terms, sweeps):
+    A = pressure3d_7pt(4, seed=2)  # n = 64
+    H = build_hierarchy(A, max_levels=3, coarse_max=8, ilu_levels=None)
+    assert H.nlevels == 3 and H.coarse_inv is not None
+    p = K.SmootherParams(smoother=smoother, neumann_terms=terms, pre_sweeps=sweeps, post_sweeps=sweeps)
+    n = A.shape[0]
+    Mv = np.column_stack([vcycle(H, e, p) for e in np.eye(n)])
+    Md = _dense_vcycle_operator(H, p)
+    np.testing.assert_allclose(Mv, Md, rtol=1e-10, atol=1e-11 * np.abs(Md).max())
+
+
+def test_coarse_direct_solves():
+    A = random_spd(40, 9)
+    b = np.random.default_rng(2).uniform(-1, 1, 40)
+    x = K.coarse_direct(A, b)
+    assert np.linalg.norm(A @ x - b) <= 1e-13 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------------------------------------------------
+# Setup invariants of the shared input (Sec. 5.1)
+# ----------------------------------------------------------------------------------------------
+
+def test_hierarchy_invariants():
+    A = poisson2d_5pt(20)
+    H = build_hierarchy(A, max_levels=4, coarse_max=16)
+    for l, lev in enumerate(H.levels[:-1]):
+        Ac = H.levels[l + 1].A
+        # Galerkin: A_c = R A P and symmetric when A is
+        np.testing.assert_allclose((lev.R @ lev.A @ lev.P - Ac).toarray(), 0, atol=1e-13)
+        assert abs(Ac - Ac.T).max() <= 1e-13 * abs(Ac).max()
+        np.testing.assert_allclose((lev.R - lev.P.T).toarray(), 0, atol=0)
+        # P 1 = 1 on rows whose row sum is zero (interpolation of constants, f = 1)
+        rs = np.asarray(lev.A.sum(axis=1)).ravel()
+        zero_rows = np.abs(rs) <= 1e-12 * abs(lev.A).max()
+        p1 = lev.P @ np.ones(lev.P.shape[1])
+        np.testing.assert_allclose(p1[zero_rows], 1.0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------------
+# GMRES (Sec. 2-4)
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver", ["mgs", "trunc", "exact"])
+def test_gmres_finite_termination_distinct_eigenvalues(solver):
+    """A diagonal matrix with 5 distinct eigenvalues: the Krylov space of any b has dimension
+    at most 5, so GMRES terminates in exactly 5 steps (b has components on all eigenvalues)."""
+    lam = np.repeat([1.0, 2.0, 3.5, 5.0, 9.0], 8)
+    A = sp.csr_matrix(sp.diags(lam))
+    b = np.random.default_rng(0).uniform(0.5, 1.0, lam.size)
+    f = gmres_mgs if solver == "mgs" else (lambda *a, **k: gmres_onereduce(*a, T_mode=solver, **k))
+    r = f(A, b, None, m=20, rtol=1e-12)
+    assert r.iters == 5 and r.converged
+    np.testing.assert_allclose(r.x, b / lam, rtol=1e-11)
+
+
+def _c1():
+    A = poisson2d_5pt(32)
+    H = build_hierarchy(A, max_levels=3, coarse_max=64)
+    b = rhs_uniform(A.shape[0], 0)
+    return A, H, b
+
+
+@pytest.mark.parametrize("solver", ["mgs", "trunc", "exact"])
+def test_gmres_arnoldi_relation_and_orthogonality(solver):
+    """A Z_k = V_{k+1} H_{k+1,k} (Sec. 1) and near-orthonormal V (Sec. 3) on a well-conditioned cycle."""
+    A, H, b = _c1()
+    p = K.SmootherParams(neumann_terms=2)
+    M = lambda v: vcycle(H, v, p)
+    f = gmres_mgs if solver == "mgs" else (lambda *a, **k: gmres_onereduce(*a, T_mode=solver, **k))
+    r = f(A, b, M, m=30, rtol=1e-6)
+    rel = np.linalg.norm(A @ r.Z - r.V @ r.H) / (np.linalg.norm(A.toarray(), 2) * np.linalg.norm(r.Z))
+    assert rel <= 1e-14
+    k = r.V.shape[1] - 1
+    eps = np.finfo(float).eps
+    # Loss of orthogonality grows like eps * kappa(B) and beta(x) kappa(B) = O(1) (Sec. 3), so
+    # after j columns it is bounded by a modest multiple of eps / relres_j.
+    for j in range(1, k + 1):
+        Vj = r.V[:, : j + 1]
+        loss = np.linalg.norm(np.eye(j + 1) - Vj.T @ Vj)
+        assert loss <= 1e2 * eps / r.history[j - 1]
+    assert np.linalg.norm(np.eye(2) - r.V[:, :2].T @ r.V[:, :2]) <= 1e-14
+
+
+@pytest.mark.parametrize("solver", ["mgs", "trunc"])
+def test_gmres_residual_monotone_and_true(solver):
+    A, H, b = _c1()
+    p = K.SmootherParams(neumann_terms=2)
+    f = gmres_mgs if solver == "mgs" else gmres_onereduce
+    r = f(A, b, lambda v: vcycle(H, v, p), m=30, rtol=1e-8)
+    h = np.array(r.history)
+    assert np.all(np.diff(h) <= 1e-15)
+    assert r.converged and r.relres_true <= 1e-8
+    true = np.linalg.norm(b - A @ r.x) / np.linalg.norm(b)
+    assert abs(true - r.relres_implicit) <= 1e-11 + 1e-3 * true
+
+
+def test_gmres_manufactured_solution():
+    A = pressure3d_7pt(12, seed=4)
+    n = A.shape[0]
+    xs = np.random.default_rng(5).uniform(-1, 1, n)
+    b = A @ xs
+    H = build_hierarchy(A, coarse_max=32)
+    p = K.SmootherParams(smoother=K.HYBRID_ILU0)
+    r = gmres_onereduce(A, b, lambda v: vcycle(H, v, p), m=30, rtol=1e-10)
+    kappa = np.linalg.cond(A.toarray())
+    assert np.linalg.norm(r.x - xs) / np.linalg.norm(xs) <= 10 * kappa * 1e-10
+
+
+def test_gmres_unpreconditioned_full_space_terminates():
+    A = random_spd(30, 11)
+    b = np.random.default_rng(6).uniform(-1, 1, 30)
+    for f in (gmres_mgs, gmres_onereduce):
+        r = f(A, b, None, m=30, rtol=1e-11)
+        assert r.converged and r.iters <= 30 and r.restarts == 0
+
+
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.JACOBI_L1])
+def test_truncation_does_not_change_convergence(smoother):
+    """Corollary of Sec. 3: T = I - L gives the same iteration count as T = (I + L)^-1 and as
+    classical MGS-GMRES, and the same solution to within the tolerance."""
+    A = pressure3d_7pt(16, seed=0)
+    b = rhs_uniform(A.shape[0], 0)
+    H = build_hierarchy(A, coarse_max=64)
+    sw = 2 if smoother == K.JACOBI_L1 else 1
+    p = K.SmootherParams(smoother=smoother, pre_sweeps=sw, post_sweeps=sw)
+    M = lambda v: vcycle(H, v, p)
+    r0 = gmres_mgs(A, b, M, m=50, rtol=1e-8)
+    r1 = gmres_onereduce(A, b, M, m=50, rtol=1e-8, T_mode="trunc")
+    r2 = gmres_onereduce(A, b, M, m=50, rtol=1e-8, T_mode="exact")
+    assert abs(r0.iters - r1.iters) <= 1 and abs(r1.iters - r2.iters) <= 1
+    for r in (r0, r1, r2):
+        assert r.converged
+    nx = np.linalg.norm(r0.x)
+    assert np.linalg.norm(r1.x - r0.x) / nx <= 1e-6
+    assert np.linalg.norm(r2.x - r1.x) / nx <= 1e-10
+
+
+def test_gmres_restart_path():
+    """GMRES(m) with m smaller than the iteration count restarts from the true residual."""
+    A, H, b = _c1()
+    for f in (gmres_mgs, gmres_onereduce):
+        r = f(A, b, None, m=10, rtol=1e-6, maxit=2000)
+        assert r.converged and r.restarts >= 1 and r.relres_true <= 1e-6
+
+
+def _check_projection(project):
+    """Sec. 3 corollary: T = I - L equals (I + L)^-1 up to O(||L||^2); (I + L) h_exact = r."""
+    rng = np.random.default_rng(12)
+    for k in (3, 8, 15):
+        Lm = np.tril(rng.standard_normal((k, k)), -1) * 1e-4
+        r = rng.standard_normal(k)
+        he = project(Lm, r, "exact")
+        np.testing.assert_allclose((np.eye(k) + Lm) @ he, r, rtol=0, atol=1e-14)
+        ht = project(Lm, r, "trunc")
+        nl = np.linalg.norm(Lm, 2)
+        assert np.linalg.norm(ht - he) <= 4 * nl ** 2 * np.linalg.norm(r)
+        assert np.linalg.norm(ht - he) >= 1e-3 * nl ** 2 * np.linalg.norm(r) or nl == 0
+        np.testing.assert_allclose(ht, np.linalg.solve(np.eye(k) + Lm, r), atol=4 * nl ** 2 * np.linalg.norm(r))
+
+
+def test_truncated_projection_is_neumann_first_order():
+    import oracle.kernels as KK
+    _check_projection(KK.project)
+
+
+def _check_lrows(solver):
+    """The accumulated L is the strictly lower part of V^T V (Sec. 3: V^T V = I + L + L^T).
+    Unpreconditioned GMRES on the 2D Poisson matrix loses enough orthogonality (kappa(B) grows
+    as the residual falls) for L to sit well above rounding level."""
+    A = poisson2d_5pt(32)
+    b = rhs_uniform(A.shape[0], 0)
+    r = solver(A, b, None, m=60, rtol=1e-9, maxit=60, T_mode="exact")
+    k = r.L.shape[0]
+    Lt = np.tril(r.V[:, :k].T @ r.V[:, :k], -1)
+    assert np.linalg.norm(Lt) >= 1e-12
+    assert np.linalg.norm(r.L - Lt) <= 1e-2 * np.linalg.norm(Lt)
+
+
+def test_onereduce_L_is_lower_gram():
+    _check_lrows(gmres_onereduce)
+
+
+MUTANTS = [
+    # (module, original source fragment, planted mistake, which pin must fail)
+    ("oracle.gmres", "r = np.concatenate([s[:i] / beta, [s[i] / beta ** 2]])",
+     "r = np.concatenate([s[:i] / beta, [s[i] / beta]])", "arnoldi"),          # step 9 scaling dropped
+    ("oracle.kernels", "return r - Lrows[:k, :k] @ r", "return r + Lrows[:k, :k] @ r", "project"),  # sign of L
+    ("oracle.kernels", "h[q] = r[q] - np.dot(Lrows[q, :q], h[:q])", "h[q] = r[q] - np.dot(Lrows[:q, q], h[:q])", "project"),
+    ("oracle.gmres", "Lm[i, :i] = a[:i] / beta", "Lm[i, :i] = a[:i]", "lrows"),  # step 10 scaling dropped
+    ("oracle.kernels", "t = -(T @ t) / d", "t = (T @ t) / d", "polygs"),        # sign of the Neumann term
+    ("oracle.kernels", "T = U if backward else L", "T = L if backward else U", "polygs"),  # transposed operand
+    ("oracle.kernels", "f = dinv * y\n        t = f.copy()", "f = y\n        t = f.copy()", "ilu"),  # D_U^-1 dropped
+]
+
+
+def _mutated(modname, old, new):
+    import importlib
+    import inspect
+    mod = importlib.import_module(modname)
+    src = inspect.getsource(mod)
+    assert src.count(old) == 1, old
+    ns = dict(mod.__dict__)
+    exec(compile(src.replace(old, new), mod.__file__, "exec"), ns)
+    return ns
+
+
+@pytest.mark.parametrize("modname,old,new,pin", MUTANTS, ids=[m[2].split("\n")[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(modname, old, new, pin):
+    """Each planted mistake in the oracle (on the CPU) makes one of the pins above fail."""
+    ns = _mutated(modname, old, new)
+    if pin == "project":
+        with pytest.raises(AssertionError):
+            _check_projection(ns["project"])
+        return
+    if pin == "lrows":
+        with pytest.raises(AssertionError):
+            _check_lrows(ns["gmres_onereduce"])
+        return
+    if pin == "arnoldi":
+        A, H, b = _c1()
+        r = ns["gmres_onereduce"](A, b, None, m=20, rtol=1e-6, T_mode="trunc")
+        rel = np.linalg.norm(A @ r.Z - r.V @ r.H) / (np.linalg.norm(A.toarray(), 2) * np.linalg.norm(r.Z))
+        k = r.V.shape[1]
+        loss = np.linalg.norm(np.eye(k) - r.V.T @ r.V)
+        assert rel > 1e-12 or loss > 1e-6 or not r.converged
+    elif pin == "polygs":
+        bad = 0
+        for row in _read_golden("poly_gs_tridiag4.txt"):
+            _, terms, direction, *vals = row
+            x = ns["poly_gs_sweep"](tridiag(4), np.ones(4), np.zeros(4), int(terms), backward=(direction == "bwd"))
+            bad += not np.allclose(x, np.array(vals, float), atol=1e-15)
+        assert bad > 0
+    else:
+        Ls, Us, dinv = _tridiag3_factors()
+        bad = 0
+        for row in _read_golden("ilu_tridiag3.txt"):
+            _, tl, tu, *vals = row
+            x = ns["ilu0_sweep"](Ls, Us, dinv, tridiag(3), np.ones(3), np.zeros(3), int(tl), int(tu))
+            bad += not np.allclose(x, np.array(vals, float), atol=1e-15)
+        assert bad > 0

@@ -1,0 +1,208 @@
+// Host-side Ruge-Stuben setup used as INPUT GENERATION for both the CUDA solve path and the
+// CPU oracle: strength of connection, PMIS coarsening, BAMG-direct interpolation and ILU(0)
+// (row-scaled LDU). The Galerkin product and transposes are done by the Python caller.
+//
+// Paper references (arXiv:2112.14681):
+//   strength  |a_ij| >= theta * max_{k!=i} |a_ik|                         -- Sec. 5.1, eq. (strength)
+//   PMIS      Luby-type maximal independent set with random weights       -- Sec. 5.1
+//   BAMG-direct closed-form weights w_ij                                   -- Sec. 5.1, eq. (bamgdir)
+//   ILU(0) as L (unit lower) * D_U * (I + U_s), rows of U scaled by diag  -- Sec. 5.3.2, Alg. 2 footnote
+//
+// Conventions: CSR with 0-based int32 indices, columns sorted ascending within each row,
+// the diagonal entry present in every row.
+#include <cstdint>
+#include <cmath>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// S_i = { j != i : |a_ij| >= theta * max_{k != i} |a_ik| } stored as a flag per nonzero.
+void strength(int n, const int* rp, const int* ci, const double* v, double theta, std::vector<char>& s) {
+  s.assign(rp[n], 0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    double mx = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] != i) mx = std::max(mx, std::fabs(v[p]));
+    if (mx == 0.0) continue;
+    const double thr = theta * mx;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] != i && v[p] != 0.0 && std::fabs(v[p]) >= thr) s[p] = 1;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// PMIS C/F splitting. cf[i] = coarse index (>= 0) for C-points, -1 for F-points.
+// Returns the number of coarse points, or -1 on invalid input.
+int nsw_amg_coarsen(int n, const int* rp, const int* ci, const double* v, double theta, uint64_t seed, int* cf) {
+  if (n <= 0) return -1;
+  std::vector<char> s;
+  strength(n, rp, ci, v, theta, s);
+  // Transpose strength: ST_j = { i : j in S_i }.
+  std::vector<int> strp(n + 1, 0), stci;
+  for (int i = 0; i < n; ++i)
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (s[p]) strp[ci[p] + 1]++;
+  for (int i = 0; i < n; ++i) strp[i + 1] += strp[i];
+  stci.resize(strp[n]);
+  {
+    std::vector<int> fill(strp.begin(), strp.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (s[p]) stci[fill[ci[p]]++] = i;
+  }
+  // Weights lambda_i = |ST_i| + U[0,1) from a counter-based generator.
+  std::vector<double> lam(n);
+  for (int i = 0; i < n; ++i) {
+    const double u = (double)(splitmix64(seed ^ (0xA24BAED4963EE407ull * (uint64_t)(i + 1))) >> 11) * 0x1.0p-53;
+    lam[i] = (double)(strp[i + 1] - strp[i]) + u;
+  }
+  // state: 0 undecided, 1 C, 2 F
+  std::vector<char> st(n, 0);
+  for (int i = 0; i < n; ++i) {
+    bool dep_any = false;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) dep_any |= (s[p] != 0);
+    const bool infl_any = strp[i + 1] > strp[i];
+    if (!infl_any) st[i] = 2;  // influences no one: cannot serve as an interpolation point
+    if (!dep_any && !infl_any) st[i] = 2;
+  }
+  std::vector<int> newc;
+  for (int round = 0; round < 10 * n + 10; ++round) {
+    newc.clear();
+    bool any_undecided = false;
+    for (int i = 0; i < n; ++i) {
+      if (st[i] != 0) continue;
+      any_undecided = true;
+      bool is_max = true;
+      auto beats = [&](int j) {  // true if undecided j outranks i
+        if (j == i || st[j] != 0) return false;
+        return lam[j] > lam[i] || (lam[j] == lam[i] && j > i);
+      };
+      for (int p = rp[i]; p < rp[i + 1] && is_max; ++p)
+        if (s[p] && beats(ci[p])) is_max = false;
+      for (int q = strp[i]; q < strp[i + 1] && is_max; ++q)
+        if (beats(stci[q])) is_max = false;
+      if (is_max) newc.push_back(i);
+    }
+    if (!any_undecided) break;
+    for (int c : newc) st[c] = 1;
+    for (int c : newc)
+      for (int q = strp[c]; q < strp[c + 1]; ++q)
+        if (st[stci[q]] == 0) st[stci[q]] = 2;
+  }
+  // F-points with no strong C-neighbour are promoted to C.
+  for (int i = 0; i < n; ++i) {
+    if (st[i] != 2) continue;
+    bool has_c = false;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (s[p] && st[ci[p]] == 1) { has_c = true; break; }
+    if (!has_c) st[i] = 1;
+  }
+  int nc = 0;
+  for (int i = 0; i < n; ++i) cf[i] = (st[i] == 1) ? nc++ : -1;
+  return nc;
+}
+
+// BAMG-direct interpolation with f = 1:
+//   w_ij = -(a_ij + beta_i / |C_i^s|) / (a_ii + sum_{k weak} a_ik),  beta_i = sum_{k in F_i^s} a_ik.
+// Output P (n x nc) in CSR; P arrays must hold n+1 row pointers and nnz(A) entries.
+// Returns nnz(P) or -1 if a row has a zero denominator.
+int64_t nsw_amg_interp(int n, const int* rp, const int* ci, const double* v, double theta, const int* cf,
+                       int* prp, int* pci, double* pv) {
+  std::vector<char> s;
+  strength(n, rp, ci, v, theta, s);
+  std::vector<int> cnt(n, 0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    if (cf[i] >= 0) { cnt[i] = 1; continue; }
+    int c = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (s[p] && cf[ci[p]] >= 0) ++c;
+    cnt[i] = c;
+  }
+  prp[0] = 0;
+  for (int i = 0; i < n; ++i) prp[i + 1] = prp[i] + cnt[i];
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+  for (int i = 0; i < n; ++i) {
+    int o = prp[i];
+    if (cf[i] >= 0) { pci[o] = cf[i]; pv[o] = 1.0; continue; }
+    double aii = 0.0, weak = 0.0, beta = 0.0;
+    int nc = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j == i) { aii += v[p]; continue; }
+      if (!s[p]) weak += v[p];
+      else if (cf[j] >= 0) ++nc;
+      else beta += v[p];
+    }
+    const double den = aii + weak;
+    if (den == 0.0 || nc == 0) { bad += 1; continue; }
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j == i || !s[p] || cf[j] < 0) continue;
+      pci[o] = cf[j];
+      pv[o] = -(v[p] + beta / nc) / den;
+      ++o;
+    }
+  }
+  // Coarse indices are increasing with fine index, so each row is already sorted.
+  return bad ? -1 : (int64_t)prp[n];
+}
+
+// ILU(0) on the pattern of A, returned as  A ~ (I + L_s) D_U (I + U_s):
+//   L_s strictly lower (multipliers), U_s strictly upper with rows scaled by 1/u_ii, dU_inv = 1/u_ii.
+// L arrays hold n+1 / nnz_strict_lower entries, U arrays n+1 / nnz_strict_upper.
+// Returns 0, or -(i+1) if a zero pivot appears in row i.
+int nsw_ilu0(int n, const int* rp, const int* ci, const double* v, int* lrp, int* lci, double* lv, int* urp,
+             int* uci, double* uv, double* dUinv) {
+  std::vector<double> a(v, v + rp[n]);
+  std::vector<int> diag(n, -1), pos(n, -1);
+  for (int i = 0; i < n; ++i)
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) diag[i] = p;
+  for (int i = 0; i < n; ++i) {
+    if (diag[i] < 0) return -(i + 1);
+    for (int p = rp[i]; p < rp[i + 1]; ++p) pos[ci[p]] = p;
+    for (int p = rp[i]; p < diag[i]; ++p) {
+      const int k = ci[p];
+      const double piv = a[diag[k]];
+      if (piv == 0.0) return -(k + 1);
+      a[p] /= piv;
+      const double lik = a[p];
+      for (int q = diag[k] + 1; q < rp[k + 1]; ++q) {
+        const int j = ci[q];
+        if (pos[j] >= 0 && pos[j] > p) a[pos[j]] -= lik * a[q];
+      }
+    }
+    for (int p = rp[i]; p < rp[i + 1]; ++p) pos[ci[p]] = -1;
+    if (a[diag[i]] == 0.0) return -(i + 1);
+  }
+  lrp[0] = 0;
+  urp[0] = 0;
+  int lo = 0, uo = 0;
+  for (int i = 0; i < n; ++i) {
+    const double inv = 1.0 / a[diag[i]];
+    dUinv[i] = inv;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] < i) { lci[lo] = ci[p]; lv[lo] = a[p]; ++lo; }
+      else if (ci[p] > i) { uci[uo] = ci[p]; uv[uo] = a[p] * inv; ++uo; }
+    }
+    lrp[i + 1] = lo;
+    urp[i + 1] = uo;
+  }
+  return 0;
+}
+
+}  // extern "C"

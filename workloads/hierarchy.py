@@ -1,0 +1,158 @@
+"""Ruge-Stuben hierarchy built on the host, fed identically to the CUDA path and the oracle.
+
+Per level l: A_l (CSR), P_l (prolongation from level l+1 to l), R_l = P_l^T, and on requested
+levels the ILU(0) factors A_l ~ (I + L_s) D_U (I + U_s). The coarsest level carries its dense
+inverse when it has at most `coarse_max` rows. Coarse operators are the Galerkin products
+A_{l+1} = R_l A_l P_l (Sec. 5, eq. A_k).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libnsw_setup.so")
+_SRC = os.path.join(_HERE, "csrc", "amg_setup.cpp")
+_lib = None
+
+
+def build_setup_library(force: bool = False) -> str:
+    """Compile the host setup library (g++, OpenMP) next to this file."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O3", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_setup_library())
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        lib.nsw_amg_coarsen.argtypes = [ctypes.c_int, i32p, i32p, f64p, ctypes.c_double, ctypes.c_uint64, i32p]
+        lib.nsw_amg_coarsen.restype = ctypes.c_int
+        lib.nsw_amg_interp.argtypes = [ctypes.c_int, i32p, i32p, f64p, ctypes.c_double, i32p, i32p, i32p, f64p]
+        lib.nsw_amg_interp.restype = ctypes.c_int64
+        lib.nsw_ilu0.argtypes = [ctypes.c_int, i32p, i32p, f64p, i32p, i32p, f64p, i32p, i32p, f64p, f64p]
+        lib.nsw_ilu0.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _csr(A) -> sp.csr_matrix:
+    A = sp.csr_matrix(A)
+    A.sum_duplicates()
+    A.sort_indices()
+    A.indices = A.indices.astype(np.int32, copy=False)
+    A.indptr = A.indptr.astype(np.int32, copy=False)
+    return A
+
+
+@dataclass
+class Level:
+    A: sp.csr_matrix
+    P: sp.csr_matrix | None = None  # n_l x n_{l+1}
+    R: sp.csr_matrix | None = None  # n_{l+1} x n_l
+    ilu_L: sp.csr_matrix | None = None  # strictly lower L_s
+    ilu_U: sp.csr_matrix | None = None  # strictly upper U_s (rows scaled by 1/u_ii)
+    ilu_dinv: np.ndarray | None = None  # 1/u_ii
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+
+@dataclass
+class Hierarchy:
+    levels: list[Level]
+    coarse_inv: np.ndarray | None = None  # dense inverse of the coarsest A, row-major
+    theta: float = 0.25
+    seed: int = 0
+    info: dict = field(default_factory=dict)
+
+    @property
+    def nlevels(self) -> int:
+        return len(self.levels)
+
+    def operator_complexity(self) -> float:
+        return sum(l.A.nnz for l in self.levels) / self.levels[0].A.nnz
+
+
+def coarsen(A: sp.csr_matrix, theta: float, seed: int) -> tuple[np.ndarray, int]:
+    lib = _load()
+    n = A.shape[0]
+    cf = np.empty(n, np.int32)
+    nc = lib.nsw_amg_coarsen(n, A.indptr, A.indices, A.data, theta, seed & 0xFFFFFFFFFFFFFFFF, cf)
+    if nc < 0:
+        raise ValueError("coarsening failed")
+    return cf, nc
+
+
+def interpolation(A: sp.csr_matrix, theta: float, cf: np.ndarray, nc: int) -> sp.csr_matrix:
+    lib = _load()
+    n = A.shape[0]
+    prp = np.empty(n + 1, np.int32)
+    pci = np.empty(A.nnz + n, np.int32)
+    pv = np.empty(A.nnz + n, np.float64)
+    nnz = lib.nsw_amg_interp(n, A.indptr, A.indices, A.data, theta, cf, prp, pci, pv)
+    if nnz < 0:
+        raise ValueError("interpolation failed: an F-row without strong C-neighbours or zero denominator")
+    return sp.csr_matrix((pv[:nnz].copy(), pci[:nnz].copy(), prp), shape=(n, nc))
+
+
+def ilu0(A: sp.csr_matrix):
+    """ILU(0) on pattern(A): returns (L_s, U_s, dU_inv) with A ~ (I + L_s) diag(1/dU_inv) (I + U_s)."""
+    lib = _load()
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    nl = int(np.count_nonzero(A.indices < rows))
+    nu = int(np.count_nonzero(A.indices > rows))
+    lrp, lci, lv = np.empty(n + 1, np.int32), np.empty(max(nl, 1), np.int32), np.empty(max(nl, 1), np.float64)
+    urp, uci, uv = np.empty(n + 1, np.int32), np.empty(max(nu, 1), np.int32), np.empty(max(nu, 1), np.float64)
+    dinv = np.empty(n, np.float64)
+    rc = lib.nsw_ilu0(n, A.indptr, A.indices, A.data, lrp, lci, lv, urp, uci, uv, dinv)
+    if rc != 0:
+        raise ValueError(f"ILU(0) zero pivot in row {-rc - 1}")
+    L = sp.csr_matrix((lv[:nl], lci[:nl], lrp), shape=(n, n))
+    U = sp.csr_matrix((uv[:nu], uci[:nu], urp), shape=(n, n))
+    return _csr(L), _csr(U), dinv
+
+
+def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: int = 512, seed: int = 0,
+                    ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512) -> Hierarchy:
+    """Build the Ruge-Stuben hierarchy of A (strength theta, PMIS, BAMG-direct, Galerkin RAP).
+
+    Coarsening stops when a level has at most `coarse_max` rows, when `max_levels` levels exist,
+    or when a coarsening step keeps more than 90% of the points. ILU(0) factors are attached to
+    the levels listed in `ilu_levels` (None for every non-coarsest level). The coarsest level
+    gets a dense inverse when it has at most `direct_max` rows.
+    """
+    A = _csr(A)
+    levels = [Level(A=A)]
+    while len(levels) < max_levels and levels[-1].n > coarse_max:
+        Al = levels[-1].A
+        cf, nc = coarsen(Al, theta, seed + 7919 * len(levels))
+        if nc < min_coarse or nc >= 0.9 * Al.shape[0] or nc == 0:
+            break
+        P = _csr(interpolation(Al, theta, cf, nc))
+        R = _csr(P.T)
+        Ac = _csr(R @ (Al @ P))
+        levels[-1].P, levels[-1].R = P, R
+        levels.append(Level(A=Ac))
+    want = range(len(levels) - 1) if ilu_levels is None else ilu_levels
+    for l in want:
+        if 0 <= l < len(levels) - 1:
+            levels[l].ilu_L, levels[l].ilu_U, levels[l].ilu_dinv = ilu0(levels[l].A)
+    H = Hierarchy(levels=levels, theta=theta, seed=seed)
+    if levels[-1].n <= direct_max:
+        H.coarse_inv = np.ascontiguousarray(np.linalg.inv(levels[-1].A.toarray()))
+    H.info = {"n": [l.n for l in levels], "nnz": [int(l.A.nnz) for l in levels],
+              "operator_complexity": H.operator_complexity()}
+    return H
