@@ -1,0 +1,166 @@
+/*
+ * nsamg -- solve phase of the GMRES + C-AMG method of arXiv:2112.14681
+ * ("Neumann Series in GMRES and Algebraic Multigrid Smoothers") on one NVIDIA B300 (sm_103a).
+ *
+ * C ABI. Plain pointers and sizes only; no exceptions cross this boundary. Every function that
+ * can fail returns an nsamg status code (0 = success, 1 = not converged, negative = error) and
+ * records a message retrievable with nsamg_last_error() (thread-local).
+ *
+ * Memory: "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of the
+ * device that was current when the handle was created (for example torch.empty(..., device="cuda")
+ * storage). All index arrays are 0-based int32 with columns sorted ascending in each row; all
+ * values are float64 (IEEE binary64), vectors contiguous.
+ */
+#ifndef NSAMG_H
+#define NSAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define NSAMG_OK 0                 /* converged (or a happy breakdown, beta = 0)               */
+#define NSAMG_NOT_CONVERGED 1      /* maxit reached; x holds the last iterate                  */
+#define NSAMG_PENDING 2            /* asynchronous request still running                       */
+#define NSAMG_ERR_INVALID_ARG (-1) /* null pointer, bad size or parameter out of range         */
+#define NSAMG_ERR_BAD_MATRIX (-2)  /* CSR validation failed (rowptr, column range, diagonal)   */
+#define NSAMG_ERR_OOM (-3)         /* cudaMalloc failed                                        */
+#define NSAMG_ERR_CUDA (-4)        /* any other CUDA runtime error (message in last_error)     */
+#define NSAMG_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                       */
+#define NSAMG_ERR_NONFINITE (-6)   /* NaN/Inf met in a reduction (b, x0 or the iteration)      */
+#define NSAMG_ERR_ADMISSION (-7)   /* request rejected by the admission policy                 */
+
+/* ---- smoothers (Sec. 5.2, 5.3 and the l1-Jacobi comparison of Sec. 6.1) ------------------ */
+#define NSAMG_SMOOTHER_POLY_GS 0     /* polynomial Gauss-Seidel: truncated Neumann series of (D+L)^-1 */
+#define NSAMG_SMOOTHER_JACOBI_L1 1   /* x += D_l1^-1 (b - A x), d_ii = sum_j |a_ij|                  */
+#define NSAMG_SMOOTHER_ILU0 2        /* ILU(0) with Neumann-series triangular solves, every level with factors */
+#define NSAMG_SMOOTHER_HYBRID_ILU0 3 /* ILU(0) on the finest level, polynomial GS below (Sec. 6.2)      */
+
+#define NSAMG_MAX_RESTART 64         /* largest supported GMRES restart length m */
+
+/* Host CSR matrix (nrows x ncols, nnz entries). An absent matrix has nrows = 0. */
+typedef struct {
+  int32_t nrows, ncols;
+  int64_t nnz;
+  const int32_t* rowptr; /* nrows + 1 */
+  const int32_t* col;    /* nnz */
+  const double* val;     /* nnz */
+} nsamg_csr;
+
+/* One level of a Ruge-Stuben hierarchy built on the host (input generation).
+ * A: level operator A_l. P: prolongation n_l x n_{l+1}; R = P^T: restriction n_{l+1} x n_l
+ * (both absent on the coarsest level). ilu_L / ilu_U / ilu_dinv: optional ILU(0) factors with
+ * A_l ~ (I + L_s) diag(1/ilu_dinv) (I + U_s) (Sec. 5.3.2); ilu_L.nrows = 0 when absent. */
+typedef struct {
+  nsamg_csr A, P, R, ilu_L, ilu_U;
+  const double* ilu_dinv;
+} nsamg_level_desc;
+
+typedef struct {
+  int32_t nlevels;
+  const nsamg_level_desc* levels; /* nlevels entries, finest first */
+  const double* coarse_inv;       /* dense row-major inverse of the coarsest A (n_L^2), or NULL */
+} nsamg_hierarchy_desc;
+
+/* Solve-phase parameters. Defaults from nsamg_default_params(). */
+typedef struct {
+  int32_t smoother;      /* NSAMG_SMOOTHER_*                                                   */
+  int32_t neumann_terms; /* k terms of the polynomial GS series (k = 1 is Jacobi), >= 1          */
+  int32_t ilu_terms_L;   /* terms of sum (-L_s)^j  (3 = "three Jacobi iterations", Sec. 6.2)     */
+  int32_t ilu_terms_U;   /* terms of sum (-U_s)^j                                                */
+  int32_t pre_sweeps;    /* sweeps before the coarse correction (forward GS direction)           */
+  int32_t post_sweeps;   /* sweeps after it (backward GS direction)                              */
+  int32_t coarse_sweeps; /* sweeps on the coarsest level when no dense inverse is given          */
+  int32_t restart;       /* GMRES restart length m, 1..NSAMG_MAX_RESTART                         */
+  int32_t vcycle_fp32;   /* 0: FP64 V-cycle. 1: FP32 matrices and vectors in the V-cycle         */
+  int32_t t_exact;       /* 0: T = I - L (truncated Neumann, Algorithm 1). 1: T = (I + L)^-1    */
+  int32_t use_graph;     /* 1: run each solve as one CUDA graph with device-side loop control    */
+  int32_t spmv_group;    /* threads per row for CSR kernels: 0 = autotune at setup, else 1..32  */
+} nsamg_params;
+
+typedef struct {
+  int32_t iters;          /* Arnoldi columns used, summed over restart cycles                   */
+  int32_t restarts;       /* completed restart cycles after the first                           */
+  int32_t converged;      /* 1 if ||b - A x|| / ||b|| <= rtol                                   */
+  int32_t status;         /* same value the call returned                                       */
+  double relres_true;     /* ||b - A x|| / ||b|| from the final true residual (eq. relres)      */
+  double relres_implicit; /* |g_{k+1}| / ||b|| from the Givens recurrence at exit               */
+  double bnorm;           /* ||b||                                                              */
+} nsamg_stats;
+
+typedef struct nsamg_handle nsamg_handle;
+
+/* Fill *p with the defaults: POLY_GS, 2 Neumann terms, 3+3 ILU terms, 1+1 sweeps, 4 coarse
+ * sweeps, m = 30, FP64 V-cycle, T = I - L, CUDA graph on, autotuned CSR kernels. */
+void nsamg_default_params(nsamg_params* p);
+
+/* Upload a host-built hierarchy (Sec. 5: A_k = R_k A_{k-1} P_k, R_k = P_k^T) and allocate the
+ * GMRES workspace. The library copies everything it needs; no host pointer is kept. The split
+ * A = L + D + U, D^-1 and the l1 diagonal are formed here. `cuda_stream` (a cudaStream_t, may
+ * be NULL for the legacy default stream) is the stream every later call on this handle uses.
+ * Errors: INVALID_ARG (null pointers, nlevels < 1, bad params), BAD_MATRIX (validation), OOM,
+ * CUDA. On error *out is set to NULL. */
+int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, void* cuda_stream,
+                          nsamg_handle** out);
+
+/* Solve A x = b with right-preconditioned flexible one-reduce MGS-GMRES(m) whose projection
+ * uses T = I - L (Algorithm 1, Sec. 4), one V-cycle per Arnoldi step (Sec. 5), restarting from
+ * the true residual until ||b - A x||/||b|| <= rtol (eq. relres) or `maxit` Arnoldi steps.
+ * d_b, d_x: device float64 arrays of n = A_0 rows; d_x holds x0 on entry and x on return.
+ * Blocks until the solve finishes. Returns OK, NOT_CONVERGED, or an error. st may be NULL. */
+int nsamg_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* st);
+
+/* Same as nsamg_solve with HOST arrays: copies b and x0 to the device, solves, copies x back. */
+int nsamg_solve_host(nsamg_handle* h, const double* h_b, double* h_x, double rtol, int maxit, nsamg_stats* st);
+
+/* z = M^-1 r: one V-cycle with zero initial guess (Sec. 5). d_r, d_z: device float64, n entries.
+ * Asynchronous on the handle's stream. */
+int nsamg_apply_vcycle(nsamg_handle* h, const double* d_r, double* d_z);
+
+/* Per-kernel entry points on a level of the handle's hierarchy (asynchronous, device arrays):
+ *   nsamg_level_spmv:     y = A_l x                                     (Sec. 1, SpMV)
+ *   nsamg_level_residual: r = b - A_l x                                  (eq. relres)
+ *   nsamg_level_smooth:   one smoother sweep x <- x + B (b - A_l x) of the level's smoother;
+ *                         backward = 1 selects the backward GS direction; x_is_zero = 1 lets the
+ *                         kernels skip the A pass (x must then hold zeros or anything: it is
+ *                         overwritten).
+ *   nsamg_level_restrict: y_{l+1} = R_l r                                (Sec. 5)
+ *   nsamg_level_prolong:  x_l += P_l e                                   (Sec. 5)
+ *   nsamg_coarse_solve:   z = A_L^-1 b on the coarsest level (dense inverse, or sweeps)
+ */
+int nsamg_level_size(nsamg_handle* h, int level);
+int nsamg_num_levels(nsamg_handle* h);
+int nsamg_level_spmv(nsamg_handle* h, int level, const double* d_x, double* d_y);
+int nsamg_level_residual(nsamg_handle* h, int level, const double* d_b, const double* d_x, double* d_r);
+int nsamg_level_smooth(nsamg_handle* h, int level, int backward, int x_is_zero, const double* d_b, double* d_x);
+int nsamg_level_restrict(nsamg_handle* h, int level, const double* d_r, double* d_y);
+int nsamg_level_prolong(nsamg_handle* h, int level, const double* d_e, double* d_x);
+int nsamg_coarse_solve(nsamg_handle* h, const double* d_b, double* d_z);
+
+/* One-reduce Arnoldi kernels on caller data (Algorithm 1 steps 6-12), asynchronous on `stream`:
+ *   nsamg_gram:   out[0..i] = [V_i, vt]^T vt and out[i+1..2i+1] = [V_i, vt]^T w, where V_i is the
+ *                 n x i column-major block at d_V with leading dimension ldv (>= n) and vt is
+ *                 column i of the same block (so the block holds i+1 columns). One pass over the
+ *                 i+2 vectors, deterministic fixed-order reduction. 0 <= i < NSAMG_MAX_RESTART.
+ *                 Uses library-owned device scratch (allocated on first use per device).
+ *   nsamg_update: given beta and h[0..i] (device), writes v_i = vt / beta in place of column i
+ *                 and column i+1 = w / beta - sum_{j<=i} h_j v_j; returns ||column i+1||^2 in
+ *                 *d_sumsq (device). */
+int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream);
+int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
+                 double* d_sumsq, void* stream);
+
+/* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
+int nsamg_level_group(nsamg_handle* h, int level);
+
+void nsamg_destroy(nsamg_handle* h);
+const char* nsamg_status_str(int status);
+const char* nsamg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSAMG_H */

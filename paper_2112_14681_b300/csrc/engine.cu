@@ -1,0 +1,1104 @@
+// Host engine and C ABI of nsamg: hierarchy upload, V-cycle orchestration, the one-reduce
+// GMRES(m) loop (run as one CUDA graph with device-side WHILE conditionals, or as a plain
+// launch loop), and the per-kernel entry points.
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "nsamg.h"
+#include "kernels.cuh"
+#include "gmres.cuh"
+
+using namespace nsamg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? NSAMG_ERR_OOM : NSAMG_ERR_CUDA;
+  return fail(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t threads) { return (int)std::max<int64_t>(1, (threads + kThreads - 1) / kThreads); }
+
+// ------------------------------------------------------------------------------------------
+// Device CSR
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct DCSR {
+  int n = 0, m = 0;
+  int64_t nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  T* v = nullptr;
+  int G = 1;
+  bool present() const { return n > 0; }
+};
+
+struct HostCSR {  // host copy used while building derived matrices
+  int n = 0, m = 0;
+  std::vector<int> rp, ci;
+  std::vector<double> v;
+};
+
+int validate(const nsamg_csr& A, bool square, bool need_diag, const char* name) {
+  if (A.nrows <= 0) return fail(NSAMG_ERR_INVALID_ARG, std::string(name) + ": empty matrix");
+  if (!A.rowptr || (A.nnz > 0 && (!A.col || !A.val))) return fail(NSAMG_ERR_INVALID_ARG, std::string(name) + ": null array");
+  if (A.nnz < 0 || A.nnz > INT32_MAX) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": nnz out of range");
+  if (square && A.ncols != A.nrows) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": not square");
+  if (A.rowptr[0] != 0 || A.rowptr[A.nrows] != A.nnz) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": bad rowptr ends");
+  for (int i = 0; i < A.nrows; ++i) {
+    const int b = A.rowptr[i], e = A.rowptr[i + 1];
+    if (e < b) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": rowptr not monotone at row " + std::to_string(i));
+    bool diag = false;
+    for (int p = b; p < e; ++p) {
+      const int c = A.col[p];
+      if (c < 0 || c >= A.ncols) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": column out of range in row " + std::to_string(i));
+      if (p > b && c <= A.col[p - 1]) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": columns not sorted in row " + std::to_string(i));
+      if (c == i && A.val[p] != 0.0) diag = true;
+      if (!std::isfinite(A.val[p])) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": non-finite value in row " + std::to_string(i));
+    }
+    if (need_diag && !diag) return fail(NSAMG_ERR_BAD_MATRIX, std::string(name) + ": missing or zero diagonal in row " + std::to_string(i));
+  }
+  return NSAMG_OK;
+}
+
+template <typename T>
+int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t nnz, DCSR<T>& d) {
+  d.n = n;
+  d.m = m;
+  d.nnz = nnz;
+  CK(cudaMalloc(&d.rp, sizeof(int) * (n + 1)));
+  CK(cudaMemcpy(d.rp, rp, sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  const int64_t cap = std::max<int64_t>(nnz, 1);
+  CK(cudaMalloc(&d.ci, sizeof(int) * cap));
+  CK(cudaMalloc(&d.v, sizeof(T) * cap));
+  if (nnz > 0) {
+    CK(cudaMemcpy(d.ci, ci, sizeof(int) * nnz, cudaMemcpyHostToDevice));
+    if constexpr (sizeof(T) == sizeof(double)) {
+      CK(cudaMemcpy(d.v, v, sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<T> tmp(v, v + nnz);
+      CK(cudaMemcpy(d.v, tmp.data(), sizeof(T) * nnz, cudaMemcpyHostToDevice));
+    }
+  }
+  const double avg = n ? (double)nnz / n : 0.0;
+  d.G = avg <= 12 ? 1 : avg <= 24 ? 2 : avg <= 48 ? 4 : avg <= 96 ? 8 : 16;
+  return NSAMG_OK;
+}
+
+template <typename T>
+int upload(const HostCSR& h, DCSR<T>& d) {
+  return upload<T>(h.rp.data(), h.ci.data(), h.v.data(), h.n, h.m, (int64_t)h.ci.size(), d);
+}
+
+template <typename T>
+int upload(const nsamg_csr& c, DCSR<T>& d) {
+  return upload<T>(c.rowptr, c.col, c.val, c.nrows, c.ncols, c.nnz, d);
+}
+
+template <typename T>
+void release(DCSR<T>& d) {
+  cudaFree(d.rp);
+  cudaFree(d.ci);
+  cudaFree(d.v);
+  d = DCSR<T>();
+}
+
+template <typename T>
+int upload_vec(const std::vector<double>& h, T** d) {
+  CK(cudaMalloc(d, sizeof(T) * std::max<size_t>(h.size(), 1)));
+  std::vector<T> tmp(h.begin(), h.end());
+  CK(cudaMemcpy(*d, tmp.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return NSAMG_OK;
+}
+
+// Triangular part of A (strict lower if lower, else strict upper), rows scaled by rs (if given)
+// and columns scaled by cs (if given).
+HostCSR tri_part(const nsamg_csr& A, bool lower, const std::vector<double>* rs, const std::vector<double>* cs) {
+  HostCSR h;
+  h.n = A.nrows;
+  h.m = A.ncols;
+  h.rp.assign(A.nrows + 1, 0);
+  for (int i = 0; i < A.nrows; ++i) {
+    for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
+      const int c = A.col[p];
+      if (lower ? c < i : c > i) {
+        double v = A.val[p];
+        if (rs) v *= (*rs)[i];
+        if (cs) v *= (*cs)[c];
+        h.ci.push_back(c);
+        h.v.push_back(v);
+      }
+    }
+    h.rp[i + 1] = (int)h.ci.size();
+  }
+  return h;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row-kernel launch
+// ------------------------------------------------------------------------------------------
+template <typename TM, typename TX, typename TY>
+void launch_row(const RowOp<TM, TX, TY>& op, int G, cudaStream_t s) {
+  if (op.n <= 0) return;
+  if (!op.v) G = 1;
+  const int nb = blocks_for((int64_t)op.n * G);
+  switch (G) {
+    case 1: k_row<1, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    case 2: k_row<2, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    case 4: k_row<4, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    case 8: k_row<8, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    case 16: k_row<16, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    default: k_row<32, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+  }
+}
+
+template <typename T>
+using VC = VRef<const T>;
+
+template <typename T>
+inline VC<T> cref(VRef<T> r) {
+  VC<T> c;
+  c.p = r.p;
+  c.sel = r.sel;
+  c.ld = r.ld;
+  return c;
+}
+template <typename T>
+inline VC<T> cref(const T* p) {
+  VC<T> c;
+  c.p = p;
+  return c;
+}
+
+// out = [add +] [scale *] (bscale*base -/+ M src)  -- builders for the common forms
+template <typename T>
+RowOp<T, T, T> op_mat(const DCSR<T>& M, VC<T> src) {
+  RowOp<T, T, T> op;
+  op.n = M.n;
+  op.rp = M.rp;
+  op.ci = M.ci;
+  op.v = M.v;
+  op.src = src;
+  return op;
+}
+
+// ------------------------------------------------------------------------------------------
+// Levels
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct Level {
+  int n = 0;
+  DCSR<T> A;       // A_l
+  DCSR<T> L2, U2;  // D^-1 L D^-1, D^-1 U D^-1 (first pass from a zero initial guess)
+  DCSR<T> L1, U1;  // D^-1 L, D^-1 U (later passes)
+  DCSR<T> P, R;    // prolongation (n x n_c), restriction (n_c x n)
+  DCSR<T> iL, iU;  // ILU(0) L_s, U_s
+  bool ilu = false;
+  T* dinv = nullptr;
+  T* dl1inv = nullptr;
+  T* idinv = nullptr;
+  T *b = nullptr, *x = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
+  char kind = 'p';  // 'p' poly GS, 'i' ILU, 'j' l1-Jacobi
+};
+
+}  // namespace
+
+struct nsamg_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  nsamg_params p{};
+  std::vector<Level<double>> lv;
+  double* coarse_inv = nullptr;
+  int nc = 0;
+  // GMRES workspace
+  int n = 0, m = 0;
+  int64_t ld = 0;
+  double* V = nullptr;  // (m+1) columns
+  double* Z = nullptr;  // m columns
+  double* w = nullptr;
+  GState* st = nullptr;
+  GState* h_st = nullptr;  // pinned host mirror
+  Scratch scr{};
+  int gram_blocks = 0, update_blocks = 0;
+  int64_t partial_cap = 0;
+  // graph
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Smoothers (Sec. 5.2 / 5.3) as sequences of row-kernel launches on one level.
+// b, x: level vectors (VRefs so level 0 can address V[:, i] / Z[:, i]); skip: stop flag.
+// ------------------------------------------------------------------------------------------
+struct Ctx {
+  cudaStream_t s;
+  const int* skip;
+};
+
+template <typename T>
+void run(RowOp<T, T, T> op, int G, const Ctx& c) {
+  op.skip = c.skip;
+  launch_row(op, G, c.s);
+}
+
+template <typename T>
+RowOp<T, T, T> op_vec(int n) {
+  RowOp<T, T, T> op;
+  op.n = n;
+  return op;
+}
+
+// Polynomial Gauss-Seidel with k terms:
+//   x <- x + g,  g = sum_{j<k} (-D^-1 T)^j D^-1 r,  r = b - A x,  T = L (forward) or U (backward),
+// evaluated by the Jacobi recurrence g_0 = D^-1 r, g_j = D^-1 r - (D^-1 T) g_{j-1}
+// (eqs. jr-initial-guess, jr, jacobi). With a zero initial guess r = b and the first pass uses
+// the pre-scaled D^-1 T D^-1 so that g_1 = D^-1 b - (D^-1 T D^-1) b needs no separate g_0.
+template <typename T>
+void sweep_poly(Level<T>& L, VC<T> b, VRef<T> x, bool backward, bool x_zero, int k, const Ctx& c) {
+  const DCSR<T>& M2 = backward ? L.U2 : L.L2;
+  const DCSR<T>& M1 = backward ? L.U1 : L.L1;
+  T* g[2] = {L.t1, L.t2};
+  if (x_zero) {
+    if (k == 1) {  // x = D^-1 b
+      auto op = op_vec<T>(L.n);
+      op.base = b;
+      op.bscale = L.dinv;
+      op.out = x;
+      run(op, 1, c);
+      return;
+    }
+    for (int j = 1; j < k; ++j) {
+      const bool last = (j == k - 1);
+      auto op = (j == 1) ? op_mat(M2, b) : op_mat(M1, cref(g[(j - 1) & 1]));
+      op.base = b;
+      op.bscale = L.dinv;
+      op.neg = 1;
+      op.out = last ? x : vref(g[j & 1]);
+      run(op, (j == 1 ? M2 : M1).G, c);
+    }
+    return;
+  }
+  // r_hat = D^-1 (b - A x)
+  {
+    auto op = op_mat(L.A, cref(x));
+    op.base = b;
+    op.neg = 1;
+    op.scale = L.dinv;
+    op.out = vref(L.r);
+    run(op, L.A.G, c);
+  }
+  if (k == 1) {  // x += r_hat
+    auto op = op_vec<T>(L.n);
+    op.base = cref((const T*)L.r);
+    op.add = cref(x);
+    op.out = x;
+    run(op, 1, c);
+    return;
+  }
+  for (int j = 1; j < k; ++j) {
+    const bool last = (j == k - 1);
+    auto op = op_mat(M1, (j == 1) ? cref((const T*)L.r) : cref(g[(j - 1) & 1]));
+    op.base = cref((const T*)L.r);
+    op.neg = 1;
+    if (last) {
+      op.add = cref(x);
+      op.out = x;
+    } else {
+      op.out = vref(g[j & 1]);
+    }
+    run(op, M1.G, c);
+  }
+}
+
+// ILU(0) smoother with Neumann-series triangular solves (Sec. 5.3.2, eq. Neumann; Algorithm 2
+// with row scaling): x <- x + sum_{j<tU} (-U_s)^j D_U^-1 sum_{j<tL} (-L_s)^j r, r = b - A x,
+// evaluated as y_1 = r, y_j = r - L_s y_{j-1}; f = D_U^-1 y; v_1 = f, v_j = f - U_s v_{j-1}.
+template <typename T>
+void sweep_ilu(Level<T>& L, VC<T> b, VRef<T> x, bool x_zero, int tL, int tU, const Ctx& c) {
+  VC<T> r = b;
+  if (!x_zero) {
+    auto op = op_mat(L.A, cref(x));
+    op.base = b;
+    op.neg = 1;
+    op.out = vref(L.r);
+    run(op, L.A.G, c);
+    r = cref((const T*)L.r);
+  }
+  T* y[2] = {L.t1, L.t2};
+  T* f = L.t3;
+  if (tL == 1) {
+    auto op = op_vec<T>(L.n);
+    op.base = r;
+    op.bscale = L.idinv;
+    op.out = vref(f);
+    run(op, 1, c);
+  } else {
+    for (int j = 2; j <= tL; ++j) {
+      const bool last = (j == tL);
+      auto op = op_mat(L.iL, (j == 2) ? r : cref((const T*)y[j & 1]));
+      op.base = r;
+      op.neg = 1;
+      if (last) {
+        op.scale = L.idinv;
+        op.out = vref(f);
+      } else {
+        op.out = vref(y[(j + 1) & 1]);
+      }
+      run(op, L.iL.G, c);
+    }
+  }
+  if (tU == 1) {
+    auto op = op_vec<T>(L.n);
+    op.base = cref((const T*)f);
+    if (!x_zero) op.add = cref(x);
+    op.out = x;
+    run(op, 1, c);
+    return;
+  }
+  for (int j = 2; j <= tU; ++j) {
+    const bool last = (j == tU);
+    auto op = op_mat(L.iU, (j == 2) ? cref((const T*)f) : cref((const T*)y[j & 1]));
+    op.base = cref((const T*)f);
+    op.neg = 1;
+    if (last) {
+      if (!x_zero) op.add = cref(x);
+      op.out = x;
+    } else {
+      op.out = vref(y[(j + 1) & 1]);
+    }
+    run(op, L.iU.G, c);
+  }
+}
+
+// l1-Jacobi: x <- x + D_l1^-1 (b - A x), d_ii = sum_j |a_ij|. `nsw` sweeps, ping-ponging with t1
+// so that the last sweep lands in x.
+template <typename T>
+void sweep_jacobi(Level<T>& L, VC<T> b, VRef<T> x, bool x_zero, int nsw, const Ctx& c) {
+  VRef<T> prev;
+  for (int s = 0; s < nsw; ++s) {
+    const bool to_x = ((nsw - 1 - s) % 2) == 0;
+    VRef<T> dst = to_x ? x : vref(L.t1);
+    if (s == 0 && x_zero) {
+      auto op = op_vec<T>(L.n);
+      op.base = b;
+      op.bscale = L.dl1inv;
+      op.out = dst;
+      run(op, 1, c);
+    } else {
+      VRef<T> src = (s == 0) ? x : prev;
+      if (s == 0) {
+        // first sweep with a nonzero x: cannot update in place; go through t1 then back
+        dst = to_x ? vref(L.t2) : vref(L.t1);
+      }
+      auto op = op_mat(L.A, cref(src));
+      op.base = b;
+      op.neg = 1;
+      op.scale = L.dl1inv;
+      op.add = cref(src);
+      op.out = dst;
+      run(op, L.A.G, c);
+      if (s == 0 && to_x) {  // copy t2 -> x (only when a single in-place sweep is requested)
+        auto cp = op_vec<T>(L.n);
+        cp.base = cref(dst);
+        cp.out = x;
+        run(cp, 1, c);
+        dst = x;
+      }
+    }
+    prev = dst;
+  }
+}
+
+template <typename T>
+void smooth(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, bool backward, bool x_zero, int sweeps, const Ctx& c) {
+  if (sweeps <= 0) return;
+  if (L.kind == 'j') {
+    sweep_jacobi(L, b, x, x_zero, sweeps, c);
+    return;
+  }
+  for (int s = 0; s < sweeps; ++s) {
+    const bool z = x_zero && s == 0;
+    if (L.kind == 'i') sweep_ilu(L, b, x, z, h->p.ilu_terms_L, h->p.ilu_terms_U, c);
+    else sweep_poly(L, b, x, backward, z, h->p.neumann_terms, c);
+  }
+}
+
+template <typename T>
+void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c) {
+  if (h->coarse_inv) {
+    const int nb = (L.n * 32 + kThreads - 1) / kThreads;
+    k_dense_gemv<double, T><<<nb, kThreads, 0, c.s>>>(L.n, h->coarse_inv, b, x, c.skip);
+  } else {
+    smooth(h, L, b, x, false, true, h->p.coarse_sweeps, c);
+  }
+}
+
+// One V-cycle with zero initial guess on level l (Sec. 5): pre-smooth, residual, restrict,
+// recurse, prolongate and correct, post-smooth.
+template <typename T>
+void vcycle(nsamg_handle* h, std::vector<Level<T>>& lv, int l, VC<T> b, VRef<T> x, const Ctx& c) {
+  Level<T>& L = lv[l];
+  if (l == (int)lv.size() - 1) {
+    coarse_solve(h, L, b, x, c);
+    return;
+  }
+  Level<T>& C = lv[l + 1];
+  const int pre = h->p.pre_sweeps, post = h->p.post_sweeps;
+  if (pre > 0) {
+    smooth(h, L, b, x, false, true, pre, c);
+    auto op = op_mat(L.A, cref(x));  // r = b - A x
+    op.base = b;
+    op.neg = 1;
+    op.out = vref(L.r);
+    run(op, L.A.G, c);
+    auto rs = op_mat(L.R, cref((const T*)L.r));  // b_c = R r
+    rs.out = vref(C.b);
+    run(rs, L.R.G, c);
+  } else {
+    auto rs = op_mat(L.R, b);  // x = 0: r = b
+    rs.out = vref(C.b);
+    run(rs, L.R.G, c);
+  }
+  vcycle(h, lv, l + 1, cref((const T*)C.b), vref(C.x), c);
+  {
+    auto op = op_mat(L.P, cref((const T*)C.x));  // x += P e  (x = P e when no pre-smoothing)
+    if (pre > 0) op.add = cref(x);
+    op.out = x;
+    run(op, L.P.G, c);
+  }
+  smooth(h, L, b, x, true, false, post, c);
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuning of threads-per-row for large CSR matrices (timed SpMV with each group size).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
+  if (M.n < 20000 || M.nnz == 0) return NSAMG_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cands[] = {1, 2, 4, 8, 16, 32};
+  float best = 1e30f;
+  int bestG = M.G;
+  const double avg = (double)M.nnz / M.n;
+  for (int G : cands) {
+    if (G > 2 * avg + 2) break;
+    auto op = op_mat(M, cref((const T*)x));
+    op.out = vref(y);
+    launch_row(op, G, s);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; ++r) launch_row(op, G, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bestG = G;
+    }
+  }
+  M.G = bestG;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return NSAMG_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// One Arnoldi step (Algorithm 1 steps 5-14) on the handle's stream.
+// ------------------------------------------------------------------------------------------
+void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner) {
+  const int* skip = &h->st->stop;
+  const int* sel = &h->st->i;
+  Ctx c{s, skip};
+  VRef<const double> b;
+  b.p = h->V;
+  b.sel = sel;
+  b.ld = h->ld;
+  VRef<double> z;
+  z.p = h->Z;
+  z.sel = sel;
+  z.ld = h->ld;
+  vcycle(h, h->lv, 0, b, z, c);  // z_i = M^-1 vt_i
+  {
+    auto op = op_mat(h->lv[0].A, cref(z));  // w = A z_i
+    op.out = vref(h->w);
+    run(op, h->lv[0].A.G, c);
+  }
+  GramArgs ga{};
+  ga.n = h->n;
+  ga.V = h->V;
+  ga.ldv = h->ld;
+  ga.w = h->w;
+  ga.st = h->st;
+  ga.scr = h->scr;
+  k_gram<<<h->gram_blocks, kGramThreads, 0, s>>>(ga);
+  UpdateArgs ua{};
+  ua.n = h->n;
+  ua.V = h->V;
+  ua.ldv = h->ld;
+  ua.w = h->w;
+  ua.st = h->st;
+  ua.cond_inner = cond_inner;
+  ua.scr = h->scr;
+  ua.scr.ticket = h->scr.ticket + 1;
+  k_update<<<h->update_blocks, kRedThreads, 0, s>>>(ua);
+}
+
+void enqueue_xupdate(nsamg_handle* h, cudaStream_t s) {
+  k_xupdate<double><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z, h->ld, h->st);
+}
+
+void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
+  const auto& A = h->lv[0].A;
+  ResidArgs ra{};
+  ra.n = A.n;
+  ra.rp = A.rp;
+  ra.ci = A.ci;
+  ra.v = A.v;
+  ra.r = h->V;
+  ra.st = h->st;
+  ra.init = init;
+  ra.cond_outer = co;
+  ra.cond_inner = ci;
+  ra.scr = h->scr;
+  ra.scr.ticket = h->scr.ticket + 2;
+  const int G = A.G;
+  const int nb = blocks_for((int64_t)A.n * G);
+  switch (G) {
+    case 1: k_resid<1><<<nb, kRedThreads, 0, s>>>(ra); break;
+    case 2: k_resid<2><<<nb, kRedThreads, 0, s>>>(ra); break;
+    case 4: k_resid<4><<<nb, kRedThreads, 0, s>>>(ra); break;
+    case 8: k_resid<8><<<nb, kRedThreads, 0, s>>>(ra); break;
+    case 16: k_resid<16><<<nb, kRedThreads, 0, s>>>(ra); break;
+    default: k_resid<32><<<nb, kRedThreads, 0, s>>>(ra); break;
+  }
+}
+
+int build_graph(nsamg_handle* h) {
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hout, hin;
+  CK(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
+  CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_resid(h, cs, 1, (unsigned long long)hout, 0ull);
+  CK(cudaStreamEndCapture(cs, &g));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hout;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t outer;
+  CK(cudaGraphAddNode(&outer, g, nodes.data(), nullptr, nn, &cp));
+  cudaGraph_t outer_body = cp.conditional.phGraph_out[0];
+  CK(cudaGraphConditionalHandleCreate(&hin, outer_body, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hin;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inner;
+  CK(cudaGraphAddNode(&inner, outer_body, nullptr, nullptr, 0, &ip));
+  cudaGraph_t inner_body = ip.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(h, cs, (unsigned long long)hin);
+  CK(cudaStreamEndCapture(cs, &inner_body));
+  CK(cudaStreamBeginCaptureToGraph(cs, outer_body, &inner, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  enqueue_xupdate(h, cs);
+  enqueue_resid(h, cs, 0, (unsigned long long)hout, (unsigned long long)hin);
+  CK(cudaStreamEndCapture(cs, &outer_body));
+  CK(cudaGraphInstantiate(&h->exec, g, 0));
+  h->graph = g;
+  cudaStreamDestroy(cs);
+  return NSAMG_OK;
+}
+
+int check_params(const nsamg_params& p) {
+  if (p.smoother < 0 || p.smoother > 3) return fail(NSAMG_ERR_INVALID_ARG, "unknown smoother");
+  if (p.neumann_terms < 1 || p.ilu_terms_L < 1 || p.ilu_terms_U < 1) return fail(NSAMG_ERR_INVALID_ARG, "series terms must be >= 1");
+  if (p.pre_sweeps < 0 || p.post_sweeps < 0 || p.coarse_sweeps < 1) return fail(NSAMG_ERR_INVALID_ARG, "bad sweep counts");
+  if (p.restart < 1 || p.restart > NSAMG_MAX_RESTART) return fail(NSAMG_ERR_INVALID_ARG, "restart out of range 1..64");
+  if (p.vcycle_fp32 != 0) return fail(NSAMG_ERR_INVALID_ARG, "FP32 V-cycle not available in this build");
+  if (p.spmv_group < 0 || p.spmv_group > 32 || (p.spmv_group & (p.spmv_group - 1))) return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be 0 or a power of two <= 32");
+  return NSAMG_OK;
+}
+
+int alloc_vec(double** p, int64_t n) {
+  CK(cudaMalloc(p, sizeof(double) * std::max<int64_t>(n, 1)));
+  CK(cudaMemset(*p, 0, sizeof(double) * std::max<int64_t>(n, 1)));
+  return NSAMG_OK;
+}
+
+int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stream, nsamg_handle* h) {
+  nsamg_params p;
+  nsamg_default_params(&p);
+  if (pp) p = *pp;
+  int rc = check_params(p);
+  if (rc) return rc;
+  h->p = p;
+  if (!H || H->nlevels < 1 || !H->levels) return fail(NSAMG_ERR_INVALID_ARG, "empty hierarchy");
+  CK(cudaGetDevice(&h->device));
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreate(&h->stream));  // blocking w.r.t. the legacy default stream
+    h->own_stream = true;
+  }
+  const int nl = H->nlevels;
+  for (int l = 0; l < nl; ++l) {
+    const nsamg_level_desc& D = H->levels[l];
+    std::string nm = "level " + std::to_string(l);
+    if ((rc = validate(D.A, true, true, (nm + " A").c_str()))) return rc;
+    if (l < nl - 1) {
+      if ((rc = validate(D.P, false, false, (nm + " P").c_str()))) return rc;
+      if ((rc = validate(D.R, false, false, (nm + " R").c_str()))) return rc;
+      if (D.P.nrows != D.A.nrows || D.R.ncols != D.A.nrows || D.P.ncols != H->levels[l + 1].A.nrows ||
+          D.R.nrows != H->levels[l + 1].A.nrows)
+        return fail(NSAMG_ERR_BAD_MATRIX, nm + ": P/R dimensions do not match the levels");
+    }
+    if (D.ilu_L.nrows > 0) {
+      if ((rc = validate(D.ilu_L, true, false, (nm + " ilu_L").c_str()))) return rc;
+      if ((rc = validate(D.ilu_U, true, false, (nm + " ilu_U").c_str()))) return rc;
+      if (!D.ilu_dinv || D.ilu_L.nrows != D.A.nrows || D.ilu_U.nrows != D.A.nrows)
+        return fail(NSAMG_ERR_BAD_MATRIX, nm + ": ILU factor dimensions");
+    }
+  }
+  h->lv.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const nsamg_level_desc& D = H->levels[l];
+    Level<double>& L = h->lv[l];
+    L.n = D.A.nrows;
+    if ((rc = upload(D.A, L.A))) return rc;
+    std::vector<double> dinv(L.n), dl1(L.n);
+    for (int i = 0; i < L.n; ++i) {
+      double a = 0, s1 = 0;
+      for (int q = D.A.rowptr[i]; q < D.A.rowptr[i + 1]; ++q) {
+        if (D.A.col[q] == i) a = D.A.val[q];
+        s1 += std::fabs(D.A.val[q]);
+      }
+      dinv[i] = 1.0 / a;
+      dl1[i] = 1.0 / s1;
+    }
+    if ((rc = upload_vec(dinv, &L.dinv))) return rc;
+    if ((rc = upload_vec(dl1, &L.dl1inv))) return rc;
+    if ((rc = upload(tri_part(D.A, true, &dinv, &dinv), L.L2))) return rc;
+    if ((rc = upload(tri_part(D.A, false, &dinv, &dinv), L.U2))) return rc;
+    if ((rc = upload(tri_part(D.A, true, &dinv, nullptr), L.L1))) return rc;
+    if ((rc = upload(tri_part(D.A, false, &dinv, nullptr), L.U1))) return rc;
+    if (l < nl - 1) {
+      if ((rc = upload(D.P, L.P))) return rc;
+      if ((rc = upload(D.R, L.R))) return rc;
+    }
+    const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
+    if (want_ilu && D.ilu_L.nrows > 0 && l < nl - 1) {
+      if ((rc = upload(D.ilu_L, L.iL))) return rc;
+      if ((rc = upload(D.ilu_U, L.iU))) return rc;
+      std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
+      if ((rc = upload_vec(idv, &L.idinv))) return rc;
+      L.ilu = true;
+    }
+    L.kind = (p.smoother == NSAMG_SMOOTHER_JACOBI_L1) ? 'j' : (L.ilu ? 'i' : 'p');
+    for (double** v : {&L.b, &L.x, &L.r, &L.t1, &L.t2, &L.t3})
+      if ((rc = alloc_vec(v, L.n))) return rc;
+  }
+  if (H->coarse_inv) {
+    h->nc = h->lv.back().n;
+    CK(cudaMalloc(&h->coarse_inv, sizeof(double) * (size_t)h->nc * h->nc));
+    CK(cudaMemcpy(h->coarse_inv, H->coarse_inv, sizeof(double) * (size_t)h->nc * h->nc, cudaMemcpyHostToDevice));
+  }
+  // GMRES workspace: V (m+1 columns), Z (m columns), w; leading dimension padded to 64 entries.
+  h->n = h->lv[0].n;
+  h->m = p.restart;
+  h->ld = ((int64_t)h->n + 63) / 64 * 64;
+  if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
+  if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
+  if ((rc = alloc_vec(&h->w, h->ld))) return rc;
+  CK(cudaMalloc(&h->st, sizeof(GState)));
+  CK(cudaMemset(h->st, 0, sizeof(GState)));
+  CK(cudaMallocHost(&h->h_st, sizeof(GState)));
+  int sms = 148;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->gram_blocks = 2 * sms;
+  h->update_blocks = 8 * sms;
+  const int resid_blocks = blocks_for((int64_t)h->n * 32);
+  h->partial_cap = std::max<int64_t>({(int64_t)h->gram_blocks * 2 * (kMaxM + 1), (int64_t)h->update_blocks,
+                                      2 * (int64_t)resid_blocks});
+  CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
+  CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
+  CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
+  // Threads per row: fixed by the caller or tuned on the device.
+  for (auto& L : h->lv) {
+    for (DCSR<double>* M : {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU}) {
+      if (!M->present()) continue;
+      if (p.spmv_group) {
+        M->G = p.spmv_group;
+      } else {
+        double* x = (M->m <= L.n) ? L.t1 : h->V;
+        double* y = (M->n <= L.n) ? L.t2 : h->w;
+        if (M == &L.R) { x = L.t1; y = h->w; }
+        if (M == &L.P) { x = h->V; y = L.t2; }
+        if ((rc = tune(*M, x, y, h->stream))) return rc;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  if (p.use_graph)
+    if ((rc = build_graph(h))) return rc;
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+void destroy_impl(nsamg_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (auto& L : h->lv) {
+    for (DCSR<double>* M : {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU}) release(*M);
+    for (double* v : {L.dinv, L.dl1inv, L.idinv, L.b, L.x, L.r, L.t1, L.t2, L.t3}) cudaFree(v);
+  }
+  cudaFree(h->coarse_inv);
+  cudaFree(h->V);
+  cudaFree(h->Z);
+  cudaFree(h->w);
+  cudaFree(h->st);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  cudaFree(h->scr.partials);
+  cudaFree(h->scr.ticket);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int level_ok(nsamg_handle* h, int level) {
+  if (!h) return fail(NSAMG_ERR_INVALID_ARG, "null handle");
+  if (level < 0 || level >= (int)h->lv.size()) return fail(NSAMG_ERR_INVALID_ARG, "level out of range");
+  return NSAMG_OK;
+}
+
+// Standalone scratch for nsamg_gram / nsamg_update (one per device, allocated on first use).
+std::mutex g_scr_mu;
+std::vector<Scratch> g_scr;
+
+int standalone_scratch(Scratch* out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_scr_mu);
+  if ((int)g_scr.size() <= dev) g_scr.resize(dev + 1, Scratch{nullptr, nullptr});
+  if (!g_scr[dev].partials) {
+    int sms = 148;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cap = std::max<int64_t>(2 * sms * 2 * (kMaxM + 1), 8 * sms);
+    CK(cudaMalloc(&g_scr[dev].partials, sizeof(double) * cap));
+    CK(cudaMalloc(&g_scr[dev].ticket, sizeof(unsigned) * 4));
+    CK(cudaMemset(g_scr[dev].ticket, 0, sizeof(unsigned) * 4));
+  }
+  *out = g_scr[dev];
+  return NSAMG_OK;
+}
+
+int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
+  if (!h || !d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->stream;
+  GState* hs = h->h_st;
+  hs->b = d_b;
+  hs->x = d_x;
+  hs->rtol = rtol;
+  hs->maxit = maxit;
+  hs->m = h->m;
+  hs->t_exact = h->p.t_exact;
+  CK(cudaMemcpyAsync(h->st, hs, offsetof(GState, i), cudaMemcpyHostToDevice, s));
+  if (h->exec) {
+    CK(cudaGraphLaunch(h->exec, s));
+  } else {
+    enqueue_resid(h, s, 1, 0, 0);
+    for (int cycle = 0; cycle <= maxit + 1; ++cycle) {
+      CK(cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hs->done) break;
+      for (int i = 0; i < h->m; ++i) {
+        enqueue_step(h, s, 0);
+        CK(cudaMemcpyAsync(&hs->stop, &h->st->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hs->stop) break;
+      }
+      enqueue_xupdate(h, s);
+      enqueue_resid(h, s, 0, 0, 0);
+    }
+  }
+  CK(cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  int status = hs->status;
+  if (status == 0 && !hs->converged) status = NSAMG_NOT_CONVERGED;
+  if (stats) {
+    stats->iters = hs->iters;
+    stats->restarts = std::max(0, hs->cycles - 1);
+    stats->converged = hs->converged;
+    stats->status = status;
+    stats->relres_true = hs->relres_true;
+    stats->relres_implicit = hs->relres_implicit;
+    stats->bnorm = hs->bnorm;
+  }
+  if (status < 0) return fail(status, status == NSAMG_ERR_NONFINITE ? "non-finite value in the iteration" : "solve failed");
+  return status;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+void nsamg_default_params(nsamg_params* p) {
+  if (!p) return;
+  p->smoother = NSAMG_SMOOTHER_POLY_GS;
+  p->neumann_terms = 2;
+  p->ilu_terms_L = 3;
+  p->ilu_terms_U = 3;
+  p->pre_sweeps = 1;
+  p->post_sweeps = 1;
+  p->coarse_sweeps = 4;
+  p->restart = 30;
+  p->vcycle_fp32 = 0;
+  p->t_exact = 0;
+  p->use_graph = 1;
+  p->spmv_group = 0;
+}
+
+int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, void* cuda_stream, nsamg_handle** out) {
+  if (!out) return fail(NSAMG_ERR_INVALID_ARG, "null output handle pointer");
+  *out = nullptr;
+  nsamg_handle* h = new nsamg_handle();
+  const int rc = setup_impl(H, p, cuda_stream, h);
+  if (rc != NSAMG_OK) {
+    std::string keep = g_err;
+    destroy_impl(h);
+    g_err = keep;
+    return rc;
+  }
+  *out = h;
+  return NSAMG_OK;
+}
+
+int nsamg_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* st) {
+  return solve_impl(h, d_b, d_x, rtol, maxit, st);
+}
+
+int nsamg_solve_host(nsamg_handle* h, const double* h_b, double* h_x, double rtol, int maxit, nsamg_stats* st) {
+  if (!h || !h_b || !h_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  CK(cudaSetDevice(h->device));
+  const size_t bytes = sizeof(double) * h->n;
+  double *db = nullptr, *dx = nullptr;
+  CK(cudaMallocAsync(&db, bytes, h->stream));
+  CK(cudaMallocAsync(&dx, bytes, h->stream));
+  CK(cudaMemcpyAsync(db, h_b, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(dx, h_x, bytes, cudaMemcpyHostToDevice, h->stream));
+  int rc = solve_impl(h, db, dx, rtol, maxit, st);
+  if (rc >= 0) {
+    CK(cudaMemcpyAsync(h_x, dx, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  cudaFreeAsync(db, h->stream);
+  cudaFreeAsync(dx, h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int nsamg_apply_vcycle(nsamg_handle* h, const double* d_r, double* d_z) {
+  if (!h || !d_r || !d_z) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  CK(cudaSetDevice(h->device));
+  Ctx c{h->stream, nullptr};
+  vcycle(h, h->lv, 0, cref(d_r), vref(d_z), c);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_num_levels(nsamg_handle* h) { return h ? (int)h->lv.size() : fail(NSAMG_ERR_INVALID_ARG, "null handle"); }
+
+int nsamg_level_size(nsamg_handle* h, int level) {
+  int rc = level_ok(h, level);
+  return rc ? rc : h->lv[level].n;
+}
+
+int nsamg_level_group(nsamg_handle* h, int level) {
+  int rc = level_ok(h, level);
+  return rc ? rc : h->lv[level].A.G;
+}
+
+int nsamg_level_spmv(nsamg_handle* h, int level, const double* d_x, double* d_y) {
+  int rc = level_ok(h, level);
+  if (rc) return rc;
+  if (!d_x || !d_y) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
+  CK(cudaSetDevice(h->device));
+  auto& L = h->lv[level];
+  auto op = op_mat(L.A, cref(d_x));
+  op.out = vref(d_y);
+  launch_row(op, L.A.G, h->stream);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_level_residual(nsamg_handle* h, int level, const double* d_b, const double* d_x, double* d_r) {
+  int rc = level_ok(h, level);
+  if (rc) return rc;
+  if (!d_b || !d_x || !d_r) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
+  CK(cudaSetDevice(h->device));
+  auto& L = h->lv[level];
+  auto op = op_mat(L.A, cref(d_x));
+  op.base = cref(d_b);
+  op.neg = 1;
+  op.out = vref(d_r);
+  launch_row(op, L.A.G, h->stream);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_level_smooth(nsamg_handle* h, int level, int backward, int x_is_zero, const double* d_b, double* d_x) {
+  int rc = level_ok(h, level);
+  if (rc) return rc;
+  if (!d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
+  CK(cudaSetDevice(h->device));
+  Ctx c{h->stream, nullptr};
+  smooth(h, h->lv[level], cref(d_b), vref(d_x), backward != 0, x_is_zero != 0, 1, c);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_level_restrict(nsamg_handle* h, int level, const double* d_r, double* d_y) {
+  int rc = level_ok(h, level);
+  if (rc) return rc;
+  if (level >= (int)h->lv.size() - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no restriction");
+  CK(cudaSetDevice(h->device));
+  auto& L = h->lv[level];
+  auto op = op_mat(L.R, cref(d_r));
+  op.out = vref(d_y);
+  launch_row(op, L.R.G, h->stream);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_level_prolong(nsamg_handle* h, int level, const double* d_e, double* d_x) {
+  int rc = level_ok(h, level);
+  if (rc) return rc;
+  if (level >= (int)h->lv.size() - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no prolongation");
+  CK(cudaSetDevice(h->device));
+  auto& L = h->lv[level];
+  auto op = op_mat(L.P, cref(d_e));
+  op.add = cref((const double*)d_x);
+  op.out = vref(d_x);
+  launch_row(op, L.P.G, h->stream);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_coarse_solve(nsamg_handle* h, const double* d_b, double* d_z) {
+  if (!h || !d_b || !d_z) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  CK(cudaSetDevice(h->device));
+  Ctx c{h->stream, nullptr};
+  coarse_solve(h, h->lv.back(), cref(d_b), vref(d_z), c);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream) {
+  if (n <= 0 || i < 0 || i >= kMaxM || !d_V || !d_w || !d_out || ldv < n) return fail(NSAMG_ERR_INVALID_ARG, "bad gram arguments");
+  Scratch scr;
+  int rc = standalone_scratch(&scr);
+  if (rc) return rc;
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GramArgs ga{};
+  ga.n = n;
+  ga.V = d_V;
+  ga.ldv = ldv;
+  ga.w = d_w;
+  ga.st = nullptr;
+  ga.i_standalone = i;
+  ga.out = d_out;
+  ga.scr = scr;
+  k_gram<<<2 * sms, kGramThreads, 0, (cudaStream_t)stream>>>(ga);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
+                 double* d_sumsq, void* stream) {
+  if (n <= 0 || i < 0 || i >= kMaxM || !d_V || !d_w || !d_h || !d_sumsq || ldv < n || !(beta != 0.0))
+    return fail(NSAMG_ERR_INVALID_ARG, "bad update arguments");
+  Scratch scr;
+  int rc = standalone_scratch(&scr);
+  if (rc) return rc;
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  UpdateArgs ua{};
+  ua.n = n;
+  ua.V = d_V;
+  ua.ldv = ldv;
+  ua.w = d_w;
+  ua.st = nullptr;
+  ua.i_standalone = i;
+  ua.invbeta_standalone = 1.0 / beta;
+  ua.h_standalone = d_h;
+  ua.sumsq_out = d_sumsq;
+  ua.scr = scr;
+  ua.scr.ticket = scr.ticket + 1;
+  k_update<<<8 * sms, kRedThreads, 0, (cudaStream_t)stream>>>(ua);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+void nsamg_destroy(nsamg_handle* h) { destroy_impl(h); }
+
+const char* nsamg_status_str(int s) {
+  switch (s) {
+    case NSAMG_OK: return "ok";
+    case NSAMG_NOT_CONVERGED: return "not converged";
+    case NSAMG_PENDING: return "pending";
+    case NSAMG_ERR_INVALID_ARG: return "invalid argument";
+    case NSAMG_ERR_BAD_MATRIX: return "bad matrix";
+    case NSAMG_ERR_OOM: return "out of device memory";
+    case NSAMG_ERR_CUDA: return "CUDA error";
+    case NSAMG_ERR_TIMEOUT: return "device wait timed out";
+    case NSAMG_ERR_NONFINITE: return "non-finite value";
+    case NSAMG_ERR_ADMISSION: return "admission rejected";
+    default: return "unknown status";
+  }
+}
+
+const char* nsamg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+"""ctypes binding of libnsamg.so (argument marshalling only).
+
+Names follow the C ABI without the `nsamg_` prefix. Device vectors are torch CUDA float64
+tensors (contiguous); host matrices are scipy.sparse CSR matrices (float64, int32 indices,
+sorted columns). Errors raise NsamgError with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnsamg.so")
+
+OK, NOT_CONVERGED, PENDING = 0, 1, 2
+POLY_GS, JACOBI_L1, ILU0, HYBRID_ILU0 = 0, 1, 2, 3
+MAX_RESTART = 64
+
+
+class NsamgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"nsamg status {status}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("A", Csr), ("P", Csr), ("R", Csr), ("ilu_L", Csr), ("ilu_U", Csr), ("ilu_dinv", ctypes.c_void_p)]
+
+
+class HierarchyDesc(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int32), ("levels", ctypes.POINTER(LevelDesc)), ("coarse_inv", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("smoother", "neumann_terms", "ilu_terms_L", "ilu_terms_U", "pre_sweeps",
+                                               "post_sweeps", "coarse_sweeps", "restart", "vcycle_fp32", "t_exact",
+                                               "use_graph", "spmv_group")]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("relres_true", ctypes.c_double), ("relres_implicit", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = [
+    "nsamg_default_params", "nsamg_setup_hierarchy", "nsamg_solve", "nsamg_solve_host", "nsamg_apply_vcycle",
+    "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
+    "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
+    "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error",
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libnsamg.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2112_14681_b300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "nsamg_default_params": (None, [ctypes.POINTER(Params)]),
+        "nsamg_setup_hierarchy": (i32, [ctypes.POINTER(HierarchyDesc), ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "nsamg_solve": (i32, [vp, vp, vp, f64, i32, ctypes.POINTER(Stats)]),
+        "nsamg_solve_host": (i32, [vp, vp, vp, f64, i32, ctypes.POINTER(Stats)]),
+        "nsamg_apply_vcycle": (i32, [vp, vp, vp]),
+        "nsamg_num_levels": (i32, [vp]),
+        "nsamg_level_size": (i32, [vp, i32]),
+        "nsamg_level_group": (i32, [vp, i32]),
+        "nsamg_level_spmv": (i32, [vp, i32, vp, vp]),
+        "nsamg_level_residual": (i32, [vp, i32, vp, vp, vp]),
+        "nsamg_level_smooth": (i32, [vp, i32, i32, i32, vp, vp]),
+        "nsamg_level_restrict": (i32, [vp, i32, vp, vp]),
+        "nsamg_level_prolong": (i32, [vp, i32, vp, vp]),
+        "nsamg_coarse_solve": (i32, [vp, vp, vp]),
+        "nsamg_gram": (i32, [i64, i32, vp, i64, vp, vp, vp]),
+        "nsamg_update": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
+        "nsamg_destroy": (None, [vp]),
+        "nsamg_status_str": (ctypes.c_char_p, [i32]),
+        "nsamg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, allow=(OK,)) -> int:
+    if rc in allow:
+        return rc
+    lib = load()
+    raise NsamgError(rc, lib.nsamg_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous torch CUDA tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().nsamg_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, int(v))
+    return p
+
+
+def _csr_desc(M, keep: list) -> Csr:
+    c = Csr()
+    if M is None:
+        return c
+    M = M.tocsr()
+    rp = np.ascontiguousarray(M.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(M.indices, dtype=np.int32)
+    v = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep += [rp, ci, v]
+    c.nrows, c.ncols, c.nnz = M.shape[0], M.shape[1], M.nnz
+    c.rowptr, c.col, c.val = rp.ctypes.data, ci.ctypes.data, v.ctypes.data
+    return c
+
+
+class Handle:
+    """Owns an nsamg handle (device hierarchy + GMRES workspace)."""
+
+    def __init__(self, hierarchy, params: Params | None = None, stream=None):
+        lib = load()
+        keep: list = []
+        levels = hierarchy.levels
+        arr = (LevelDesc * len(levels))()
+        for l, lev in enumerate(levels):
+            arr[l].A = _csr_desc(lev.A, keep)
+            arr[l].P = _csr_desc(lev.P, keep)
+            arr[l].R = _csr_desc(lev.R, keep)
+            arr[l].ilu_L = _csr_desc(lev.ilu_L, keep)
+            arr[l].ilu_U = _csr_desc(lev.ilu_U, keep)
+            if lev.ilu_dinv is not None:
+                d = np.ascontiguousarray(lev.ilu_dinv, dtype=np.float64)
+                keep.append(d)
+                arr[l].ilu_dinv = d.ctypes.data
+        desc = HierarchyDesc()
+        desc.nlevels = len(levels)
+        desc.levels = arr
+        if hierarchy.coarse_inv is not None:
+            ci = np.ascontiguousarray(hierarchy.coarse_inv, dtype=np.float64)
+            keep.append(ci)
+            desc.coarse_inv = ci.ctypes.data
+        self.params = params or default_params()
+        h = ctypes.c_void_p()
+        sptr = None if stream is None else ctypes.c_void_p(stream)
+        _check(lib.nsamg_setup_hierarchy(ctypes.byref(desc), ctypes.byref(self.params), sptr, ctypes.byref(h)))
+        self._h = h
+        self.n = levels[0].A.shape[0]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().nsamg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def setup_hierarchy(hierarchy, params: Params | None = None, stream=None) -> Handle:
+    return Handle(hierarchy, params, stream)
+
+
+def solve(h: Handle, b, x, rtol: float = 1e-8, maxit: int = 1000) -> dict:
+    st = Stats()
+    rc = load().nsamg_solve(h._h, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(st))
+    _check(rc, (OK, NOT_CONVERGED))
+    return st.as_dict()
+
+
+def solve_host(h: Handle, b: np.ndarray, x: np.ndarray, rtol: float = 1e-8, maxit: int = 1000) -> dict:
+    """b, x: host float64 arrays (pinned torch CPU tensors or numpy); x is updated in place."""
+    st = Stats()
+
+    def hptr(a):
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+            return a.ctypes.data
+        return a.data_ptr()
+    rc = load().nsamg_solve_host(h._h, hptr(b), hptr(x), float(rtol), int(maxit), ctypes.byref(st))
+    _check(rc, (OK, NOT_CONVERGED))
+    return st.as_dict()
+
+
+def apply_vcycle(h: Handle, r, z) -> None:
+    _check(load().nsamg_apply_vcycle(h._h, _ptr(r), _ptr(z)))
+
+
+def num_levels(h: Handle) -> int:
+    return _check(load().nsamg_num_levels(h._h), allow=range(0, 1 << 30))
+
+
+def level_size(h: Handle, level: int) -> int:
+    return _check(load().nsamg_level_size(h._h, level), allow=range(0, 1 << 31))
+
+
+def level_group(h: Handle, level: int) -> int:
+    return _check(load().nsamg_level_group(h._h, level), allow=range(1, 33))
+
+
+def level_spmv(h: Handle, level: int, x, y) -> None:
+    _check(load().nsamg_level_spmv(h._h, level, _ptr(x), _ptr(y)))
+
+
+def level_residual(h: Handle, level: int, b, x, r) -> None:
+    _check(load().nsamg_level_residual(h._h, level, _ptr(b), _ptr(x), _ptr(r)))
+
+
+def level_smooth(h: Handle, level: int, b, x, backward: bool = False, x_is_zero: bool = False) -> None:
+    _check(load().nsamg_level_smooth(h._h, level, int(backward), int(x_is_zero), _ptr(b), _ptr(x)))
+
+
+def level_restrict(h: Handle, level: int, r, y) -> None:
+    _check(load().nsamg_level_restrict(h._h, level, _ptr(r), _ptr(y)))
+
+
+def level_prolong(h: Handle, level: int, e, x) -> None:
+    _check(load().nsamg_level_prolong(h._h, level, _ptr(e), _ptr(x)))
+
+
+def coarse_solve(h: Handle, b, z) -> None:
+    _check(load().nsamg_coarse_solve(h._h, _ptr(b), _ptr(z)))
+
+
+def gram(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
+    _check(load().nsamg_gram(int(n), int(i), _ptr(V), int(ldv), _ptr(w), _ptr(out), stream))
+
+
+def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
+    _check(load().nsamg_update(int(n), int(i), _ptr(V), int(ldv), _ptr(w), float(beta), _ptr(h), _ptr(sumsq), stream))
+
+
+def status_str(s: int) -> str:
+    return load().nsamg_status_str(int(s)).decode()

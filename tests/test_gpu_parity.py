@@ -1,0 +1,292 @@
+"""GPU parity: every kernel of the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs. Tolerances: per-kernel FP64 results within 1e-12 relative
+(componentwise against |A||x| for products, norm-wise for multi-pass sweeps); solves reach
+relative residual 1e-8 with iteration counts within +-1 of the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle.kernels as K
+from oracle.gmres import gmres_mgs, gmres_onereduce
+from oracle.vcycle import vcycle as ovcycle, level_smoother
+from workloads import build_hierarchy, poisson2d_5pt, pressure3d_7pt, rhs_uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2112_14681_b300 import nsamg  # noqa: E402
+
+TOL = 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def params_for(smoother, **kw):
+    d = dict(smoother=smoother)
+    if smoother == K.JACOBI_L1:
+        d.update(pre_sweeps=2, post_sweeps=2)
+    d.update(kw)
+    return d
+
+
+def oracle_params(p: nsamg.Params):
+    return K.SmootherParams(smoother=p.smoother, neumann_terms=p.neumann_terms, ilu_terms_L=p.ilu_terms_L,
+                            ilu_terms_U=p.ilu_terms_U, pre_sweeps=p.pre_sweeps, post_sweeps=p.post_sweeps,
+                            coarse_sweeps=p.coarse_sweeps)
+
+
+CASES = {
+    # C1: 2D 5-point 32x32, 3 levels
+    "c1": lambda: (poisson2d_5pt(32), dict(max_levels=3, coarse_max=64)),
+    # ragged 3D variable-coefficient case: 23^3 = 12167 rows (not a multiple of any tile)
+    "p23": lambda: (pressure3d_7pt(23, seed=3), dict(coarse_max=100)),
+    # deeper hierarchy with a coarsest level solved by sweeps (no dense inverse)
+    "p20s": lambda: (pressure3d_7pt(20, seed=5), dict(coarse_max=600, direct_max=0)),
+}
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        A, kw = CASES[name]()
+        H = build_hierarchy(A, ilu_levels=None, **kw)
+        _cache[name] = (A, H)
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    nsamg.load()
+    yield
+
+
+def rel_err_componentwise(y, yo, bound):
+    return float(np.max(np.abs(y - yo) / np.maximum(bound, 1e-300)))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_level_spmv_residual_transfer(name):
+    A, H = case(name)
+    with nsamg.setup_hierarchy(H, nsamg.default_params()) as h:
+        assert nsamg.num_levels(h) == H.nlevels
+        rng = np.random.default_rng(1)
+        for l, lev in enumerate(H.levels):
+            n = lev.n
+            x, b = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+            bound = abs(lev.A) @ np.abs(x)
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            nsamg.level_spmv(h, l, dev(x), y)
+            assert rel_err_componentwise(host(y), K.spmv(lev.A, x), bound) <= TOL
+            r = torch.empty_like(y)
+            nsamg.level_residual(h, l, dev(b), dev(x), r)
+            assert rel_err_componentwise(host(r), K.residual(lev.A, b, x), bound + np.abs(b)) <= TOL
+            if l < H.nlevels - 1:
+                nc = lev.R.shape[0]
+                yc = torch.empty(nc, dtype=torch.float64, device="cuda")
+                nsamg.level_restrict(h, l, dev(x), yc)
+                assert rel_err_componentwise(host(yc), K.restrict(lev.R, x), abs(lev.R) @ np.abs(x)) <= TOL
+                e = rng.uniform(-1, 1, nc)
+                xt = dev(x)
+                nsamg.level_prolong(h, l, dev(e), xt)
+                assert rel_err_componentwise(host(xt), K.prolong(lev.P, x, e), np.abs(x) + abs(lev.P) @ np.abs(e)) <= TOL
+
+
+SMOOTHERS = [(K.POLY_GS, 2), (K.POLY_GS, 1), (K.POLY_GS, 4), (K.ILU0, 3), (K.HYBRID_ILU0, 3), (K.JACOBI_L1, 1)]
+
+
+@pytest.mark.parametrize("smoother,terms", SMOOTHERS)
+@pytest.mark.parametrize("backward", [False, True])
+@pytest.mark.parametrize("x_zero", [True, False])
+def test_smoother_sweep(smoother, terms, backward, x_zero):
+    A, H = case("p23")
+    kw = dict(smoother=smoother, neumann_terms=terms, ilu_terms_L=terms, ilu_terms_U=max(1, terms - 1))
+    p = nsamg.default_params(**kw)
+    op = oracle_params(p)
+    with nsamg.setup_hierarchy(H, p) as h:
+        rng = np.random.default_rng(7)
+        for l in range(H.nlevels - 1):
+            lev = H.levels[l]
+            b = rng.uniform(-1, 1, lev.n)
+            x0 = np.zeros(lev.n) if x_zero else rng.uniform(-1, 1, lev.n)
+            xt = dev(x0)
+            nsamg.level_smooth(h, l, dev(b), xt, backward=backward, x_is_zero=x_zero)
+            kind = level_smoother(H, l, op)
+            if kind == "ilu":
+                want = K.ilu0_sweep(lev.ilu_L, lev.ilu_U, lev.ilu_dinv, lev.A, b, x0, op.ilu_terms_L, op.ilu_terms_U)
+            elif kind == "jacobi":
+                want = K.l1_jacobi_sweep(lev.A, b, x0)
+            else:
+                want = K.poly_gs_sweep(lev.A, b, x0, op.neumann_terms, backward=backward)
+            got = host(xt)
+            assert np.max(np.abs(got - want)) <= TOL * max(1.0, np.max(np.abs(want))), (l, kind)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve(name):
+    A, H = case(name)
+    p = nsamg.default_params()
+    with nsamg.setup_hierarchy(H, p) as h:
+        lev = H.levels[-1]
+        b = np.random.default_rng(3).uniform(-1, 1, lev.n)
+        z = torch.empty(lev.n, dtype=torch.float64, device="cuda")
+        nsamg.coarse_solve(h, dev(b), z)
+        if H.coarse_inv is not None:
+            want = K.coarse_direct(lev.A, b)
+            kappa = np.linalg.cond(lev.A.toarray())
+            assert np.max(np.abs(host(z) - want)) <= 1e-14 * kappa * np.max(np.abs(want)) + TOL
+        else:
+            x = np.zeros(lev.n)
+            for _ in range(p.coarse_sweeps):
+                x = K.poly_gs_sweep(lev.A, b, x, p.neumann_terms, backward=False)
+            assert np.max(np.abs(host(z) - x)) <= TOL * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.ILU0, K.JACOBI_L1])
+def test_vcycle(name, smoother):
+    A, H = case(name)
+    p = nsamg.default_params(**params_for(smoother))
+    with nsamg.setup_hierarchy(H, p) as h:
+        r = rhs_uniform(A.shape[0], 11)
+        z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h, dev(r), z)
+        want = ovcycle(H, r, oracle_params(p))
+        got = host(z)
+        assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("n,i", [(1, 0), (1000, 0), (4097, 3), (100003, 17), (262144, 63)])
+def test_gram_and_update(n, i):
+    rng = np.random.default_rng(n + i)
+    ld = n + (7 if n > 1 else 0)
+    Vb = np.zeros((i + 2, ld))
+    Q, _ = np.linalg.qr(rng.standard_normal((n, i + 1))) if n >= i + 1 else (rng.standard_normal((n, i + 1)), None)
+    Vb[: i + 1, :n] = Q.T[: i + 1]
+    Vb[i, :n] = rng.standard_normal(n) * 3.0  # unnormalised newest vector
+    w = rng.standard_normal(n)
+    Vt = dev(Vb.ravel())
+    out = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
+    nsamg.gram(n, i, Vt, ld, dev(w), out)
+    a, s = K.gram(Vb[:i, :n].T, Vb[i, :n], w)
+    got = host(out)
+    scale_a = np.sqrt(np.sum(Vb[: i + 1, :n] ** 2, axis=1)) * np.linalg.norm(Vb[i, :n])
+    scale_s = np.sqrt(np.sum(Vb[: i + 1, :n] ** 2, axis=1)) * np.linalg.norm(w)
+    assert np.all(np.abs(got[: i + 1] - a) <= TOL * scale_a)
+    assert np.all(np.abs(got[i + 1:] - s) <= TOL * scale_s)
+    beta = float(np.sqrt(a[i]))
+    hcoef = rng.standard_normal(i + 1)
+    ss = torch.empty(1, dtype=torch.float64, device="cuda")
+    nsamg.update(n, i, Vt, ld, dev(w), beta, dev(hcoef), ss)
+    v_o, nxt_o = K.update(Vb[:i, :n].T, Vb[i, :n], w, beta, hcoef)
+    Vg = host(Vt).reshape(i + 2, ld)
+    assert np.max(np.abs(Vg[i, :n] - v_o)) <= TOL * np.max(np.abs(v_o))
+    bound = np.abs(w) / beta + np.abs(Vb[:i, :n].T) @ np.abs(hcoef[:i]) + np.abs(v_o) * abs(hcoef[i])
+    assert np.max(np.abs(Vg[i + 1, :n] - nxt_o) / bound) <= TOL
+    assert abs(host(ss)[0] - np.dot(nxt_o, nxt_o)) <= TOL * np.dot(bound, bound)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.JACOBI_L1])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_solve_matches_oracle(name, smoother, graph):
+    A, H = case(name)
+    m = 30
+    p = nsamg.default_params(**params_for(smoother), restart=m, use_graph=graph)
+    op = oracle_params(p)
+    b = rhs_uniform(A.shape[0], 0)
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=m, rtol=1e-8)
+    ref_mgs = gmres_mgs(A, b, lambda v: ovcycle(H, v, op), m=m, rtol=1e-8)
+    with nsamg.setup_hierarchy(H, p) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        xs = host(x)
+    true = np.linalg.norm(b - A @ xs) / np.linalg.norm(b)
+    assert st["converged"] == 1 and st["status"] == 0
+    assert true <= 1e-8 and abs(true - st["relres_true"]) <= 1e-12
+    assert abs(st["iters"] - ref.iters) <= 1 and abs(st["iters"] - ref_mgs.iters) <= 1
+    assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+
+
+def test_solve_restarts_and_texact():
+    A, H = case("c1")
+    b = rhs_uniform(A.shape[0], 4)
+    for t_exact in (0, 1):
+        p = nsamg.default_params(restart=4, t_exact=t_exact)
+        op = oracle_params(p)
+        ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=4, rtol=1e-9,
+                              T_mode="exact" if t_exact else "trunc")
+        with nsamg.setup_hierarchy(H, p) as h:
+            x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            st = nsamg.solve(h, dev(b), x, rtol=1e-9, maxit=500)
+        assert st["converged"] and st["restarts"] >= 1
+        assert abs(st["iters"] - ref.iters) <= 1
+        assert np.linalg.norm(host(x) - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+
+
+def test_solve_edge_cases():
+    A, H = case("p23")
+    n = A.shape[0]
+    b = rhs_uniform(n, 2)
+    with nsamg.setup_hierarchy(H, nsamg.default_params()) as h:
+        # maxit = 0: no iteration, NOT_CONVERGED, x unchanged
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=0)
+        assert st["status"] == nsamg.NOT_CONVERGED and st["iters"] == 0 and float(x.abs().max()) == 0.0
+        # starting from the solution: zero iterations
+        xs = np.linalg.solve(A.toarray(), b)
+        x = dev(xs)
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=100)
+        assert st["converged"] and st["iters"] == 0
+        # b = 0 with x0 = 0: converged at once, x stays 0
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, torch.zeros(n, dtype=torch.float64, device="cuda"), x, rtol=1e-8, maxit=100)
+        assert st["converged"] and st["iters"] == 0
+        # NaN in b: reported, not hidden
+        bn = b.copy()
+        bn[5] = np.nan
+        with pytest.raises(nsamg.NsamgError) as ei:
+            nsamg.solve(h, dev(bn), torch.zeros(n, dtype=torch.float64, device="cuda"), rtol=1e-8, maxit=100)
+        assert ei.value.status == -6
+        # the handle still works afterwards
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        assert st["converged"]
+        # host-buffer entry point gives the same x
+        xh = np.zeros(n)
+        st2 = nsamg.solve_host(h, b, xh, rtol=1e-8, maxit=500)
+        assert st2["iters"] == st["iters"] and np.array_equal(xh, host(x))
+
+
+def test_solve_is_deterministic():
+    A, H = case("p23")
+    b = rhs_uniform(A.shape[0], 9)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(smoother=K.HYBRID_ILU0)) as h:
+        xs = []
+        for _ in range(2):
+            x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            nsamg.solve(h, dev(b), x, rtol=1e-10, maxit=500)
+            xs.append(host(x))
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_setup_rejects_bad_input():
+    A, H = case("c1")
+    import copy
+    bad = copy.deepcopy(H)
+    Ab = bad.levels[0].A.copy()
+    Ab.indices[3] = 10_000_000  # column out of range
+    bad.levels[0].A = Ab
+    with pytest.raises(nsamg.NsamgError) as ei:
+        nsamg.setup_hierarchy(bad, nsamg.default_params())
+    assert ei.value.status == -2
+    with pytest.raises(nsamg.NsamgError) as ei:
+        nsamg.setup_hierarchy(H, nsamg.default_params(restart=65))
+    assert ei.value.status == -1
