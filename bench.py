@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark: GMRES(50) + one C-AMG V-cycle per step, solved to relative residual 1e-8 on the
+128^3 variable-coefficient 7-point pressure Poisson system (2,097,152 rows, 14,581,760 nnz,
+FP64), smoother = hybrid ILU(0) (3 + 3 Neumann terms) on the finest level with 2-term
+polynomial Gauss-Seidel below; the polynomial GS and l1-Jacobi smoothers are timed beside it.
+
+One step = one complete solve from x0 = 0 (all hot-path kernels: V-cycle smoothers and
+transfers, outer SpMV, fused Gram + T = I - L projection, basis update + Givens, x-update,
+true residual). Inputs are resident in HBM before the timed region; the working set
+(hierarchy ~0.7 GB + Krylov basis ~0.9 GB) is larger than the 126 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {nsamg,reference}]
+
+Under torchrun each rank solves its own copy on its own GPU (replicas; no data-path collective);
+value = total solves / max-over-ranks time. `--impl reference` times the FP64 CPU oracle on the
+host cores on the same workload (bounded sample per step) and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+# The CPU oracle legs are timed single-threaded: pin BLAS to one thread before numpy loads.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EDGE = 128
+RESTART = 50
+RTOL = 1e-8
+MAXIT = 500
+SEED = 0
+N_RHS = 4
+WORKLOAD = "pressure3d_7pt_128^3_sigma1_gmres50_rtol1e-8_fp64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def build_inputs():
+    from workloads import build_hierarchy, pressure3d_7pt, rhs_uniform
+    A = pressure3d_7pt(EDGE, sigma=1.0, seed=SEED)
+    H = build_hierarchy(A, theta=0.25, coarse_max=512, seed=SEED, ilu_levels=(0,))
+    rhs = [rhs_uniform(A.shape[0], SEED + k) for k in range(N_RHS)]
+    return A, H, rhs
+
+
+SMOOTHERS = {
+    "hybrid_ilu0": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
+    "poly_gs": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
+    "l1_jacobi": dict(smoother=1, pre_sweeps=2, post_sweeps=2),
+}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def spmv_bytes(A) -> int:
+    n, nnz = A.shape[0], A.nnz
+    return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
+
+
+def time_kernels(nsamg, torch, h, A, H, stream, reps=20):
+    """CUDA-event timing (on the library's stream) of single kernels of the level-0 operator."""
+    n = A.shape[0]
+    x = torch.rand(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    t = timed(lambda: nsamg.level_spmv(h, 0, x, y))
+    out["spmv_l0"] = {"s": t, "bytes": spmv_bytes(A), "GBps": spmv_bytes(A) / t / 1e9}
+    # ILU pass on the finest level: y_{j+1} = r - L_s y_j (strict lower factor)
+    Ls = H.levels[0].ilu_L
+    if Ls is not None:
+        b_ilu = 12 * Ls.nnz + 4 * (n + 1) + 8 * n * 3
+        tl = timed(lambda: nsamg.level_smooth(h, 0, x, y, backward=False, x_is_zero=True))
+        out["ilu_sweep_x0_l0"] = {"s": tl, "bytes": 2 * (12 * Ls.nnz + 4 * (n + 1)) + 2 * (12 * H.levels[0].ilu_U.nnz + 4 * (n + 1)) + 8 * n * 10,
+                                  "note": "4 triangular passes (2 L_s, 2 U_s) from a zero guess"}
+        out["ilu_sweep_x0_l0"]["GBps"] = out["ilu_sweep_x0_l0"]["bytes"] / tl / 1e9
+        del b_ilu
+    # one-reduce Gram at step i = 10 and basis update over n rows
+    i = 10
+    ld = (n + 63) // 64 * 64
+    V = torch.rand((i + 2) * ld, dtype=torch.float64, device="cuda")
+    w = torch.rand(n, dtype=torch.float64, device="cuda")
+    o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
+    hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
+    ss = torch.empty(1, dtype=torch.float64, device="cuda")
+    sp = stream.cuda_stream
+    tg = timed(lambda: nsamg.gram(n, i, V, ld, w, o, sp))
+    out["gram_i10"] = {"s": tg, "bytes": 8 * (i + 2) * n, "GBps": 8 * (i + 2) * n / tg / 1e9,
+                       "dfma": 2 * (i + 1) * n}
+    tu = timed(lambda: nsamg.update(n, i, V, ld, w, 1.0, hc, ss, sp))
+    out["update_i10"] = {"s": tu, "bytes": 8 * (i + 4) * n, "GBps": 8 * (i + 4) * n / tu / 1e9,
+                         "dfma": (i + 2) * n}
+    return out
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2112_14681_b300 import nsamg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    nsamg.load()
+    A, H, rhs = build_inputs()
+    n = A.shape[0]
+    stream = torch.cuda.Stream()
+    d_rhs = [torch.from_numpy(b).cuda() for b in rhs]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    results = {}
+    handles = {}
+    for name, kw in SMOOTHERS.items():
+        p = nsamg.default_params(restart=RESTART, **kw)
+        handles[name] = nsamg.setup_hierarchy(H, p, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    main = "hybrid_ilu0"
+    for name, h in handles.items():
+        stats = []
+        for wi in range(args.warmup):
+            with torch.cuda.stream(stream):
+                x.zero_()
+            stats.append(nsamg.solve(h, d_rhs[wi % N_RHS], x, RTOL, MAXIT))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        K = args.steps if name == main else max(3, args.steps // 5)
+        launches = 0
+        barrier()
+        sampler = ClockSampler(local)
+        with sampler:
+            e0.record(stream)
+            for k in range(K):
+                with torch.cuda.stream(stream):
+                    x.zero_()
+                st = nsamg.solve(h, d_rhs[k % N_RHS], x, RTOL, MAXIT)
+                stats.append(st)
+                launches += nsamg.solve_launches(h, st)
+            e1.record(stream)
+            e1.synchronize()
+        barrier()
+        dt = e0.elapsed_time(e1) * 1e-3
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        relres = max(s["relres_true"] for s in stats[-K:])
+        results[name] = {"solves": K, "time_s": dt, "solves_per_s": world * K / dt, "s_per_solve": dt / K,
+                         "iters": [s["iters"] for s in stats[-K:]][:4], "max_relres_true": relres,
+                         "all_converged": all(s["converged"] == 1 for s in stats), "launches": launches,
+                         "launches_per_step": nsamg.launches_per_step(h), "clocks": sampler.summary()}
+    # end-to-end through the host-buffer entry point (copies inside the timed region)
+    h = handles[main]
+    hb = [torch.from_numpy(b).pin_memory() for b in rhs]
+    hx = torch.zeros(n, dtype=torch.float64).pin_memory()
+    for wi in range(2):
+        hx.zero_()
+        nsamg.solve_host(h, hb[wi % N_RHS], hx, RTOL, MAXIT)
+    Ke = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(Ke):
+        hx.zero_()
+        nsamg.solve_host(h, hb[k % N_RHS], hx, RTOL, MAXIT)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    kern = time_kernels(nsamg, torch, h, A, H, stream) if rank == 0 else {}
+    for hh in handles.values():
+        hh.close()
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        main_r = results[main]
+        sp = kern["spmv_l0"]
+        line = {
+            "metric": "solves/s to rel-res 1e-8 (GMRES(50)+C-AMG, 128^3 pressure Poisson)",
+            "value": main_r["solves_per_s"],
+            "unit": "solves/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": main_r["s_per_solve"] * 1e3,
+            "time_to_rel_res_1e-8_s": main_r["s_per_solve"],
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic (seeded lognormal-density 7-point FV pressure Poisson, b ~ U[-1,1])",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": int(A.nnz), "levels": H.info["n"],
+                       "operator_complexity": round(H.info["operator_complexity"], 3), "smoother": main,
+                       "restart": RESTART, "rtol": RTOL, "l2_flush": "none: working set > L2 (126 MB)",
+                       "parallelism": f"replicas x{world}", "iters": main_r["iters"],
+                       "max_relres_true": main_r["max_relres_true"], "all_converged": main_r["all_converged"],
+                       "smoothers": {k: {kk: v[kk] for kk in ("s_per_solve", "solves_per_s", "iters", "max_relres_true",
+                                                             "all_converged")} for k, v in results.items()}},
+            "roofline": {"kernel": "k_row<1,double,double,double> level-0 SpMV y = A x", "bound": "hbm",
+                         "achieved": sp["GBps"], "peak": peak, "unit": "GB/s", "frac": sp["GBps"] / peak,
+                         "peak_kind": peak_kind, "traffic": None,
+                         "algorithmic_bytes": sp["bytes"], "launch_s": sp["s"]},
+            "kernels": {k: {kk: (round(vv, 9) if isinstance(vv, float) else vv) for kk, vv in v.items()} for k, v in kern.items()},
+            "clocks": main_r["clocks"],
+            "e2e": {"value": world * Ke / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * 8 * n,
+                    "d2h_bytes_per_step": 8 * n, "entry_point": "nsamg_solve_host"},
+            "gpu_launches": main_r["launches"],
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(A, H, rhs[0], main_r["iters"][0])
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _single_thread():
+    """Context limiting BLAS threads to 1 (returns (context, cores))."""
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(limits=1), 1
+    except ImportError:
+        import contextlib
+        pinned = os.environ.get("OPENBLAS_NUM_THREADS") == "1"
+        return contextlib.nullcontext(), 1 if pinned else (os.cpu_count() or 1)
+
+
+def oracle_sample(A, H, b, iters_sample: int):
+    """Time `iters_sample` Arnoldi steps of the oracle's one-reduce GMRES with its V-cycle
+    (definition-mode smoothers) on the full system; returns seconds per Arnoldi step."""
+    import oracle.kernels as K
+    from oracle.gmres import gmres_onereduce
+    from oracle.vcycle import vcycle
+    p = K.SmootherParams(smoother=K.HYBRID_ILU0, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3)
+    M = lambda v: vcycle(H, v, p)
+    M(b)  # caches the splits
+    t0 = time.perf_counter()
+    r = gmres_onereduce(A, b, M, m=RESTART, rtol=1e-300, maxit=iters_sample)
+    dt = time.perf_counter() - t0
+    return dt / max(r.iters, 1), r.iters
+
+
+def cpu_baseline(A, H, b, iters_full: int):
+    ctx, cores = _single_thread()
+    with ctx:
+        s_per_step, k = oracle_sample(A, H, b, 10)
+    t_solve = s_per_step * iters_full
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} Arnoldi steps of the FP64 oracle (numpy/scipy, single thread) on the full 128^3 system, "
+                      f"{s_per_step:.3f} s/step, scaled to the {iters_full}-step solve the GPU took"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    A, H, rhs = build_inputs()
+    import oracle.kernels as K
+    from oracle.gmres import gmres_onereduce
+    from oracle.vcycle import vcycle
+    p = K.SmootherParams(smoother=K.HYBRID_ILU0, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3)
+    # warm-up: one full oracle solve gives its own iteration count for the workload
+    t0 = time.perf_counter()
+    full = gmres_onereduce(A, rhs[0], lambda v: vcycle(H, v, p), m=RESTART, rtol=RTOL, maxit=MAXIT)
+    t_full = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(A, H, rhs[0], 2)
+    per = []
+    ctx, cores = _single_thread()
+    with ctx:
+        for k in range(args.steps):
+            s, _ = oracle_sample(A, H, rhs[k % N_RHS], 3)
+            per.append(s)
+    s_step = statistics.mean(per)
+    value = 1.0 / (s_step * full.iters)
+    line = {"impl": "reference", "metric": "solves/s to rel-res 1e-8 (GMRES(50)+C-AMG, 128^3 pressure Poisson)",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_iters": full.iters,
+                                                            "oracle_full_solve_s": t_full,
+                                                            "oracle_relres": full.relres_true},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: 3 Arnoldi steps of the FP64 oracle on the full system; "
+                                       f"value = 1 / (s per step x {full.iters} steps)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_profile(args):
+    """One solve of the main configuration inside an NVTX range 'timed_solve' (for ncu
+    --nvtx-include), after warm-up solves."""
+    import torch
+    from paper_2112_14681_b300 import nsamg
+    nsamg.load()
+    A, H, rhs = build_inputs()
+    stream = torch.cuda.Stream()
+    p = nsamg.default_params(restart=RESTART, use_graph=0 if args.no_graph else 1, **SMOOTHERS[args.smoother])
+    h = nsamg.setup_hierarchy(H, p, stream=stream.cuda_stream)
+    b = torch.from_numpy(rhs[0]).cuda()
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            x.zero_()
+        nsamg.solve(h, b, x, RTOL, MAXIT)
+    with torch.cuda.stream(stream):
+        x.zero_()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_solve")
+    st = nsamg.solve(h, b, x, RTOL, MAXIT)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": st, "launches": nsamg.solve_launches(h, st)}))
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nsamg", choices=["nsamg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "nsamg":
+        args.warmup = 3
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

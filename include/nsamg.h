@@ -156,6 +156,10 @@ int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, 
 /* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
 int nsamg_level_group(nsamg_handle* h, int level);
 
+/* Kernel launches in one Arnoldi step (V-cycle, SpMV, Gram, update). A solve launches
+ * 1 + iters * launches_per_step + 2 * (restarts + 1) kernels. */
+int nsamg_launches_per_step(nsamg_handle* h);
+
 void nsamg_destroy(nsamg_handle* h);
 const char* nsamg_status_str(int status);
 const char* nsamg_last_error(void);

@@ -37,6 +37,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int kThreads = 256;
 
+// Kernel launches enqueued by the engine on this thread (used to report launches per step).
+thread_local int64_t g_launches = 0;
+
 inline int blocks_for(int64_t threads) { return (int)std::max<int64_t>(1, (threads + kThreads - 1) / kThreads); }
 
 // ------------------------------------------------------------------------------------------
@@ -161,6 +164,7 @@ template <typename TM, typename TX, typename TY>
 void launch_row(const RowOp<TM, TX, TY>& op, int G, cudaStream_t s) {
   if (op.n <= 0) return;
   if (!op.v) G = 1;
+  ++g_launches;
   const int nb = blocks_for((int64_t)op.n * G);
   switch (G) {
     case 1: k_row<1, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
@@ -245,6 +249,7 @@ struct nsamg_handle {
   // graph
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  int launches_per_step = 0;
 };
 
 namespace {
@@ -449,6 +454,7 @@ void smooth(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, bool backward, boo
 template <typename T>
 void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c) {
   if (h->coarse_inv) {
+    ++g_launches;
     const int nb = (L.n * 32 + kThreads - 1) / kThreads;
     k_dense_gemv<double, T><<<nb, kThreads, 0, c.s>>>(L.n, h->coarse_inv, b, x, c.skip);
   } else {
@@ -556,6 +562,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ga.st = h->st;
   ga.scr = h->scr;
   k_gram<<<h->gram_blocks, kGramThreads, 0, s>>>(ga);
+  g_launches += 2;
   UpdateArgs ua{};
   ua.n = h->n;
   ua.V = h->V;
@@ -569,6 +576,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
 }
 
 void enqueue_xupdate(nsamg_handle* h, cudaStream_t s) {
+  ++g_launches;
   k_xupdate<double><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z, h->ld, h->st);
 }
 
@@ -588,6 +596,7 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   ra.scr.ticket = h->scr.ticket + 2;
   const int G = A.G;
   const int nb = blocks_for((int64_t)A.n * G);
+  ++g_launches;
   switch (G) {
     case 1: k_resid<1><<<nb, kRedThreads, 0, s>>>(ra); break;
     case 2: k_resid<2><<<nb, kRedThreads, 0, s>>>(ra); break;
@@ -630,7 +639,9 @@ int build_graph(nsamg_handle* h) {
   CK(cudaGraphAddNode(&inner, outer_body, nullptr, nullptr, 0, &ip));
   cudaGraph_t inner_body = ip.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = g_launches;
   enqueue_step(h, cs, (unsigned long long)hin);
+  h->launches_per_step = (int)(g_launches - before);
   CK(cudaStreamEndCapture(cs, &inner_body));
   CK(cudaStreamBeginCaptureToGraph(cs, outer_body, &inner, nullptr, 1, cudaStreamCaptureModeThreadLocal));
   enqueue_xupdate(h, cs);
@@ -771,8 +782,20 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     }
   }
   CK(cudaStreamSynchronize(h->stream));
-  if (p.use_graph)
+  if (p.use_graph) {
     if ((rc = build_graph(h))) return rc;
+  } else {  // count the launches of one step without running it
+    cudaGraph_t tmp;
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = g_launches;
+    enqueue_step(h, cs, 0ull);
+    h->launches_per_step = (int)(g_launches - before);
+    CK(cudaStreamEndCapture(cs, &tmp));
+    cudaGraphDestroy(tmp);
+    cudaStreamDestroy(cs);
+  }
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
@@ -950,6 +973,10 @@ int nsamg_num_levels(nsamg_handle* h) { return h ? (int)h->lv.size() : fail(NSAM
 int nsamg_level_size(nsamg_handle* h, int level) {
   int rc = level_ok(h, level);
   return rc ? rc : h->lv[level].n;
+}
+
+int nsamg_launches_per_step(nsamg_handle* h) {
+  return h ? h->launches_per_step : fail(NSAMG_ERR_INVALID_ARG, "null handle");
 }
 
 int nsamg_level_group(nsamg_handle* h, int level) {

@@ -57,7 +57,7 @@ EXPORTS = [
     "nsamg_default_params", "nsamg_setup_hierarchy", "nsamg_solve", "nsamg_solve_host", "nsamg_apply_vcycle",
     "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
-    "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error",
+    "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
 ]
 
 _lib = None
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "nsamg_gram": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_update": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
         "nsamg_destroy": (None, [vp]),
+        "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
         "nsamg_last_error": (ctypes.c_char_p, []),
     }
@@ -230,6 +231,15 @@ def level_size(h: Handle, level: int) -> int:
 
 def level_group(h: Handle, level: int) -> int:
     return _check(load().nsamg_level_group(h._h, level), allow=range(1, 33))
+
+
+def launches_per_step(h: Handle) -> int:
+    return _check(load().nsamg_launches_per_step(h._h), allow=range(0, 1 << 30))
+
+
+def solve_launches(h: Handle, stats: dict) -> int:
+    """Kernel launches of a finished solve: 1 + iters * per_step + 2 * cycles."""
+    return 1 + stats["iters"] * launches_per_step(h) + 2 * (stats["restarts"] + 1)
 
 
 def level_spmv(h: Handle, level: int, x, y) -> None:
