@@ -398,6 +398,43 @@ def run_profile(args):
     h.close()
 
 
+def run_profile_kernel(args):
+    """Launch one hot kernel 3 times on the full-size finest level (no autotuning, no graph, no
+    other launches before it), for a detailed ncu capture."""
+    import torch
+    from paper_2112_14681_b300 import nsamg
+    nsamg.load()
+    A, H, rhs = build_inputs()
+    n = A.shape[0]
+    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=1, **SMOOTHERS["hybrid_ilu0"])
+    h = nsamg.setup_hierarchy(H, p)
+    x = torch.from_numpy(rhs[0]).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    if args.profile_kernel == "spmv":
+        for _ in range(3):
+            nsamg.level_spmv(h, 0, x, y)
+    elif args.profile_kernel == "ilu":
+        for _ in range(3):
+            nsamg.level_smooth(h, 0, x, y, backward=False, x_is_zero=True)
+    else:
+        i = 10
+        ld = (n + 63) // 64 * 64
+        V = torch.rand((i + 2) * ld, dtype=torch.float64, device="cuda")
+        o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
+        hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
+        ss = torch.empty(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(3):
+            if args.profile_kernel == "gram":
+                nsamg.gram(n, i, V, ld, x, o)
+            else:
+                nsamg.update(n, i, V, ld, x, 1.0, hc, ss)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_kernel": args.profile_kernel, "n": n}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,10 +445,14 @@ def main():
     ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
+    ap.add_argument("--profile-kernel", choices=["spmv", "ilu", "gram", "update"],
+                    help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":
         args.warmup = 3
-    if args.profile:
+    if args.profile_kernel:
+        run_profile_kernel(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)
