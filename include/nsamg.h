@@ -153,6 +153,22 @@ int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d
 int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
                  double* d_sumsq, void* stream);
 
+/* Allocation-free variant of nsamg_gram (the paper has no counterpart; this is a service
+ * to callers). Same arguments, same results: out[0..i] = [V_i, vt]^T vt, out[i+1..2i+1] =
+ * [V_i, vt]^T w. It is meant for callers that must not allocate device memory: an application
+ * whose own allocator has already reserved the device memory it is allowed to use, or a
+ * latency-critical loop that cannot risk entering the CUDA allocator (which may synchronise the
+ * device or fail under memory pressure). Its scratch is a fixed array inside the library image
+ * (about 520 KB, room for 512 blocks x 2 x 65 doubles plus a counter) that every device loading
+ * the library keeps until the process exits; no cudaMalloc, cudaFree or other allocating routine
+ * is called. Limit: i <= 63 (columns 0..63); larger i is rejected with NSAMG_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture. All calls share the one array and each call clears its
+ * counter first: calls that overlap on the GPU (different streams, or threads without ordering)
+ * race and give wrong results, so serialise them. */
+int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out,
+                       void* stream);
+
 /* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
 int nsamg_level_group(nsamg_handle* h, int level);
 

@@ -849,6 +849,41 @@ int standalone_scratch(Scratch* out) {
   return NSAMG_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Allocation-free Gram: its scratch lives in a fixed file-scope device array instead of memory
+// from cudaMalloc. Layout: bytes [0, 256) hold the last-block ticket, the block partials start
+// at byte 256. Every device that loads this library holds the array until the process exits.
+// ------------------------------------------------------------------------------------------
+constexpr int kNoAllocBlocks = 512;  // most blocks the array has room for
+constexpr size_t kNoAllocBytes = 256 + sizeof(double) * (size_t)kNoAllocBlocks * 2 * (kMaxM + 1);
+static __device__ __align__(256) unsigned char g_gram_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+std::vector<void*> g_noalloc_addr;  // device address of g_gram_scratch, per device (set-up once)
+
+// Looks up the device address of the array for the current device. In host code the array's
+// name is only a host-side stand-in, so kernels must be given this address instead.
+int noalloc_scratch(Scratch* out, int* blocks) {
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_addr.size() <= dev) g_noalloc_addr.resize(dev + 1, nullptr);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_gram_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  out->ticket = (unsigned*)base;
+  out->partials = (double*)((unsigned char*)base + 256);
+  *blocks = std::min(2 * sms, kNoAllocBlocks);
+  return NSAMG_OK;
+}
+
 int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
   if (!h || !d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
   if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
@@ -1077,6 +1112,32 @@ int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d
   ga.out = d_out;
   ga.scr = scr;
   k_gram<<<2 * sms, kGramThreads, 0, (cudaStream_t)stream>>>(ga);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out,
+                       void* stream) {
+  if (i < 0 || i >= kMaxM)
+    return fail(NSAMG_ERR_INVALID_ARG, "nsamg_gram_noalloc: i = " + std::to_string(i) +
+                                           " is beyond the fixed scratch, which holds columns 0..63 (i <= 63)");
+  if (n <= 0 || !d_V || !d_w || !d_out || ldv < n) return fail(NSAMG_ERR_INVALID_ARG, "bad gram arguments");
+  Scratch scr;
+  int blocks = 0;
+  int rc = noalloc_scratch(&scr, &blocks);
+  if (rc) return rc;
+  // The ticket must start at zero; clear it on every call (a plain memset, no allocation).
+  CK(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), (cudaStream_t)stream));
+  GramArgs ga{};
+  ga.n = n;
+  ga.V = d_V;
+  ga.ldv = ldv;
+  ga.w = d_w;
+  ga.st = nullptr;
+  ga.i_standalone = i;
+  ga.out = d_out;
+  ga.scr = scr;
+  k_gram<<<blocks, kGramThreads, 0, (cudaStream_t)stream>>>(ga);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }

@@ -58,6 +58,7 @@ EXPORTS = [
     "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
     "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
+    "nsamg_gram_noalloc",
 ]
 
 _lib = None
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
         "nsamg_coarse_solve": (i32, [vp, vp, vp]),
         "nsamg_gram": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_update": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
+        "nsamg_gram_noalloc": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_destroy": (None, [vp]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
@@ -268,6 +270,13 @@ def coarse_solve(h: Handle, b, z) -> None:
 
 def gram(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
     _check(load().nsamg_gram(int(n), int(i), _ptr(V), int(ldv), _ptr(w), _ptr(out), stream))
+
+
+def gram_noalloc(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
+    """Same as gram() but never allocates device memory: the scratch is a fixed array inside the
+    library (room for i <= 63). For callers whose device memory is owned by another allocator or
+    who must stay out of the CUDA allocator; overlapping calls race on the shared array."""
+    _check(load().nsamg_gram_noalloc(int(n), int(i), _ptr(V), int(ldv), _ptr(w), _ptr(out), stream))
 
 
 def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
