@@ -118,6 +118,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic(key: str):
+    """DRAM read+write bytes per launch from the committed ncu summary, or None once the kernel
+    sources have changed since those counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        src = b"".join(open(os.path.join(ROOT, "paper_2112_14681_b300", "csrc", n), "rb").read()
+                       for n in ("kernels.cuh", "gmres.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] != d["source_sha"]:
+            return None
+        return d[key]["traffic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def spmv_bytes(A) -> int:
     n, nnz = A.shape[0], A.nnz
     return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
@@ -282,7 +298,7 @@ def run_gpu(args):
                                                              "all_converged")} for k, v in results.items()}},
             "roofline": {"kernel": "k_row<1,double,double,double> level-0 SpMV y = A x", "bound": "hbm",
                          "achieved": sp["GBps"], "peak": peak, "unit": "GB/s", "frac": sp["GBps"] / peak,
-                         "peak_kind": peak_kind, "traffic": None,
+                         "peak_kind": peak_kind, "traffic": measured_traffic("spmv_l0"),
                          "algorithmic_bytes": sp["bytes"], "launch_s": sp["s"]},
             "kernels": {k: {kk: (round(vv, 9) if isinstance(vv, float) else vv) for kk, vv in v.items()} for k, v in kern.items()},
             "clocks": main_r["clocks"],
