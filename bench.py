@@ -64,6 +64,10 @@ SMOOTHERS = {
     "hybrid_ilu0": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
     "poly_gs": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
     "l1_jacobi": dict(smoother=1, pre_sweeps=2, post_sweeps=2),
+    # mixed precision: FP32 V-cycle (matrices + vectors) inside FP64 flexible GMRES
+    "hybrid_ilu0_fp32v": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1,
+                              vcycle_fp32=1),
+    "poly_gs_fp32v": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1, vcycle_fp32=1),
 }
 
 

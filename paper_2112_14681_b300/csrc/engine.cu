@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <initializer_list>
 
 #include "nsamg.h"
 #include "kernels.cuh"
@@ -232,14 +233,18 @@ struct nsamg_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   nsamg_params p{};
-  std::vector<Level<double>> lv;
+  bool fp32 = false;               // FP32 V-cycle (matrices and vectors) inside FP64 GMRES
+  std::vector<Level<double>> lv;    // FP64 levels (only level 0's A when fp32)
+  std::vector<Level<float>> lv32;   // FP32 levels (fp32 only)
   double* coarse_inv = nullptr;
+  float* coarse_inv32 = nullptr;
   int nc = 0;
   // GMRES workspace
   int n = 0, m = 0;
   int64_t ld = 0;
   double* V = nullptr;  // (m+1) columns
-  double* Z = nullptr;  // m columns
+  double* Z = nullptr;  // m columns (FP64 V-cycle)
+  float* Z32 = nullptr; // m columns (FP32 V-cycle)
   double* w = nullptr;
   GState* st = nullptr;
   GState* h_st = nullptr;  // pinned host mirror
@@ -451,12 +456,16 @@ void smooth(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, bool backward, boo
   }
 }
 
+inline const double* coarse_ptr(nsamg_handle* h, double*) { return h->coarse_inv; }
+inline const float* coarse_ptr(nsamg_handle* h, float*) { return h->coarse_inv32; }
+
 template <typename T>
 void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c) {
-  if (h->coarse_inv) {
+  const T* C = coarse_ptr(h, (T*)nullptr);
+  if (C) {
     ++g_launches;
     const int nb = (L.n * 32 + kThreads - 1) / kThreads;
-    k_dense_gemv<double, T><<<nb, kThreads, 0, c.s>>>(L.n, h->coarse_inv, b, x, c.skip);
+    k_dense_gemv<T, T><<<nb, kThreads, 0, c.s>>>(L.n, C, b, x, c.skip);
   } else {
     smooth(h, L, b, x, false, true, h->p.coarse_sweeps, c);
   }
@@ -544,15 +553,36 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   b.p = h->V;
   b.sel = sel;
   b.ld = h->ld;
-  VRef<double> z;
-  z.p = h->Z;
-  z.sel = sel;
-  z.ld = h->ld;
-  vcycle(h, h->lv, 0, b, z, c);  // z_i = M^-1 vt_i
-  {
+  if (!h->fp32) {
+    VRef<double> z;
+    z.p = h->Z;
+    z.sel = sel;
+    z.ld = h->ld;
+    vcycle(h, h->lv, 0, b, z, c);  // z_i = M^-1 vt_i
     auto op = op_mat(h->lv[0].A, cref(z));  // w = A z_i
     op.out = vref(h->w);
     run(op, h->lv[0].A.G, c);
+  } else {
+    // FP32 V-cycle: vt_i rounded to FP32 (round to nearest), z_i kept in FP32 (flexible GMRES
+    // stores Z), outer product w = A z_i with the FP64 matrix.
+    Level<float>& L0 = h->lv32[0];
+    ++g_launches;
+    k_cast<double, float><<<8 * 148, kThreads, 0, s>>>(h->n, b, vref(L0.b), skip);
+    VRef<float> z;
+    z.p = h->Z32;
+    z.sel = sel;
+    z.ld = h->ld;
+    vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
+    const auto& A = h->lv[0].A;
+    RowOp<double, float, double> op;
+    op.n = A.n;
+    op.rp = A.rp;
+    op.ci = A.ci;
+    op.v = A.v;
+    op.src = cref(z);
+    op.out = vref(h->w);
+    op.skip = skip;
+    launch_row(op, A.G, s);
   }
   GramArgs ga{};
   ga.n = h->n;
@@ -577,7 +607,8 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
 
 void enqueue_xupdate(nsamg_handle* h, cudaStream_t s) {
   ++g_launches;
-  k_xupdate<double><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z, h->ld, h->st);
+  if (h->fp32) k_xupdate<float><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z32, h->ld, h->st);
+  else k_xupdate<double><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z, h->ld, h->st);
 }
 
 void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
@@ -658,15 +689,99 @@ int check_params(const nsamg_params& p) {
   if (p.neumann_terms < 1 || p.ilu_terms_L < 1 || p.ilu_terms_U < 1) return fail(NSAMG_ERR_INVALID_ARG, "series terms must be >= 1");
   if (p.pre_sweeps < 0 || p.post_sweeps < 0 || p.coarse_sweeps < 1) return fail(NSAMG_ERR_INVALID_ARG, "bad sweep counts");
   if (p.restart < 1 || p.restart > NSAMG_MAX_RESTART) return fail(NSAMG_ERR_INVALID_ARG, "restart out of range 1..64");
-  if (p.vcycle_fp32 != 0) return fail(NSAMG_ERR_INVALID_ARG, "FP32 V-cycle not available in this build");
+  if (p.vcycle_fp32 != 0 && p.vcycle_fp32 != 1) return fail(NSAMG_ERR_INVALID_ARG, "vcycle_fp32 must be 0 or 1");
   if (p.spmv_group < 0 || p.spmv_group > 32 || (p.spmv_group & (p.spmv_group - 1))) return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be 0 or a power of two <= 32");
   return NSAMG_OK;
 }
 
-int alloc_vec(double** p, int64_t n) {
-  CK(cudaMalloc(p, sizeof(double) * std::max<int64_t>(n, 1)));
-  CK(cudaMemset(*p, 0, sizeof(double) * std::max<int64_t>(n, 1)));
+template <typename T>
+int alloc_vec(T** p, int64_t n) {
+  CK(cudaMalloc(p, sizeof(T) * std::max<int64_t>(n, 1)));
+  CK(cudaMemset(*p, 0, sizeof(T) * std::max<int64_t>(n, 1)));
   return NSAMG_OK;
+}
+
+// Upload every level of the host hierarchy at precision T (matrix values and vectors): A, the
+// pre-scaled triangles of A for polynomial GS, D^-1, the l1 diagonal, P, R and, where the
+// smoother uses it, the ILU(0) factors. `only_A0` uploads just the finest A (the FP64 operator
+// of an FP32-V-cycle handle).
+template <typename T>
+int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vector<Level<T>>& lvs, bool only_A0) {
+  int rc;
+  const int nl = only_A0 ? 1 : H->nlevels;
+  lvs.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const nsamg_level_desc& D = H->levels[l];
+    Level<T>& L = lvs[l];
+    L.n = D.A.nrows;
+    if ((rc = upload(D.A, L.A))) return rc;
+    if (only_A0) return NSAMG_OK;
+    std::vector<double> dinv(L.n), dl1(L.n);
+    for (int i = 0; i < L.n; ++i) {
+      double a = 0, s1 = 0;
+      for (int q = D.A.rowptr[i]; q < D.A.rowptr[i + 1]; ++q) {
+        if (D.A.col[q] == i) a = D.A.val[q];
+        s1 += std::fabs(D.A.val[q]);
+      }
+      dinv[i] = 1.0 / a;
+      dl1[i] = 1.0 / s1;
+    }
+    if ((rc = upload_vec(dinv, &L.dinv))) return rc;
+    if ((rc = upload_vec(dl1, &L.dl1inv))) return rc;
+    if ((rc = upload(tri_part(D.A, true, &dinv, &dinv), L.L2))) return rc;
+    if ((rc = upload(tri_part(D.A, false, &dinv, &dinv), L.U2))) return rc;
+    if ((rc = upload(tri_part(D.A, true, &dinv, nullptr), L.L1))) return rc;
+    if ((rc = upload(tri_part(D.A, false, &dinv, nullptr), L.U1))) return rc;
+    if (l < nl - 1) {
+      if ((rc = upload(D.P, L.P))) return rc;
+      if ((rc = upload(D.R, L.R))) return rc;
+    }
+    const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
+    if (want_ilu && D.ilu_L.nrows > 0 && l < nl - 1) {
+      if ((rc = upload(D.ilu_L, L.iL))) return rc;
+      if ((rc = upload(D.ilu_U, L.iU))) return rc;
+      std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
+      if ((rc = upload_vec(idv, &L.idinv))) return rc;
+      L.ilu = true;
+    }
+    L.kind = (p.smoother == NSAMG_SMOOTHER_JACOBI_L1) ? 'j' : (L.ilu ? 'i' : 'p');
+    T** vecs[] = {&L.b, &L.x, &L.r, &L.t1, &L.t2, &L.t3};
+    for (T** v : vecs)
+      if ((rc = alloc_vec(v, L.n))) return rc;
+  }
+  return NSAMG_OK;
+}
+
+template <typename T>
+int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaStream_t s) {
+  int rc;
+  for (auto& L : lvs) {
+    DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
+    for (DCSR<T>* M : mats) {
+      if (!M->present()) continue;
+      if (group) {
+        M->G = group;
+        continue;
+      }
+      T* x = (M->m <= L.n && L.t1) ? L.t1 : big_x;
+      T* y = (M->n <= L.n && L.t2) ? L.t2 : big_y;
+      if (M == &L.R) { x = L.t1; y = big_y; }
+      if (M == &L.P) { x = big_x; y = L.t2; }
+      if ((rc = tune(*M, x, y, s))) return rc;
+    }
+  }
+  return NSAMG_OK;
+}
+
+template <typename T>
+void release_levels(std::vector<Level<T>>& lvs) {
+  for (auto& L : lvs) {
+    DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
+    for (DCSR<T>* M : mats) release(*M);
+    T* vecs[] = {L.dinv, L.dl1inv, L.idinv, L.b, L.x, L.r, L.t1, L.t2, L.t3};
+    for (T* v : vecs) cudaFree(v);
+  }
+  lvs.clear();
 }
 
 int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stream, nsamg_handle* h) {
@@ -703,55 +818,31 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
         return fail(NSAMG_ERR_BAD_MATRIX, nm + ": ILU factor dimensions");
     }
   }
-  h->lv.resize(nl);
-  for (int l = 0; l < nl; ++l) {
-    const nsamg_level_desc& D = H->levels[l];
-    Level<double>& L = h->lv[l];
-    L.n = D.A.nrows;
-    if ((rc = upload(D.A, L.A))) return rc;
-    std::vector<double> dinv(L.n), dl1(L.n);
-    for (int i = 0; i < L.n; ++i) {
-      double a = 0, s1 = 0;
-      for (int q = D.A.rowptr[i]; q < D.A.rowptr[i + 1]; ++q) {
-        if (D.A.col[q] == i) a = D.A.val[q];
-        s1 += std::fabs(D.A.val[q]);
-      }
-      dinv[i] = 1.0 / a;
-      dl1[i] = 1.0 / s1;
-    }
-    if ((rc = upload_vec(dinv, &L.dinv))) return rc;
-    if ((rc = upload_vec(dl1, &L.dl1inv))) return rc;
-    if ((rc = upload(tri_part(D.A, true, &dinv, &dinv), L.L2))) return rc;
-    if ((rc = upload(tri_part(D.A, false, &dinv, &dinv), L.U2))) return rc;
-    if ((rc = upload(tri_part(D.A, true, &dinv, nullptr), L.L1))) return rc;
-    if ((rc = upload(tri_part(D.A, false, &dinv, nullptr), L.U1))) return rc;
-    if (l < nl - 1) {
-      if ((rc = upload(D.P, L.P))) return rc;
-      if ((rc = upload(D.R, L.R))) return rc;
-    }
-    const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
-    if (want_ilu && D.ilu_L.nrows > 0 && l < nl - 1) {
-      if ((rc = upload(D.ilu_L, L.iL))) return rc;
-      if ((rc = upload(D.ilu_U, L.iU))) return rc;
-      std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
-      if ((rc = upload_vec(idv, &L.idinv))) return rc;
-      L.ilu = true;
-    }
-    L.kind = (p.smoother == NSAMG_SMOOTHER_JACOBI_L1) ? 'j' : (L.ilu ? 'i' : 'p');
-    for (double** v : {&L.b, &L.x, &L.r, &L.t1, &L.t2, &L.t3})
-      if ((rc = alloc_vec(v, L.n))) return rc;
-  }
+  h->fp32 = p.vcycle_fp32 == 1;
+  if ((rc = build_levels<double>(H, p, h->lv, h->fp32))) return rc;
+  if (h->fp32 && (rc = build_levels<float>(H, p, h->lv32, false))) return rc;
   if (H->coarse_inv) {
-    h->nc = h->lv.back().n;
-    CK(cudaMalloc(&h->coarse_inv, sizeof(double) * (size_t)h->nc * h->nc));
-    CK(cudaMemcpy(h->coarse_inv, H->coarse_inv, sizeof(double) * (size_t)h->nc * h->nc, cudaMemcpyHostToDevice));
+    h->nc = H->levels[nl - 1].A.nrows;
+    const size_t nc2 = (size_t)h->nc * h->nc;
+    if (h->fp32) {
+      std::vector<float> c32(H->coarse_inv, H->coarse_inv + nc2);
+      CK(cudaMalloc(&h->coarse_inv32, sizeof(float) * nc2));
+      CK(cudaMemcpy(h->coarse_inv32, c32.data(), sizeof(float) * nc2, cudaMemcpyHostToDevice));
+    } else {
+      CK(cudaMalloc(&h->coarse_inv, sizeof(double) * nc2));
+      CK(cudaMemcpy(h->coarse_inv, H->coarse_inv, sizeof(double) * nc2, cudaMemcpyHostToDevice));
+    }
   }
   // GMRES workspace: V (m+1 columns), Z (m columns), w; leading dimension padded to 64 entries.
   h->n = h->lv[0].n;
   h->m = p.restart;
   h->ld = ((int64_t)h->n + 63) / 64 * 64;
   if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
-  if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
+  if (h->fp32) {
+    if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
+  } else {
+    if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
+  }
   if ((rc = alloc_vec(&h->w, h->ld))) return rc;
   CK(cudaMalloc(&h->st, sizeof(GState)));
   CK(cudaMemset(h->st, 0, sizeof(GState)));
@@ -767,19 +858,10 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
   // Threads per row: fixed by the caller or tuned on the device.
-  for (auto& L : h->lv) {
-    for (DCSR<double>* M : {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU}) {
-      if (!M->present()) continue;
-      if (p.spmv_group) {
-        M->G = p.spmv_group;
-      } else {
-        double* x = (M->m <= L.n) ? L.t1 : h->V;
-        double* y = (M->n <= L.n) ? L.t2 : h->w;
-        if (M == &L.R) { x = L.t1; y = h->w; }
-        if (M == &L.P) { x = h->V; y = L.t2; }
-        if ((rc = tune(*M, x, y, h->stream))) return rc;
-      }
-    }
+  if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, h->stream))) return rc;
+  if (h->fp32) {
+    // FP32 scratch for tuning: the finest level's work vectors are the largest
+    if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, h->stream))) return rc;
   }
   CK(cudaStreamSynchronize(h->stream));
   if (p.use_graph) {
@@ -806,13 +888,13 @@ void destroy_impl(nsamg_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  for (auto& L : h->lv) {
-    for (DCSR<double>* M : {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU}) release(*M);
-    for (double* v : {L.dinv, L.dl1inv, L.idinv, L.b, L.x, L.r, L.t1, L.t2, L.t3}) cudaFree(v);
-  }
+  release_levels(h->lv);
+  release_levels(h->lv32);
   cudaFree(h->coarse_inv);
+  cudaFree(h->coarse_inv32);
   cudaFree(h->V);
   cudaFree(h->Z);
+  cudaFree(h->Z32);
   cudaFree(h->w);
   cudaFree(h->st);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -822,10 +904,20 @@ void destroy_impl(nsamg_handle* h) {
   delete h;
 }
 
+int nlev(nsamg_handle* h) { return h->fp32 ? (int)h->lv32.size() : (int)h->lv.size(); }
+
 int level_ok(nsamg_handle* h, int level) {
   if (!h) return fail(NSAMG_ERR_INVALID_ARG, "null handle");
-  if (level < 0 || level >= (int)h->lv.size()) return fail(NSAMG_ERR_INVALID_ARG, "level out of range");
+  if (level < 0 || level >= nlev(h)) return fail(NSAMG_ERR_INVALID_ARG, "level out of range");
   return NSAMG_OK;
+}
+
+void to32(nsamg_handle* h, const double* a, float* b, int64_t n) {
+  k_cast<double, float><<<blocks_for(n), kThreads, 0, h->stream>>>(n, cref(a), vref(b), nullptr);
+}
+
+void to64(nsamg_handle* h, const float* a, double* b, int64_t n) {
+  k_cast<float, double><<<blocks_for(n), kThreads, 0, h->stream>>>(n, cref(a), vref(b), nullptr);
 }
 
 // Standalone scratch for nsamg_gram / nsamg_update (one per device, allocated on first use).
@@ -933,6 +1025,81 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
   return status;
 }
 
+// Per-level operations. FP64 handles run the FP64 kernels on the caller's arrays; FP32-V-cycle
+// handles round the inputs to FP32 in the level's work vectors, run the FP32 kernels and widen
+// the result back to FP64.
+template <typename T>
+int level_op(nsamg_handle* h, std::vector<Level<T>>& lv, int which, int level, int backward, int x_is_zero,
+             const T* in1, const T* in2, T* out) {
+  Level<T>& L = lv[level];
+  Ctx c{h->stream, nullptr};
+  switch (which) {
+    case 0: {  // spmv: out = A in1
+      auto op = op_mat(L.A, cref(in1));
+      op.out = vref(out);
+      launch_row(op, L.A.G, h->stream);
+      break;
+    }
+    case 1: {  // residual: out = in1 - A in2
+      auto op = op_mat(L.A, cref(in2));
+      op.base = cref(in1);
+      op.neg = 1;
+      op.out = vref(out);
+      launch_row(op, L.A.G, h->stream);
+      break;
+    }
+    case 2:  // smooth: out (= x) <- sweep(b = in1, x = out)
+      smooth(h, L, cref(in1), vref(out), backward != 0, x_is_zero != 0, 1, c);
+      break;
+    case 3: {  // restrict: out = R in1
+      auto op = op_mat(L.R, cref(in1));
+      op.out = vref(out);
+      launch_row(op, L.R.G, h->stream);
+      break;
+    }
+    case 4: {  // prolong: out += P in1
+      auto op = op_mat(L.P, cref(in1));
+      op.add = cref((const T*)out);
+      op.out = vref(out);
+      launch_row(op, L.P.G, h->stream);
+      break;
+    }
+    case 5:  // coarse solve: out = A_L^-1 in1
+      coarse_solve(h, L, cref(in1), vref(out), c);
+      break;
+  }
+  return NSAMG_OK;
+}
+
+int level_dispatch(nsamg_handle* h, int which, int level, int backward, int x_is_zero, const double* in1,
+                   const double* in2, double* out) {
+  CK(cudaSetDevice(h->device));
+  if (!h->fp32) {
+    level_op<double>(h, h->lv, which, level, backward, x_is_zero, in1, in2, out);
+  } else {
+    auto& lv = h->lv32;
+    Level<float>& L = lv[level];
+    const int nl = (int)lv.size();
+    // staging: input 1 / input 2 / output in FP32 work vectors of the right sizes
+    float *a = L.b, *b2 = L.x, *o = L.x;
+    int na = L.n, no = L.n;
+    if (which == 0) { a = L.x; o = L.b; }
+    if (which == 1) { a = L.b; b2 = L.x; o = L.r; }
+    if (which == 2) { a = L.b; o = L.x; }
+    if (which == 3) { a = L.r; o = lv[level + 1].b; no = lv[level + 1].n; }
+    if (which == 4) { a = lv[level + 1].x; na = lv[level + 1].n; o = L.x; }
+    if (which == 5) { a = L.b; o = L.x; }
+    (void)nl;
+    to32(h, in1, a, na);
+    if (which == 1) to32(h, in2, b2, L.n);
+    if (which == 2 || which == 4) to32(h, out, o, no);
+    level_op<float>(h, lv, which, level, backward, x_is_zero, a, b2, o);
+    to64(h, o, out, no);
+  }
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -998,16 +1165,23 @@ int nsamg_apply_vcycle(nsamg_handle* h, const double* d_r, double* d_z) {
   if (!h || !d_r || !d_z) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
   CK(cudaSetDevice(h->device));
   Ctx c{h->stream, nullptr};
-  vcycle(h, h->lv, 0, cref(d_r), vref(d_z), c);
+  if (!h->fp32) {
+    vcycle(h, h->lv, 0, cref(d_r), vref(d_z), c);
+  } else {
+    Level<float>& L0 = h->lv32[0];
+    to32(h, d_r, L0.b, L0.n);
+    vcycle(h, h->lv32, 0, cref((const float*)L0.b), vref(L0.x), c);
+    to64(h, L0.x, d_z, L0.n);
+  }
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
 
-int nsamg_num_levels(nsamg_handle* h) { return h ? (int)h->lv.size() : fail(NSAMG_ERR_INVALID_ARG, "null handle"); }
+int nsamg_num_levels(nsamg_handle* h) { return h ? nlev(h) : fail(NSAMG_ERR_INVALID_ARG, "null handle"); }
 
 int nsamg_level_size(nsamg_handle* h, int level) {
   int rc = level_ok(h, level);
-  return rc ? rc : h->lv[level].n;
+  return rc ? rc : (h->fp32 ? h->lv32[level].n : h->lv[level].n);
 }
 
 int nsamg_launches_per_step(nsamg_handle* h) {
@@ -1016,82 +1190,49 @@ int nsamg_launches_per_step(nsamg_handle* h) {
 
 int nsamg_level_group(nsamg_handle* h, int level) {
   int rc = level_ok(h, level);
-  return rc ? rc : h->lv[level].A.G;
+  return rc ? rc : (h->fp32 ? h->lv32[level].A.G : h->lv[level].A.G);
 }
 
 int nsamg_level_spmv(nsamg_handle* h, int level, const double* d_x, double* d_y) {
   int rc = level_ok(h, level);
   if (rc) return rc;
   if (!d_x || !d_y) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
-  CK(cudaSetDevice(h->device));
-  auto& L = h->lv[level];
-  auto op = op_mat(L.A, cref(d_x));
-  op.out = vref(d_y);
-  launch_row(op, L.A.G, h->stream);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  return level_dispatch(h, 0, level, 0, 0, d_x, nullptr, d_y);
 }
 
 int nsamg_level_residual(nsamg_handle* h, int level, const double* d_b, const double* d_x, double* d_r) {
   int rc = level_ok(h, level);
   if (rc) return rc;
   if (!d_b || !d_x || !d_r) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
-  CK(cudaSetDevice(h->device));
-  auto& L = h->lv[level];
-  auto op = op_mat(L.A, cref(d_x));
-  op.base = cref(d_b);
-  op.neg = 1;
-  op.out = vref(d_r);
-  launch_row(op, L.A.G, h->stream);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  return level_dispatch(h, 1, level, 0, 0, d_b, d_x, d_r);
 }
 
 int nsamg_level_smooth(nsamg_handle* h, int level, int backward, int x_is_zero, const double* d_b, double* d_x) {
   int rc = level_ok(h, level);
   if (rc) return rc;
   if (!d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
-  CK(cudaSetDevice(h->device));
-  Ctx c{h->stream, nullptr};
-  smooth(h, h->lv[level], cref(d_b), vref(d_x), backward != 0, x_is_zero != 0, 1, c);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  return level_dispatch(h, 2, level, backward, x_is_zero, d_b, nullptr, d_x);
 }
 
 int nsamg_level_restrict(nsamg_handle* h, int level, const double* d_r, double* d_y) {
   int rc = level_ok(h, level);
   if (rc) return rc;
-  if (level >= (int)h->lv.size() - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no restriction");
-  CK(cudaSetDevice(h->device));
-  auto& L = h->lv[level];
-  auto op = op_mat(L.R, cref(d_r));
-  op.out = vref(d_y);
-  launch_row(op, L.R.G, h->stream);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  if (level >= nlev(h) - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no restriction");
+  if (!d_r || !d_y) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
+  return level_dispatch(h, 3, level, 0, 0, d_r, nullptr, d_y);
 }
 
 int nsamg_level_prolong(nsamg_handle* h, int level, const double* d_e, double* d_x) {
   int rc = level_ok(h, level);
   if (rc) return rc;
-  if (level >= (int)h->lv.size() - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no prolongation");
-  CK(cudaSetDevice(h->device));
-  auto& L = h->lv[level];
-  auto op = op_mat(L.P, cref(d_e));
-  op.add = cref((const double*)d_x);
-  op.out = vref(d_x);
-  launch_row(op, L.P.G, h->stream);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  if (level >= nlev(h) - 1) return fail(NSAMG_ERR_INVALID_ARG, "coarsest level has no prolongation");
+  if (!d_e || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null vector");
+  return level_dispatch(h, 4, level, 0, 0, d_e, nullptr, d_x);
 }
 
 int nsamg_coarse_solve(nsamg_handle* h, const double* d_b, double* d_z) {
   if (!h || !d_b || !d_z) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
-  CK(cudaSetDevice(h->device));
-  Ctx c{h->stream, nullptr};
-  coarse_solve(h, h->lv.back(), cref(d_b), vref(d_z), c);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  return level_dispatch(h, 5, nlev(h) - 1, 0, 0, d_b, nullptr, d_z);
 }
 
 int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream) {

@@ -290,3 +290,78 @@ def test_setup_rejects_bad_input():
     with pytest.raises(nsamg.NsamgError) as ei:
         nsamg.setup_hierarchy(H, nsamg.default_params(restart=65))
     assert ei.value.status == -1
+
+
+# ------------------------------------------------------------------------------------------------
+# FP32 V-cycle inside FP64 flexible GMRES (mixed precision). Per-kernel bound from the arithmetic:
+# an FP32 product sum over k entries with FP32-rounded inputs errs by at most
+# gamma_{k+3} |A||x| with u = 2^-24 (rounding of A, of x, and k accumulations).
+# ------------------------------------------------------------------------------------------------
+U32 = 2.0 ** -24
+
+
+def gamma(k):
+    return k * U32 / (1 - k * U32)
+
+
+@pytest.mark.parametrize("name", ["c1", "p23"])
+def test_fp32_level_kernels(name):
+    A, H = case(name)
+    p = nsamg.default_params(vcycle_fp32=1)
+    with nsamg.setup_hierarchy(H, p) as h:
+        rng = np.random.default_rng(5)
+        for l, lev in enumerate(H.levels):
+            n = lev.n
+            x, b = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+            k = int(np.diff(lev.A.indptr).max())
+            bound = gamma(k + 3) * (abs(lev.A) @ np.abs(x))
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            nsamg.level_spmv(h, l, dev(x), y)
+            assert np.all(np.abs(host(y) - K.spmv(lev.A, x)) <= bound)
+            r = torch.empty_like(y)
+            nsamg.level_residual(h, l, dev(b), dev(x), r)
+            assert np.all(np.abs(host(r) - K.residual(lev.A, b, x)) <= bound + gamma(k + 3) * np.abs(b))
+            if l < H.nlevels - 1:
+                yc = torch.empty(lev.R.shape[0], dtype=torch.float64, device="cuda")
+                nsamg.level_restrict(h, l, dev(x), yc)
+                kr = int(np.diff(lev.R.indptr).max())
+                assert np.all(np.abs(host(yc) - K.restrict(lev.R, x)) <= gamma(kr + 3) * (abs(lev.R) @ np.abs(x)))
+
+
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.JACOBI_L1])
+def test_fp32_vcycle_close_to_fp64(smoother):
+    """The FP32 V-cycle is the FP64 V-cycle up to FP32 rounding: norm-wise relative difference
+    below 1e-4 (a few hundred u across ~10 passes per level and the coarse solve)."""
+    A, H = case("p23")
+    p = nsamg.default_params(vcycle_fp32=1, **params_for(smoother))
+    with nsamg.setup_hierarchy(H, p) as h:
+        r = rhs_uniform(A.shape[0], 11)
+        z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h, dev(r), z)
+        want = ovcycle(H, r, oracle_params(p))
+        got = host(z)
+    assert np.linalg.norm(got - want) <= 1e-4 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.JACOBI_L1])
+def test_fp32_vcycle_solve(name, smoother):
+    """Mixed precision: FP32 V-cycle in FP64 flexible GMRES reaches relative residual 1e-8 in
+    FP64, with iterations within +-1 of the FP64 oracle; solved to 1e-12 both ways, x agrees
+    with the FP64 oracle to 1e-6 relative."""
+    A, H = case(name)
+    p = nsamg.default_params(vcycle_fp32=1, restart=30, **params_for(smoother))
+    op = oracle_params(p)
+    b = rhs_uniform(A.shape[0], 0)
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-8)
+    with nsamg.setup_hierarchy(H, p) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        xs = host(x)
+        assert st["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
+        assert abs(st["iters"] - ref.iters) <= 1
+        x2 = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st2 = nsamg.solve(h, dev(b), x2, rtol=1e-12, maxit=500)
+    ref2 = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-12)
+    assert st2["converged"]
+    assert np.linalg.norm(host(x2) - ref2.x) / np.linalg.norm(ref2.x) <= 1e-6
