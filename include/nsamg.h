@@ -169,6 +169,24 @@ int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, 
 int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out,
                        void* stream);
 
+/* ---- batched solves of many independent systems ----------------------------------------
+ * nsamg_batch_setup: `count` host hierarchies with the same number of levels (and either all or
+ * none with a coarse dense inverse) are concatenated block-diagonally: system s owns rows
+ * [off_s, off_s + n_s) of every concatenated vector (nsamg_batch_offsets returns the count+1
+ * offsets). Every V-cycle kernel then covers all systems in one launch; GMRES runs in lock step
+ * with a separate state per system (its own beta, L, Hessenberg/Givens and stopping), each
+ * system stopping on its own test. The returned handle works with nsamg_apply_vcycle and
+ * nsamg_batch_solve (not nsamg_solve). Errors as nsamg_setup_hierarchy; INVALID_ARG if the
+ * depths differ or the total row count exceeds INT32_MAX.
+ * nsamg_batch_solve: d_b, d_x are the concatenated device vectors (x0 in, x out); `stats` (may
+ * be NULL) receives `count` entries. Returns OK if every system converged, NOT_CONVERGED if some
+ * did not, or the first error. Blocks until done. */
+int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_params* p, void* cuda_stream,
+                      nsamg_handle** out);
+int nsamg_batch_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats);
+int nsamg_batch_count(nsamg_handle* h);
+int nsamg_batch_offsets(nsamg_handle* h, int64_t* out);
+
 /* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
 int nsamg_level_group(nsamg_handle* h, int level);
 

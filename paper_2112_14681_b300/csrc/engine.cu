@@ -13,6 +13,9 @@
 #include "nsamg.h"
 #include "kernels.cuh"
 #include "gmres.cuh"
+#include "batch.cuh"
+#include <functional>
+#include <deque>
 
 using namespace nsamg;
 
@@ -255,6 +258,33 @@ struct nsamg_handle {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int launches_per_step = 0;
+  struct BatchData* batch = nullptr;  // set for handles made by nsamg_batch_setup
+};
+
+// Batched solve data: systems concatenated block-diagonally (system s owns rows off[s]..off[s+1]
+// of every concatenated vector), per-system GMRES states and per-kernel block tables.
+struct BatchData {
+  int nsys = 0;
+  std::vector<int64_t> off;       // host copy of the row offsets
+  int64_t* d_off = nullptr;
+  GState* d_st = nullptr;
+  GState* h_st = nullptr;         // pinned
+  BatchCtl* d_ctl = nullptr;
+  BatchCtl* h_ctl = nullptr;      // pinned
+  enum { kGram = 0, kUpdate = 1, kX = 2, kResid = 3 };
+  int64_t rpb[4] = {8192, 2048, 2048, 256};
+  int* d_bstart[4] = {nullptr, nullptr, nullptr, nullptr};
+  int nblocks[4] = {0, 0, 0, 0};
+  unsigned* d_sticket = nullptr;  // nsys per kernel kind (4 * nsys)
+  unsigned* d_gticket = nullptr;  // 4
+  double* partials = nullptr;
+  // coarse dense blocks (all systems), row -> system map
+  int ncrows = 0;
+  int* d_row_sys = nullptr;
+  int64_t* d_coff = nullptr;
+  int64_t* d_cblk = nullptr;
+  double* d_cinv = nullptr;
+  float* d_cinv32 = nullptr;
 };
 
 namespace {
@@ -459,10 +489,19 @@ void smooth(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, bool backward, boo
 inline const double* coarse_ptr(nsamg_handle* h, double*) { return h->coarse_inv; }
 inline const float* coarse_ptr(nsamg_handle* h, float*) { return h->coarse_inv32; }
 
+inline const double* bcoarse_ptr(BatchData* B, double*) { return B->d_cinv; }
+inline const float* bcoarse_ptr(BatchData* B, float*) { return B->d_cinv32; }
+
 template <typename T>
 void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c) {
   const T* C = coarse_ptr(h, (T*)nullptr);
-  if (C) {
+  if (h->batch && bcoarse_ptr(h->batch, (T*)nullptr)) {
+    BatchData* B = h->batch;
+    ++g_launches;
+    const int nb = (B->ncrows * 32 + kThreads - 1) / kThreads;
+    k_bdense_gemv<T, T><<<nb, kThreads, 0, c.s>>>(B->ncrows, B->d_row_sys, B->d_coff, B->d_cblk,
+                                                  bcoarse_ptr(B, (T*)nullptr), b, x, c.skip);
+  } else if (C) {
     ++g_launches;
     const int nb = (L.n * 32 + kThreads - 1) / kThreads;
     k_dense_gemv<T, T><<<nb, kThreads, 0, c.s>>>(L.n, C, b, x, c.skip);
@@ -638,7 +677,13 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   }
 }
 
-int build_graph(nsamg_handle* h) {
+using ResidFn = std::function<void(cudaStream_t, int, unsigned long long, unsigned long long)>;
+using StepFn = std::function<void(cudaStream_t, unsigned long long)>;
+using XFn = std::function<void(cudaStream_t)>;
+
+// One CUDA graph per solve: init residual -> WHILE(outer) { WHILE(inner) { step }, x-update,
+// residual }. Kernels set the two conditions from the device.
+int build_graph_fn(nsamg_handle* h, const ResidFn& enq_resid, const StepFn& enq_step, const XFn& enq_x) {
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
@@ -646,7 +691,7 @@ int build_graph(nsamg_handle* h) {
   cudaGraphConditionalHandle hout, hin;
   CK(cudaGraphConditionalHandleCreate(&hout, g, 0, 0));
   CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  enqueue_resid(h, cs, 1, (unsigned long long)hout, 0ull);
+  enq_resid(cs, 1, (unsigned long long)hout, 0ull);
   CK(cudaStreamEndCapture(cs, &g));
   size_t nn = 0;
   CK(cudaGraphGetNodes(g, nullptr, &nn));
@@ -671,17 +716,109 @@ int build_graph(nsamg_handle* h) {
   cudaGraph_t inner_body = ip.conditional.phGraph_out[0];
   CK(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const int64_t before = g_launches;
-  enqueue_step(h, cs, (unsigned long long)hin);
+  enq_step(cs, (unsigned long long)hin);
   h->launches_per_step = (int)(g_launches - before);
   CK(cudaStreamEndCapture(cs, &inner_body));
   CK(cudaStreamBeginCaptureToGraph(cs, outer_body, &inner, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  enqueue_xupdate(h, cs);
-  enqueue_resid(h, cs, 0, (unsigned long long)hout, (unsigned long long)hin);
+  enq_x(cs);
+  enq_resid(cs, 0, (unsigned long long)hout, (unsigned long long)hin);
   CK(cudaStreamEndCapture(cs, &outer_body));
   CK(cudaGraphInstantiate(&h->exec, g, 0));
   h->graph = g;
   cudaStreamDestroy(cs);
   return NSAMG_OK;
+}
+
+int build_graph(nsamg_handle* h) {
+  return build_graph_fn(
+      h, [h](cudaStream_t s, int init, unsigned long long co, unsigned long long ci) { enqueue_resid(h, s, init, co, ci); },
+      [h](cudaStream_t s, unsigned long long ci) { enqueue_step(h, s, ci); }, [h](cudaStream_t s) { enqueue_xupdate(h, s); });
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched solve: one lock-step Arnoldi step for all systems, x-update, residual.
+// ------------------------------------------------------------------------------------------
+BatchArgs batch_args(nsamg_handle* h, int kind, unsigned long long co, unsigned long long ci) {
+  BatchData* B = h->batch;
+  BatchArgs a{};
+  a.nsys = B->nsys;
+  a.off = B->d_off;
+  a.bstart = B->d_bstart[kind];
+  a.rpb = B->rpb[kind];
+  a.st = B->d_st;
+  a.ctl = B->d_ctl;
+  a.V = h->V;
+  a.ldv = h->ld;
+  a.w = h->w;
+  a.partials = B->partials;
+  a.sticket = B->d_sticket + (int64_t)kind * B->nsys;
+  a.gticket = B->d_gticket + kind;
+  a.cond_outer = co;
+  a.cond_inner = ci;
+  return a;
+}
+
+void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner) {
+  BatchData* B = h->batch;
+  const int* sel = &B->d_ctl->gi;
+  Ctx c{s, nullptr};
+  VRef<const double> b;
+  b.p = h->V;
+  b.sel = sel;
+  b.ld = h->ld;
+  if (!h->fp32) {
+    VRef<double> z;
+    z.p = h->Z;
+    z.sel = sel;
+    z.ld = h->ld;
+    vcycle(h, h->lv, 0, b, z, c);
+    auto op = op_mat(h->lv[0].A, cref(z));
+    op.out = vref(h->w);
+    run(op, h->lv[0].A.G, c);
+  } else {
+    Level<float>& L0 = h->lv32[0];
+    ++g_launches;
+    k_cast<double, float><<<8 * 148, kThreads, 0, s>>>(h->n, b, vref(L0.b), nullptr);
+    VRef<float> z;
+    z.p = h->Z32;
+    z.sel = sel;
+    z.ld = h->ld;
+    vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
+    const auto& A = h->lv[0].A;
+    RowOp<double, float, double> op;
+    op.n = A.n;
+    op.rp = A.rp;
+    op.ci = A.ci;
+    op.v = A.v;
+    op.src = cref(z);
+    op.out = vref(h->w);
+    launch_row(op, A.G, s);
+  }
+  g_launches += 2;
+  k_bgram<<<B->nblocks[BatchData::kGram], kGramThreads, 0, s>>>(batch_args(h, BatchData::kGram, 0, 0));
+  k_bupdate<<<B->nblocks[BatchData::kUpdate], kRedThreads, 0, s>>>(batch_args(h, BatchData::kUpdate, 0, cond_inner));
+}
+
+void enqueue_bxupdate(nsamg_handle* h, cudaStream_t s) {
+  BatchData* B = h->batch;
+  ++g_launches;
+  if (h->fp32)
+    k_bxupdate<float><<<B->nblocks[BatchData::kX], kRedThreads, 0, s>>>(batch_args(h, BatchData::kX, 0, 0), h->Z32, h->ld);
+  else
+    k_bxupdate<double><<<B->nblocks[BatchData::kX], kRedThreads, 0, s>>>(batch_args(h, BatchData::kX, 0, 0), h->Z, h->ld);
+}
+
+void enqueue_bresid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
+  BatchData* B = h->batch;
+  const auto& A = h->lv[0].A;
+  BResidArgs ra{};
+  ra.ba = batch_args(h, BatchData::kResid, co, ci);
+  ra.rp = A.rp;
+  ra.ci = A.ci;
+  ra.v = A.v;
+  ra.init = init;
+  ++g_launches;
+  k_bresid<<<B->nblocks[BatchData::kResid], kRedThreads, 0, s>>>(ra);
 }
 
 int check_params(const nsamg_params& p) {
@@ -784,7 +921,18 @@ void release_levels(std::vector<Level<T>>& lvs) {
   lvs.clear();
 }
 
-int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stream, nsamg_handle* h) {
+// Host-side description of a batch (concatenated systems) handed to setup_impl.
+struct BatchInit {
+  std::vector<int64_t> off;          // nsys + 1 finest-level row offsets
+  std::vector<int64_t> coff;         // nsys + 1 coarsest-level row offsets
+  std::vector<int64_t> cblk;         // nsys offsets of each dense inverse block
+  std::vector<double> cinv;          // all dense inverse blocks (row-major), empty if none
+};
+
+int setup_batch_data(nsamg_handle* h, const BatchInit& bi);
+
+int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stream, nsamg_handle* h,
+               const BatchInit* bi = nullptr) {
   nsamg_params p;
   nsamg_default_params(&p);
   if (pp) p = *pp;
@@ -857,6 +1005,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
+  if (bi && (rc = setup_batch_data(h, *bi))) return rc;
   // Threads per row: fixed by the caller or tuned on the device.
   if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, h->stream))) return rc;
   if (h->fp32) {
@@ -864,7 +1013,25 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, h->stream))) return rc;
   }
   CK(cudaStreamSynchronize(h->stream));
-  if (p.use_graph) {
+  if (h->batch) {
+    if (p.use_graph) {
+      rc = build_graph_fn(
+          h, [h](cudaStream_t s, int init, unsigned long long co, unsigned long long ci) { enqueue_bresid(h, s, init, co, ci); },
+          [h](cudaStream_t s, unsigned long long ci) { enqueue_bstep(h, s, ci); }, [h](cudaStream_t s) { enqueue_bxupdate(h, s); });
+      if (rc) return rc;
+    } else {
+      cudaGraph_t tmp;
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      const int64_t before = g_launches;
+      enqueue_bstep(h, cs, 0ull);
+      h->launches_per_step = (int)(g_launches - before);
+      CK(cudaStreamEndCapture(cs, &tmp));
+      cudaGraphDestroy(tmp);
+      cudaStreamDestroy(cs);
+    }
+  } else if (p.use_graph) {
     if ((rc = build_graph(h))) return rc;
   } else {  // count the launches of one step without running it
     cudaGraph_t tmp;
@@ -882,10 +1049,191 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   return NSAMG_OK;
 }
 
+template <typename T>
+int upload_raw(const std::vector<T>& hv, T** d) {
+  CK(cudaMalloc(d, sizeof(T) * std::max<size_t>(hv.size(), 1)));
+  if (!hv.empty()) CK(cudaMemcpy(*d, hv.data(), sizeof(T) * hv.size(), cudaMemcpyHostToDevice));
+  return NSAMG_OK;
+}
+
+int setup_batch_data(nsamg_handle* h, const BatchInit& bi) {
+  int rc;
+  BatchData* B = new BatchData();
+  h->batch = B;
+  B->nsys = (int)bi.off.size() - 1;
+  B->off = bi.off;
+  if ((rc = upload_raw(bi.off, &B->d_off))) return rc;
+  int64_t maxpart = 0;
+  for (int k = 0; k < 4; ++k) {
+    std::vector<int> bs(B->nsys + 1, 0);
+    for (int sI = 0; sI < B->nsys; ++sI) {
+      const int64_t n = bi.off[sI + 1] - bi.off[sI];
+      bs[sI + 1] = bs[sI] + (int)std::max<int64_t>(1, (n + B->rpb[k] - 1) / B->rpb[k]);
+    }
+    B->nblocks[k] = bs[B->nsys];
+    if ((rc = upload_raw(bs, &B->d_bstart[k]))) return rc;
+    const int64_t per = (k == BatchData::kGram) ? 2 * (kMaxM + 1) : 2;
+    maxpart = std::max<int64_t>(maxpart, per * B->nblocks[k]);
+  }
+  CK(cudaMalloc(&B->partials, sizeof(double) * maxpart));
+  CK(cudaMalloc(&B->d_sticket, sizeof(unsigned) * 4 * B->nsys));
+  CK(cudaMemset(B->d_sticket, 0, sizeof(unsigned) * 4 * B->nsys));
+  CK(cudaMalloc(&B->d_gticket, sizeof(unsigned) * 4));
+  CK(cudaMemset(B->d_gticket, 0, sizeof(unsigned) * 4));
+  CK(cudaMalloc(&B->d_st, sizeof(GState) * B->nsys));
+  CK(cudaMemset(B->d_st, 0, sizeof(GState) * B->nsys));
+  CK(cudaMallocHost(&B->h_st, sizeof(GState) * B->nsys));
+  CK(cudaMalloc(&B->d_ctl, sizeof(BatchCtl)));
+  CK(cudaMemset(B->d_ctl, 0, sizeof(BatchCtl)));
+  CK(cudaMallocHost(&B->h_ctl, sizeof(BatchCtl)));
+  if (!bi.cinv.empty()) {
+    B->ncrows = (int)bi.coff.back();
+    std::vector<int> rs(B->ncrows);
+    for (int sI = 0; sI < B->nsys; ++sI)
+      for (int64_t r = bi.coff[sI]; r < bi.coff[sI + 1]; ++r) rs[r] = sI;
+    if ((rc = upload_raw(rs, &B->d_row_sys))) return rc;
+    if ((rc = upload_raw(bi.coff, &B->d_coff))) return rc;
+    if ((rc = upload_raw(bi.cblk, &B->d_cblk))) return rc;
+    if (h->fp32) {
+      std::vector<float> c32(bi.cinv.begin(), bi.cinv.end());
+      if ((rc = upload_raw(c32, &B->d_cinv32))) return rc;
+    } else {
+      if ((rc = upload_raw(bi.cinv, &B->d_cinv))) return rc;
+    }
+  }
+  return NSAMG_OK;
+}
+
+void destroy_batch(BatchData* B) {
+  if (!B) return;
+  cudaFree(B->d_off);
+  for (int k = 0; k < 4; ++k) cudaFree(B->d_bstart[k]);
+  cudaFree(B->partials);
+  cudaFree(B->d_sticket);
+  cudaFree(B->d_gticket);
+  cudaFree(B->d_st);
+  if (B->h_st) cudaFreeHost(B->h_st);
+  cudaFree(B->d_ctl);
+  if (B->h_ctl) cudaFreeHost(B->h_ctl);
+  cudaFree(B->d_row_sys);
+  cudaFree(B->d_coff);
+  cudaFree(B->d_cblk);
+  cudaFree(B->d_cinv);
+  cudaFree(B->d_cinv32);
+  delete B;
+}
+
+// Concatenate equal-depth hierarchies into one block-diagonal hierarchy (host), keeping the
+// arrays alive in `store`.
+struct ConcatStore {  // deques: references to earlier arrays stay valid while more are added
+  std::deque<std::vector<int>> ints;
+  std::deque<std::vector<double>> dbls;
+  std::vector<nsamg_level_desc> levels;
+};
+
+nsamg_csr concat_csr(const std::vector<const nsamg_csr*>& parts, ConcatStore& store) {
+  int64_t nr = 0, nc = 0, nnz = 0;
+  for (auto* c : parts) {
+    nr += c->nrows;
+    nc += c->ncols;
+    nnz += c->nnz;
+  }
+  store.ints.emplace_back();
+  std::vector<int>& rp = store.ints.back();
+  store.ints.emplace_back();
+  std::vector<int>& ci = store.ints.back();
+  store.dbls.emplace_back();
+  std::vector<double>& v = store.dbls.back();
+  rp.reserve(nr + 1);
+  ci.reserve(nnz);
+  v.reserve(nnz);
+  rp.push_back(0);
+  int64_t roff = 0, coff = 0;
+  for (auto* c : parts) {
+    for (int i = 0; i < c->nrows; ++i) {
+      for (int64_t q = c->rowptr[i]; q < c->rowptr[i + 1]; ++q) {
+        ci.push_back((int)(c->col[q] + coff));
+        v.push_back(c->val[q]);
+      }
+      rp.push_back((int)ci.size());
+    }
+    roff += c->nrows;
+    coff += c->ncols;
+  }
+  nsamg_csr out{};
+  out.nrows = (int32_t)nr;
+  out.ncols = (int32_t)nc;
+  out.nnz = nnz;
+  out.rowptr = rp.data();
+  out.col = ci.data();
+  out.val = v.data();
+  return out;
+}
+
+int solve_batch_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
+  if (!h || !h->batch || !d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument or not a batch handle");
+  if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
+  CK(cudaSetDevice(h->device));
+  BatchData* B = h->batch;
+  cudaStream_t s = h->stream;
+  BatchCtl* c = B->h_ctl;
+  std::memset(c, 0, sizeof(BatchCtl));
+  c->b = d_b;
+  c->x = d_x;
+  c->rtol = rtol;
+  c->maxit = maxit;
+  c->m = h->m;
+  c->t_exact = h->p.t_exact;
+  CK(cudaMemcpyAsync(B->d_ctl, c, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+  if (h->exec) {
+    CK(cudaGraphLaunch(h->exec, s));
+  } else {
+    enqueue_bresid(h, s, 1, 0, 0);
+    for (int cycle = 0; cycle <= maxit + 1; ++cycle) {
+      CK(cudaMemcpyAsync(c, B->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (c->running == 0) break;
+      for (int i = 0; i < h->m; ++i) {
+        const int gi_before = i;
+        enqueue_bstep(h, s, 0);
+        CK(cudaMemcpyAsync(c, B->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (c->active == 0 || c->gi == gi_before) break;  // all stopped, or the step did not advance
+      }
+      enqueue_bxupdate(h, s);
+      enqueue_bresid(h, s, 0, 0, 0);
+    }
+  }
+  CK(cudaMemcpyAsync(B->h_st, B->d_st, sizeof(GState) * B->nsys, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  int worst = NSAMG_OK;
+  for (int sI = 0; sI < B->nsys; ++sI) {
+    const GState& g = B->h_st[sI];
+    int status = g.status;
+    if (status == 0 && !g.converged) status = NSAMG_NOT_CONVERGED;
+    if (stats) {
+      stats[sI].iters = g.iters;
+      stats[sI].restarts = std::max(0, g.cycles - 1);
+      stats[sI].converged = g.converged;
+      stats[sI].status = status;
+      stats[sI].relres_true = g.relres_true;
+      stats[sI].relres_implicit = g.relres_implicit;
+      stats[sI].bnorm = g.bnorm;
+    }
+    if (status < 0) worst = status;
+    else if (status == NSAMG_NOT_CONVERGED && worst == NSAMG_OK) worst = NSAMG_NOT_CONVERGED;
+  }
+  if (worst < 0) return fail(worst, "a system of the batch failed (see its stats)");
+  return worst;
+}
+
 void destroy_impl(nsamg_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_batch(h->batch);
+  h->batch = nullptr;
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   release_levels(h->lv);
@@ -978,6 +1326,7 @@ int noalloc_scratch(Scratch* out, int* blocks) {
 
 int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
   if (!h || !d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  if (h->batch) return fail(NSAMG_ERR_INVALID_ARG, "batch handle: use nsamg_batch_solve");
   if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
   CK(cudaSetDevice(h->device));
   cudaStream_t s = h->stream;
@@ -1307,6 +1656,99 @@ int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, 
   ua.scr.ticket = scr.ticket + 1;
   k_update<<<8 * sms, kRedThreads, 0, (cudaStream_t)stream>>>(ua);
   CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_params* p, void* cuda_stream,
+                      nsamg_handle** out) {
+  if (!out) return fail(NSAMG_ERR_INVALID_ARG, "null output handle pointer");
+  *out = nullptr;
+  if (!hs || count < 1) return fail(NSAMG_ERR_INVALID_ARG, "empty batch");
+  const int nl = hs[0].nlevels;
+  int with_inv = 0;
+  for (int sI = 0; sI < count; ++sI) {
+    if (hs[sI].nlevels != nl || nl < 1 || !hs[sI].levels)
+      return fail(NSAMG_ERR_INVALID_ARG, "batch: every system needs the same number of levels");
+    with_inv += hs[sI].coarse_inv ? 1 : 0;
+  }
+  if (with_inv != 0 && with_inv != count)
+    return fail(NSAMG_ERR_INVALID_ARG, "batch: give a coarse inverse for every system or for none");
+  ConcatStore store;
+  store.levels.resize(nl);
+  BatchInit bi;
+  bi.off.push_back(0);
+  bi.coff.push_back(0);
+  for (int sI = 0; sI < count; ++sI) {
+    bi.off.push_back(bi.off.back() + hs[sI].levels[0].A.nrows);
+    const int nc = hs[sI].levels[nl - 1].A.nrows;
+    bi.coff.push_back(bi.coff.back() + nc);
+    if (with_inv) {
+      bi.cblk.push_back((int64_t)bi.cinv.size());
+      bi.cinv.insert(bi.cinv.end(), hs[sI].coarse_inv, hs[sI].coarse_inv + (size_t)nc * nc);
+    }
+  }
+  if (bi.off.back() > INT32_MAX) return fail(NSAMG_ERR_INVALID_ARG, "batch too large for int32 indices");
+  for (int l = 0; l < nl; ++l) {
+    std::vector<const nsamg_csr*> A, P, R, iL, iU;
+    bool has_ilu = true;
+    for (int sI = 0; sI < count; ++sI) {
+      const nsamg_level_desc& D = hs[sI].levels[l];
+      A.push_back(&D.A);
+      if (l < nl - 1) {
+        P.push_back(&D.P);
+        R.push_back(&D.R);
+      }
+      has_ilu = has_ilu && D.ilu_L.nrows > 0 && D.ilu_dinv;
+      iL.push_back(&D.ilu_L);
+      iU.push_back(&D.ilu_U);
+    }
+    nsamg_level_desc& O = store.levels[l];
+    O = nsamg_level_desc{};
+    O.A = concat_csr(A, store);
+    if (l < nl - 1) {
+      O.P = concat_csr(P, store);
+      O.R = concat_csr(R, store);
+    }
+    if (has_ilu) {
+      O.ilu_L = concat_csr(iL, store);
+      O.ilu_U = concat_csr(iU, store);
+      store.dbls.emplace_back();
+      auto& d = store.dbls.back();
+      for (int sI = 0; sI < count; ++sI) {
+        const nsamg_level_desc& D = hs[sI].levels[l];
+        d.insert(d.end(), D.ilu_dinv, D.ilu_dinv + D.A.nrows);
+      }
+      O.ilu_dinv = d.data();
+    }
+  }
+  nsamg_hierarchy_desc H{};
+  H.nlevels = nl;
+  H.levels = store.levels.data();
+  H.coarse_inv = nullptr;
+  nsamg_handle* h = new nsamg_handle();
+  const int rc = setup_impl(&H, p, cuda_stream, h, &bi);
+  if (rc != NSAMG_OK) {
+    std::string keep = g_err;
+    destroy_impl(h);
+    g_err = keep;
+    return rc;
+  }
+  *out = h;
+  return NSAMG_OK;
+}
+
+int nsamg_batch_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
+  return solve_batch_impl(h, d_b, d_x, rtol, maxit, stats);
+}
+
+int nsamg_batch_count(nsamg_handle* h) {
+  if (!h || !h->batch) return fail(NSAMG_ERR_INVALID_ARG, "not a batch handle");
+  return h->batch->nsys;
+}
+
+int nsamg_batch_offsets(nsamg_handle* h, int64_t* out) {
+  if (!h || !h->batch || !out) return fail(NSAMG_ERR_INVALID_ARG, "not a batch handle");
+  std::copy(h->batch->off.begin(), h->batch->off.end(), out);
   return NSAMG_OK;
 }
 

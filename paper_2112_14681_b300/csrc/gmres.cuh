@@ -84,6 +84,11 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
   const int i = st ? st->i : a.i_standalone;
   const int ncol = i + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Warps form C column groups x R row groups (C * R = 16) so that all warps (and all four SM
+  // sub-partitions' FP64 units) stay busy whatever the number of columns.
+  const int C = ncol <= 1 ? 1 : ncol <= 2 ? 2 : ncol <= 4 ? 4 : ncol <= 8 ? 8 : 16;
+  const int R = kGramWarps / C;
+  const int cg = warp % C, rg = warp / C;
   const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + kGramTile - 1) / kGramTile * kGramTile;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(a.n, r0 + chunk);
@@ -101,16 +106,18 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < kGramSlots; ++s) {
-      const int j = warp + s * kGramWarps;
+      const int j = cg + s * C;
+      if (j > i) break;
       if (j < i) {
         const double* vj = a.V + (int64_t)j * a.ldv + t0;
-        for (int r = lane; r < tn; r += 32) {
+#pragma unroll 2
+        for (int r = lane + 32 * rg; r < tn; r += 32 * R) {
           const double x = __ldcs(vj + r);
           acc_a[s] = fma(x, s_vt[r], acc_a[s]);
           acc_s[s] = fma(x, s_w[r], acc_s[s]);
         }
-      } else if (j == i) {
-        for (int r = lane; r < tn; r += 32) {
+      } else {
+        for (int r = lane + 32 * rg; r < tn; r += 32 * R) {
           const double x = s_vt[r];
           acc_a[s] = fma(x, x, acc_a[s]);
           acc_s[s] = fma(x, s_w[r], acc_s[s]);
@@ -119,9 +126,10 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
     }
   }
   const int stride = 2 * (kMaxM + 1);
+  __shared__ double s_part[kGramWarps][2 * (kMaxM + 1)];
 #pragma unroll
   for (int s = 0; s < kGramSlots; ++s) {
-    const int j = warp + s * kGramWarps;
+    const int j = cg + s * C;
     if (j > i) break;
     double va = acc_a[s], vs = acc_s[s];
 #pragma unroll
@@ -130,9 +138,16 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
       vs += __shfl_xor_sync(0xffffffffu, vs, o);
     }
     if (lane == 0) {
-      a.scr.partials[(int64_t)blockIdx.x * stride + j] = va;
-      a.scr.partials[(int64_t)blockIdx.x * stride + (kMaxM + 1) + j] = vs;
+      s_part[rg][j] = va;
+      s_part[rg][kMaxM + 1 + j] = vs;
     }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < 2 * ncol; v += blockDim.x) {
+    const int col = v < ncol ? v : (kMaxM + 1) + (v - ncol);
+    double sum = 0.0;
+    for (int g = 0; g < R; ++g) sum += s_part[g][col];
+    a.scr.partials[(int64_t)blockIdx.x * stride + col] = sum;
   }
   if (!last_block(a.scr.ticket)) return;
   // red[0..i] = a, red[kMaxM+1 .. kMaxM+1+i] = s
@@ -249,6 +264,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(UpdateArgs a) {
     const double v = __ldcs(vi + r) * invb;
     vi[r] = v;
     double acc = fma(-hi, v, __ldcs(a.w + r) * invb);
+#pragma unroll 8
     for (int j = 0; j < i; ++j) acc = fma(-s_h[j], __ldcs(a.V + (int64_t)j * a.ldv + r), acc);
     vn[r] = acc;
     ss = fma(acc, acc, ss);

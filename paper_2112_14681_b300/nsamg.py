@@ -58,7 +58,7 @@ EXPORTS = [
     "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
     "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
-    "nsamg_gram_noalloc",
+    "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
 ]
 
 _lib = None
@@ -91,6 +91,10 @@ def load(path: str = LIB_PATH):
         "nsamg_gram": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_update": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
         "nsamg_gram_noalloc": (i32, [i64, i32, vp, i64, vp, vp, vp]),
+        "nsamg_batch_setup": (i32, [ctypes.POINTER(HierarchyDesc), i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "nsamg_batch_solve": (i32, [vp, vp, vp, f64, i32, ctypes.POINTER(Stats)]),
+        "nsamg_batch_count": (i32, [vp]),
+        "nsamg_batch_offsets": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "nsamg_destroy": (None, [vp]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
@@ -144,34 +148,53 @@ def _csr_desc(M, keep: list) -> Csr:
     return c
 
 
+def _hierarchy_desc(hierarchy, keep: list) -> HierarchyDesc:
+    levels = hierarchy.levels
+    arr = (LevelDesc * len(levels))()
+    keep.append(arr)
+    for l, lev in enumerate(levels):
+        arr[l].A = _csr_desc(lev.A, keep)
+        arr[l].P = _csr_desc(lev.P, keep)
+        arr[l].R = _csr_desc(lev.R, keep)
+        arr[l].ilu_L = _csr_desc(lev.ilu_L, keep)
+        arr[l].ilu_U = _csr_desc(lev.ilu_U, keep)
+        if lev.ilu_dinv is not None:
+            d = np.ascontiguousarray(lev.ilu_dinv, dtype=np.float64)
+            keep.append(d)
+            arr[l].ilu_dinv = d.ctypes.data
+    desc = HierarchyDesc()
+    desc.nlevels = len(levels)
+    desc.levels = arr
+    if hierarchy.coarse_inv is not None:
+        ci = np.ascontiguousarray(hierarchy.coarse_inv, dtype=np.float64)
+        keep.append(ci)
+        desc.coarse_inv = ci.ctypes.data
+    return desc
+
+
 class Handle:
     """Owns an nsamg handle (device hierarchy + GMRES workspace)."""
 
-    def __init__(self, hierarchy, params: Params | None = None, stream=None):
+    def __init__(self, hierarchy, params: Params | None = None, stream=None, _batch=None):
         lib = load()
         keep: list = []
-        levels = hierarchy.levels
-        arr = (LevelDesc * len(levels))()
-        for l, lev in enumerate(levels):
-            arr[l].A = _csr_desc(lev.A, keep)
-            arr[l].P = _csr_desc(lev.P, keep)
-            arr[l].R = _csr_desc(lev.R, keep)
-            arr[l].ilu_L = _csr_desc(lev.ilu_L, keep)
-            arr[l].ilu_U = _csr_desc(lev.ilu_U, keep)
-            if lev.ilu_dinv is not None:
-                d = np.ascontiguousarray(lev.ilu_dinv, dtype=np.float64)
-                keep.append(d)
-                arr[l].ilu_dinv = d.ctypes.data
-        desc = HierarchyDesc()
-        desc.nlevels = len(levels)
-        desc.levels = arr
-        if hierarchy.coarse_inv is not None:
-            ci = np.ascontiguousarray(hierarchy.coarse_inv, dtype=np.float64)
-            keep.append(ci)
-            desc.coarse_inv = ci.ctypes.data
         self.params = params or default_params()
-        h = ctypes.c_void_p()
         sptr = None if stream is None else ctypes.c_void_p(stream)
+        h = ctypes.c_void_p()
+        if _batch is not None:  # list of hierarchies -> one batch handle
+            descs = (HierarchyDesc * len(_batch))()
+            for k, hier in enumerate(_batch):
+                descs[k] = _hierarchy_desc(hier, keep)
+            _check(lib.nsamg_batch_setup(descs, len(_batch), ctypes.byref(self.params), sptr, ctypes.byref(h)))
+            self._h = h
+            self.count = len(_batch)
+            off = (ctypes.c_int64 * (self.count + 1))()
+            _check(lib.nsamg_batch_offsets(h, off))
+            self.offsets = np.array(off[:], dtype=np.int64)
+            self.n = int(self.offsets[-1])
+            return
+        levels = hierarchy.levels
+        desc = _hierarchy_desc(hierarchy, keep)
         _check(lib.nsamg_setup_hierarchy(ctypes.byref(desc), ctypes.byref(self.params), sptr, ctypes.byref(h)))
         self._h = h
         self.n = levels[0].A.shape[0]
@@ -196,6 +219,19 @@ class Handle:
 
 def setup_hierarchy(hierarchy, params: Params | None = None, stream=None) -> Handle:
     return Handle(hierarchy, params, stream)
+
+
+def batch_setup(hierarchies, params: Params | None = None, stream=None) -> Handle:
+    """Block-diagonal batch of independent systems (same depth); see nsamg_batch_setup."""
+    return Handle(None, params, stream, _batch=list(hierarchies))
+
+
+def batch_solve(h: Handle, b, x, rtol: float = 1e-8, maxit: int = 1000) -> list:
+    """b, x: concatenated device vectors (system s at rows offsets[s]:offsets[s+1])."""
+    st = (Stats * h.count)()
+    rc = load().nsamg_batch_solve(h._h, _ptr(b), _ptr(x), float(rtol), int(maxit), st)
+    _check(rc, (OK, NOT_CONVERGED))
+    return [s.as_dict() for s in st]
 
 
 def solve(h: Handle, b, x, rtol: float = 1e-8, maxit: int = 1000) -> dict:
