@@ -187,6 +187,33 @@ int nsamg_batch_solve(nsamg_handle* h, const double* d_b, double* d_x, double rt
 int nsamg_batch_count(nsamg_handle* h);
 int nsamg_batch_offsets(nsamg_handle* h, int64_t* out);
 
+/* ---- request server (continuous batching of solves on resident hierarchies) -------------
+ * nsamg_server_create: a server for the current device with a device-memory budget (bytes) for
+ * solver contexts and at most `max_slots` solves in flight. A worker thread admits queued
+ * requests in arrival order as soon as a slot is free and a context for the request's
+ * hierarchy fits the budget (idle contexts are reused, least recently used idle contexts of
+ * other hierarchies are evicted); solves of different slots run concurrently on their own
+ * streams, each as one CUDA graph. Hierarchies stay owned by the caller and must outlive the
+ * server's use of them; they must be set up with use_graph = 1.
+ * nsamg_server_submit: queue a solve of A x = b (device arrays, valid until the request
+ * completes); returns a ticket. `ready_stream` (a cudaStream_t, NULL = legacy default stream) is
+ * the stream on which b and x0 were produced: the solve starts after the work queued there so far. nsamg_server_poll: NSAMG_PENDING while queued or running, else
+ * the final status (the ticket is then released); `times` (may be NULL) gets submit, start and
+ * completion times in seconds on the server's clock. nsamg_server_wait blocks until done.
+ * nsamg_server_cancel removes a request that has not started. A request whose context can never
+ * fit the budget completes with NSAMG_ERR_ADMISSION. nsamg_server_info: bytes in use, contexts,
+ * running, queued. nsamg_server_destroy drops queued requests, waits for running ones and frees
+ * every context. */
+typedef struct nsamg_server nsamg_server;
+int nsamg_server_create(size_t hbm_budget_bytes, int max_slots, nsamg_server** out);
+int nsamg_server_submit(nsamg_server* s, nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit,
+                        void* ready_stream, uint64_t* ticket);
+int nsamg_server_poll(nsamg_server* s, uint64_t ticket, nsamg_stats* st, double* times);
+int nsamg_server_wait(nsamg_server* s, uint64_t ticket, nsamg_stats* st, double* times);
+int nsamg_server_cancel(nsamg_server* s, uint64_t ticket);
+int nsamg_server_info(nsamg_server* s, int64_t* out4);
+void nsamg_server_destroy(nsamg_server* s);
+
 /* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
 int nsamg_level_group(nsamg_handle* h, int level);
 

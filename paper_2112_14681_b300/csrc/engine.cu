@@ -16,6 +16,11 @@
 #include "batch.cuh"
 #include <functional>
 #include <deque>
+#include <thread>
+#include <condition_variable>
+#include <chrono>
+#include <unordered_map>
+#include <atomic>
 
 using namespace nsamg;
 
@@ -259,6 +264,8 @@ struct nsamg_handle {
   cudaGraph_t graph = nullptr;
   int launches_per_step = 0;
   struct BatchData* batch = nullptr;  // set for handles made by nsamg_batch_setup
+  bool shared_mats = false;           // a solver context: matrices belong to another handle
+  size_t ctx_bytes = 0;               // device bytes of the per-solve workspace (server accounting)
 };
 
 // Batched solve data: systems concatenated block-diagonally (system s owns rows off[s]..off[s+1]
@@ -911,6 +918,15 @@ int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaS
 }
 
 template <typename T>
+void release_level_vectors(std::vector<Level<T>>& lvs) {
+  for (auto& L : lvs) {
+    T* vecs[] = {L.b, L.x, L.r, L.t1, L.t2, L.t3};
+    for (T* v : vecs) cudaFree(v);
+  }
+  lvs.clear();
+}
+
+template <typename T>
 void release_levels(std::vector<Level<T>>& lvs) {
   for (auto& L : lvs) {
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
@@ -919,6 +935,55 @@ void release_levels(std::vector<Level<T>>& lvs) {
     for (T* v : vecs) cudaFree(v);
   }
   lvs.clear();
+}
+
+// GMRES workspace of a handle or solver context: V (m+1 columns), Z (m columns), w, the device
+// state and reduction scratch; leading dimension padded to 64 entries.
+int alloc_workspace(nsamg_handle* h) {
+  int rc;
+  h->n = h->lv[0].n;
+  h->m = h->p.restart;
+  h->ld = ((int64_t)h->n + 63) / 64 * 64;
+  if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
+  if (h->fp32) {
+    if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
+  } else {
+    if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
+  }
+  if ((rc = alloc_vec(&h->w, h->ld))) return rc;
+  CK(cudaMalloc(&h->st, sizeof(GState)));
+  CK(cudaMemset(h->st, 0, sizeof(GState)));
+  CK(cudaMallocHost(&h->h_st, sizeof(GState)));
+  int sms = 148;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->gram_blocks = 2 * sms;
+  h->update_blocks = 8 * sms;
+  const int resid_blocks = blocks_for((int64_t)h->n * 32);
+  h->partial_cap = std::max<int64_t>({(int64_t)h->gram_blocks * 2 * (kMaxM + 1), (int64_t)h->update_blocks,
+                                      2 * (int64_t)resid_blocks});
+  CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
+  CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
+  CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
+  h->ctx_bytes = sizeof(double) * h->ld * (h->m + 2) + (h->fp32 ? sizeof(float) : sizeof(double)) * h->ld * h->m +
+                 sizeof(GState) + sizeof(double) * h->partial_cap;
+  return NSAMG_OK;
+}
+
+int finish_graph(nsamg_handle* h) {
+  if (!h->p.use_graph) {  // count the launches of one step without running it
+    cudaGraph_t tmp;
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = g_launches;
+    enqueue_step(h, cs, 0ull);
+    h->launches_per_step = (int)(g_launches - before);
+    CK(cudaStreamEndCapture(cs, &tmp));
+    cudaGraphDestroy(tmp);
+    cudaStreamDestroy(cs);
+    return NSAMG_OK;
+  }
+  return build_graph(h);
 }
 
 // Host-side description of a batch (concatenated systems) handed to setup_impl.
@@ -930,6 +995,7 @@ struct BatchInit {
 };
 
 int setup_batch_data(nsamg_handle* h, const BatchInit& bi);
+void destroy_impl(nsamg_handle* h);
 
 int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stream, nsamg_handle* h,
                const BatchInit* bi = nullptr) {
@@ -981,30 +1047,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
       CK(cudaMemcpy(h->coarse_inv, H->coarse_inv, sizeof(double) * nc2, cudaMemcpyHostToDevice));
     }
   }
-  // GMRES workspace: V (m+1 columns), Z (m columns), w; leading dimension padded to 64 entries.
-  h->n = h->lv[0].n;
-  h->m = p.restart;
-  h->ld = ((int64_t)h->n + 63) / 64 * 64;
-  if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
-  if (h->fp32) {
-    if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
-  } else {
-    if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
-  }
-  if ((rc = alloc_vec(&h->w, h->ld))) return rc;
-  CK(cudaMalloc(&h->st, sizeof(GState)));
-  CK(cudaMemset(h->st, 0, sizeof(GState)));
-  CK(cudaMallocHost(&h->h_st, sizeof(GState)));
-  int sms = 148;
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  h->gram_blocks = 2 * sms;
-  h->update_blocks = 8 * sms;
-  const int resid_blocks = blocks_for((int64_t)h->n * 32);
-  h->partial_cap = std::max<int64_t>({(int64_t)h->gram_blocks * 2 * (kMaxM + 1), (int64_t)h->update_blocks,
-                                      2 * (int64_t)resid_blocks});
-  CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
-  CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
-  CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
+  if ((rc = alloc_workspace(h))) return rc;
   if (bi && (rc = setup_batch_data(h, *bi))) return rc;
   // Threads per row: fixed by the caller or tuned on the device.
   if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, h->stream))) return rc;
@@ -1031,21 +1074,60 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
       cudaGraphDestroy(tmp);
       cudaStreamDestroy(cs);
     }
-  } else if (p.use_graph) {
-    if ((rc = build_graph(h))) return rc;
-  } else {  // count the launches of one step without running it
-    cudaGraph_t tmp;
-    cudaStream_t cs;
-    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const int64_t before = g_launches;
-    enqueue_step(h, cs, 0ull);
-    h->launches_per_step = (int)(g_launches - before);
-    CK(cudaStreamEndCapture(cs, &tmp));
-    cudaGraphDestroy(tmp);
-    cudaStreamDestroy(cs);
+  } else {
+    if ((rc = finish_graph(h))) return rc;
   }
   CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+// A solver context for `parent`: shares its (read-only) matrices, coarse inverse and tuned
+// kernel shapes, owns its own level work vectors, GMRES workspace, stream and graph, so several
+// solves on one hierarchy can run concurrently.
+template <typename T>
+int clone_level_vectors(const std::vector<Level<T>>& src, std::vector<Level<T>>& dst) {
+  int rc;
+  dst = src;
+  for (auto& L : dst) {
+    L.b = L.x = L.r = L.t1 = L.t2 = L.t3 = nullptr;
+    if (!L.dinv) continue;  // matrix-only level (FP64 operator of an FP32 handle)
+    T** vecs[] = {&L.b, &L.x, &L.r, &L.t1, &L.t2, &L.t3};
+    for (T** v : vecs)
+      if ((rc = alloc_vec(v, L.n))) return rc;
+  }
+  return NSAMG_OK;
+}
+
+int clone_context(nsamg_handle* parent, nsamg_handle** out) {
+  int rc;
+  *out = nullptr;
+  if (parent->batch) return fail(NSAMG_ERR_INVALID_ARG, "batch handles cannot be served");
+  nsamg_handle* h = new nsamg_handle();
+  h->device = parent->device;
+  h->p = parent->p;
+  h->fp32 = parent->fp32;
+  h->shared_mats = true;
+  h->coarse_inv = parent->coarse_inv;
+  h->coarse_inv32 = parent->coarse_inv32;
+  h->nc = parent->nc;
+  auto bail = [&](int code) {
+    std::string keep = g_err;
+    destroy_impl(h);
+    g_err = keep;
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(NSAMG_ERR_CUDA, "stream"));
+  h->own_stream = true;
+  if ((rc = clone_level_vectors(parent->lv, h->lv))) return bail(rc);
+  if ((rc = clone_level_vectors(parent->lv32, h->lv32))) return bail(rc);
+  if ((rc = alloc_workspace(h))) return bail(rc);
+  size_t vec_bytes = 0;
+  for (auto& L : h->lv) vec_bytes += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
+  for (auto& L : h->lv32) vec_bytes += 6 * sizeof(float) * (size_t)L.n;
+  h->ctx_bytes += vec_bytes;
+  if ((rc = finish_graph(h))) return bail(rc);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail(NSAMG_ERR_CUDA, "sync"));
+  *out = h;
   return NSAMG_OK;
 }
 
@@ -1236,10 +1318,15 @@ void destroy_impl(nsamg_handle* h) {
   h->batch = nullptr;
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  release_levels(h->lv);
-  release_levels(h->lv32);
-  cudaFree(h->coarse_inv);
-  cudaFree(h->coarse_inv32);
+  if (h->shared_mats) {
+    release_level_vectors(h->lv);
+    release_level_vectors(h->lv32);
+  } else {
+    release_levels(h->lv);
+    release_levels(h->lv32);
+    cudaFree(h->coarse_inv);
+    cudaFree(h->coarse_inv32);
+  }
   cudaFree(h->V);
   cudaFree(h->Z);
   cudaFree(h->Z32);
@@ -1771,5 +1858,354 @@ const char* nsamg_status_str(int s) {
 }
 
 const char* nsamg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// ==========================================================================================
+// Request server: continuous batching of solves on resident hierarchies.
+//
+// Requests (hierarchy handle, b, x, rtol, maxit) queue in arrival order. A worker thread admits
+// the head of the queue as soon as a slot is free and a solver context for its hierarchy fits in
+// the device-memory budget (idle contexts are reused; idle contexts of other hierarchies are
+// evicted when the budget requires), writes the request into the context's device state and
+// launches the context's solve graph on the context's own stream. Solves of different contexts
+// overlap on the device. Completion is signalled by a host function enqueued after the graph.
+// ==========================================================================================
+struct ServerReq {
+  uint64_t ticket = 0;
+  nsamg_handle* hier = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double rtol = 1e-8;
+  int maxit = 1000;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 cancelled, 4 rejected
+  int status = NSAMG_PENDING;
+  nsamg_stats stats{};
+  nsamg_handle* ctx = nullptr;
+  cudaEvent_t ready = nullptr;  // recorded on the caller's stream at submit: inputs are ready
+};
+
+struct ServerCtx {
+  nsamg_handle* ctx = nullptr;
+  nsamg_handle* hier = nullptr;
+  bool busy = false;
+  uint64_t last_use = 0;
+};
+
+struct nsamg_server {
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 1;
+  size_t used = 0;
+  int running = 0;
+  uint64_t next_ticket = 1;
+  uint64_t use_clock = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, ServerReq> reqs;
+  std::vector<ServerCtx> ctxs;
+  std::vector<uint64_t> finished;  // tickets completed by stream callbacks, not yet processed
+  std::thread worker;
+  bool stop = false;
+  std::chrono::steady_clock::time_point t0;
+  std::string last_error;
+  double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace {
+
+struct DoneMsg {
+  nsamg_server* srv;
+  uint64_t ticket;
+};
+
+void CUDART_CB on_done(void* p) {
+  DoneMsg* m = (DoneMsg*)p;
+  {
+    std::lock_guard<std::mutex> lk(m->srv->mu);
+    m->srv->finished.push_back(m->ticket);
+  }
+  m->srv->cv.notify_all();
+  delete m;
+}
+
+// Finish requests whose graphs completed (called with the lock held).
+void server_collect(nsamg_server* S) {
+  for (uint64_t t : S->finished) {
+    auto it = S->reqs.find(t);
+    if (it == S->reqs.end()) continue;
+    ServerReq& r = it->second;
+    nsamg_handle* h = r.ctx;
+    const GState* g = h->h_st;
+    int status = g->status;
+    if (status == 0 && !g->converged) status = NSAMG_NOT_CONVERGED;
+    r.stats.iters = g->iters;
+    r.stats.restarts = std::max(0, g->cycles - 1);
+    r.stats.converged = g->converged;
+    r.stats.status = status;
+    r.stats.relres_true = g->relres_true;
+    r.stats.relres_implicit = g->relres_implicit;
+    r.stats.bnorm = g->bnorm;
+    r.status = status;
+    r.state = 2;
+    r.t_done = S->now();
+    for (auto& c : S->ctxs)
+      if (c.ctx == h) c.busy = false;
+    S->running -= 1;
+  }
+  S->finished.clear();
+}
+
+// Try to start the request at the head of the queue. Returns true if it started (or was
+// rejected), false if it must wait for a slot or memory.
+bool server_try_start(nsamg_server* S, std::unique_lock<std::mutex>& lk) {
+  if (S->queue.empty() || S->running >= S->max_slots) return false;
+  const uint64_t t = S->queue.front();
+  ServerReq& r = S->reqs[t];
+  if (r.state == 3) {  // cancelled while queued
+    S->queue.pop_front();
+    return true;
+  }
+  ServerCtx* slot = nullptr;
+  for (auto& c : S->ctxs)
+    if (!c.busy && c.hier == r.hier) {
+      slot = &c;
+      break;
+    }
+  if (!slot) {
+    // estimate the context's size from the hierarchy handle's own workspace
+    const size_t need = r.hier->ctx_bytes + [&] {
+      size_t v = 0;
+      for (auto& L : r.hier->lv) v += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
+      for (auto& L : r.hier->lv32) v += 6 * sizeof(float) * (size_t)L.n;
+      return v;
+    }();
+    if (need > S->budget) {  // can never fit: reject
+      r.state = 4;
+      r.status = NSAMG_ERR_ADMISSION;
+      r.stats.status = NSAMG_ERR_ADMISSION;
+      r.t_done = S->now();
+      S->queue.pop_front();
+      return true;
+    }
+    std::vector<nsamg_handle*> victims;
+    while (S->used + need > S->budget) {  // evict the least recently used idle contexts
+      int victim = -1;
+      for (int k = 0; k < (int)S->ctxs.size(); ++k)
+        if (!S->ctxs[k].busy && (victim < 0 || S->ctxs[k].last_use < S->ctxs[victim].last_use)) victim = k;
+      if (victim < 0) break;
+      victims.push_back(S->ctxs[victim].ctx);
+      S->used -= S->ctxs[victim].ctx->ctx_bytes;
+      S->ctxs.erase(S->ctxs.begin() + victim);
+    }
+    if (!victims.empty()) {
+      // Freeing device memory synchronises the device, and running solves signal completion
+      // through callbacks that take the lock: free without holding it.
+      lk.unlock();
+      for (nsamg_handle* v : victims) destroy_impl(v);
+      lk.lock();
+    }
+    if (S->used + need > S->budget) return false;  // wait for running solves to finish
+    nsamg_handle* c = nullptr;
+    lk.unlock();
+    const int rc = clone_context(r.hier, &c);
+    lk.lock();
+    ServerReq& rr = S->reqs[t];
+    if (rc != NSAMG_OK) {
+      rr.state = 4;
+      rr.status = rc;
+      rr.stats.status = rc;
+      rr.t_done = S->now();
+      S->last_error = g_err;
+      S->queue.pop_front();
+      return true;
+    }
+    S->used += c->ctx_bytes;
+    S->ctxs.push_back(ServerCtx{c, rr.hier, false, 0});
+    slot = &S->ctxs.back();
+  }
+  ServerReq& rq = S->reqs[t];
+  nsamg_handle* h = slot->ctx;
+  slot->busy = true;
+  slot->last_use = ++S->use_clock;
+  S->queue.pop_front();
+  rq.ctx = h;
+  rq.state = 1;
+  rq.t_start = S->now();
+  S->running += 1;
+  GState* hs = h->h_st;
+  hs->b = rq.b;
+  hs->x = rq.x;
+  hs->rtol = rq.rtol;
+  hs->maxit = rq.maxit;
+  hs->m = h->m;
+  hs->t_exact = h->p.t_exact;
+  cudaStream_t st = h->stream;
+  bool ok = (!rq.ready || cudaStreamWaitEvent(st, rq.ready, 0) == cudaSuccess) &&
+            cudaMemcpyAsync(h->st, hs, offsetof(GState, i), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaGraphLaunch(h->exec, st) == cudaSuccess &&
+            cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaLaunchHostFunc(st, on_done, new DoneMsg{S, t}) == cudaSuccess;
+  if (!ok) {
+    rq.state = 2;
+    rq.status = NSAMG_ERR_CUDA;
+    rq.stats.status = NSAMG_ERR_CUDA;
+    rq.t_done = S->now();
+    slot->busy = false;
+    S->running -= 1;
+    S->last_error = cudaGetErrorString(cudaGetLastError());
+  }
+  return true;
+}
+
+void server_loop(nsamg_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    server_collect(S);
+    bool progressed = false;
+    while (server_try_start(S, lk)) {
+      progressed = true;
+      server_collect(S);
+    }
+    if (S->stop && S->queue.empty() && S->running == 0) break;
+    if (!progressed) S->cv.wait_for(lk, std::chrono::milliseconds(5));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int nsamg_server_create(size_t hbm_budget_bytes, int max_slots, nsamg_server** out) {
+  if (!out) return fail(NSAMG_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (max_slots < 1) return fail(NSAMG_ERR_INVALID_ARG, "max_slots must be >= 1");
+  nsamg_server* S = new nsamg_server();
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    delete S;
+    return fail(NSAMG_ERR_CUDA, "no current device");
+  }
+  S->budget = hbm_budget_bytes;
+  S->max_slots = max_slots;
+  S->t0 = std::chrono::steady_clock::now();
+  S->worker = std::thread(server_loop, S);
+  *out = S;
+  return NSAMG_OK;
+}
+
+int nsamg_server_submit(nsamg_server* S, nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit,
+                        void* ready_stream, uint64_t* ticket) {
+  if (!S || !h || !d_b || !d_x || !ticket) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  if (h->batch || h->shared_mats) return fail(NSAMG_ERR_INVALID_ARG, "serve hierarchy handles from nsamg_setup_hierarchy");
+  if (!h->p.use_graph) return fail(NSAMG_ERR_INVALID_ARG, "served hierarchies need use_graph = 1");
+  if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
+  cudaEvent_t ev = nullptr;
+  CK(cudaSetDevice(S->device));
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, (cudaStream_t)ready_stream));
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      cudaEventDestroy(ev);
+      return fail(NSAMG_ERR_INVALID_ARG, "server is shutting down");
+    }
+    ServerReq r;
+    r.ticket = S->next_ticket++;
+    r.hier = h;
+    r.b = d_b;
+    r.x = d_x;
+    r.rtol = rtol;
+    r.maxit = maxit;
+    r.t_submit = S->now();
+    r.ready = ev;
+    *ticket = r.ticket;
+    S->reqs[r.ticket] = r;
+    S->queue.push_back(r.ticket);
+  }
+  S->cv.notify_all();
+  return NSAMG_OK;
+}
+
+int nsamg_server_poll(nsamg_server* S, uint64_t ticket, nsamg_stats* st, double* times) {
+  if (!S) return fail(NSAMG_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
+  ServerReq& r = it->second;
+  if (r.state < 2) return NSAMG_PENDING;
+  if (st) *st = r.stats;
+  if (times) {
+    times[0] = r.t_submit;
+    times[1] = r.t_start;
+    times[2] = r.t_done;
+  }
+  const int status = r.status;
+  if (r.ready) cudaEventDestroy(r.ready);
+  S->reqs.erase(it);
+  if (status < 0) return fail(status, status == NSAMG_ERR_ADMISSION ? "request rejected by admission (too large for the budget)"
+                                                                   : "request failed: " + S->last_error);
+  return status;
+}
+
+int nsamg_server_wait(nsamg_server* S, uint64_t ticket, nsamg_stats* st, double* times) {
+  if (!S) return fail(NSAMG_ERR_INVALID_ARG, "null server");
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
+    S->cv.wait(lk, [&] {
+      server_collect(S);
+      auto jt = S->reqs.find(ticket);
+      return jt == S->reqs.end() || jt->second.state >= 2;
+    });
+  }
+  return nsamg_server_poll(S, ticket, st, times);
+}
+
+int nsamg_server_cancel(nsamg_server* S, uint64_t ticket) {
+  if (!S) return fail(NSAMG_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
+  if (it->second.state != 0) return fail(NSAMG_ERR_INVALID_ARG, "request already started or finished");
+  it->second.state = 3;
+  it->second.status = NSAMG_ERR_INVALID_ARG;
+  it->second.stats.status = NSAMG_ERR_INVALID_ARG;
+  it->second.t_done = S->now();
+  return NSAMG_OK;
+}
+
+int nsamg_server_info(nsamg_server* S, int64_t* out4) {
+  if (!S || !out4) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  out4[0] = (int64_t)S->used;
+  out4[1] = (int64_t)S->ctxs.size();
+  out4[2] = S->running;
+  out4[3] = (int64_t)S->queue.size();
+  return NSAMG_OK;
+}
+
+void nsamg_server_destroy(nsamg_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    for (uint64_t t : S->queue) {  // drop queued requests
+      auto& r = S->reqs[t];
+      r.state = 3;
+    }
+    S->queue.clear();
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  cudaSetDevice(S->device);
+  for (auto& c : S->ctxs) destroy_impl(c.ctx);
+  for (auto& kv : S->reqs)
+    if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+  delete S;
+}
 
 }  // extern "C"

@@ -59,6 +59,8 @@ EXPORTS = [
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
     "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
+    "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
+    "nsamg_server_info", "nsamg_server_destroy",
 ]
 
 _lib = None
@@ -95,6 +97,13 @@ def load(path: str = LIB_PATH):
         "nsamg_batch_solve": (i32, [vp, vp, vp, f64, i32, ctypes.POINTER(Stats)]),
         "nsamg_batch_count": (i32, [vp]),
         "nsamg_batch_offsets": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "nsamg_server_create": (i32, [ctypes.c_size_t, i32, ctypes.POINTER(vp)]),
+        "nsamg_server_submit": (i32, [vp, vp, vp, vp, f64, i32, vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "nsamg_server_poll": (i32, [vp, ctypes.c_uint64, ctypes.POINTER(Stats), ctypes.POINTER(f64)]),
+        "nsamg_server_wait": (i32, [vp, ctypes.c_uint64, ctypes.POINTER(Stats), ctypes.POINTER(f64)]),
+        "nsamg_server_cancel": (i32, [vp, ctypes.c_uint64]),
+        "nsamg_server_info": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "nsamg_server_destroy": (None, [vp]),
         "nsamg_destroy": (None, [vp]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
@@ -321,3 +330,72 @@ def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -
 
 def status_str(s: int) -> str:
     return load().nsamg_status_str(int(s)).decode()
+
+
+ERR_ADMISSION = -7
+
+
+class Server:
+    """Continuous-batching request server (see nsamg_server_create). Device arrays passed to
+    submit() must stay alive until the request completes; the object keeps references."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.nsamg_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+        self._s = h
+        self._keep: dict = {}
+
+    def submit(self, handle: Handle, b, x, rtol: float = 1e-8, maxit: int = 1000, ready_stream=None) -> int:
+        """ready_stream: cudaStream_t (int) on which b and x were produced; None = legacy default."""
+        t = ctypes.c_uint64()
+        rs = None if not ready_stream else ctypes.c_void_p(ready_stream)
+        _check(load().nsamg_server_submit(self._s, handle._h, _ptr(b), _ptr(x), float(rtol), int(maxit), rs,
+                                          ctypes.byref(t)))
+        self._keep[t.value] = (b, x)
+        return t.value
+
+    def _result(self, fn, ticket: int):
+        st = Stats()
+        times = (ctypes.c_double * 3)()
+        rc = fn(self._s, ctypes.c_uint64(ticket), ctypes.byref(st), times)
+        if rc == PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        _check(rc, (OK, NOT_CONVERGED))
+        d = st.as_dict()
+        d["t_submit"], d["t_start"], d["t_done"] = times[0], times[1], times[2]
+        return d
+
+    def poll(self, ticket: int):
+        """None while pending, else the stats dict (with server-clock times)."""
+        return self._result(load().nsamg_server_poll, ticket)
+
+    def wait(self, ticket: int) -> dict:
+        return self._result(load().nsamg_server_wait, ticket)
+
+    def cancel(self, ticket: int) -> None:
+        _check(load().nsamg_server_cancel(self._s, ctypes.c_uint64(ticket)))
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(load().nsamg_server_info(self._s, out))
+        return {"bytes_in_use": out[0], "contexts": out[1], "running": out[2], "queued": out[3]}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().nsamg_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
