@@ -60,6 +60,50 @@ def build_inputs():
     return A, H, rhs
 
 
+# Batched workload (C4): 256 independent 7-point systems, cube edge ~ U{16..64}, 4 levels each.
+BATCH_COUNT = 256
+BATCH_EDGES = (16, 64)
+BATCH_RESTART = 30
+# Served workload (C5): 32 resident hierarchies, edge ~ U{32..160}, Poisson arrivals.
+SERVE_POOL = 32
+SERVE_EDGES = (32, 160)
+SERVE_RATE = 200.0
+SERVE_WARM = 200
+SERVE_REQS = 2000
+
+
+def _batch_system(args):
+    k, e = args
+    from workloads import build_hierarchy, pressure3d_7pt, rhs_uniform
+    A = pressure3d_7pt(int(e), sigma=1.0, seed=1000 + k)
+    H = build_hierarchy(A, max_levels=4, coarse_max=1, direct_max=4096, ilu_levels=(), seed=1000 + k)
+    if H.nlevels != 4 or H.coarse_inv is None:
+        raise RuntimeError(f"batch system {k}: {H.nlevels} levels, coarse inverse {H.coarse_inv is not None}")
+    return A, H, rhs_uniform(A.shape[0], 1000 + k)
+
+
+def _serve_system(args):
+    k, e = args
+    from workloads import build_hierarchy, pressure3d_7pt
+    A = pressure3d_7pt(int(e), sigma=1.0, seed=2000 + k)
+    H = build_hierarchy(A, coarse_max=512, seed=2000 + k, ilu_levels=())
+    return A, H
+
+
+def build_pools(nbatch: int, nserve: int, workers: int = 8):
+    """Host setup of the batched and served workloads in a spawn process pool (before any CUDA
+    call in this process)."""
+    import multiprocessing as mp
+    from workloads import edge_sizes
+    be = edge_sizes(nbatch, *BATCH_EDGES, seed=1) if nbatch else []
+    se = edge_sizes(nserve, *SERVE_EDGES, seed=2) if nserve else []
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        batch = pool.map(_batch_system, list(enumerate(be)), chunksize=4) if nbatch else []
+        serve = pool.map(_serve_system, list(enumerate(se)), chunksize=1) if nserve else []
+    return batch, serve
+
+
 SMOOTHERS = {
     "hybrid_ilu0": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
     "poly_gs": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
@@ -199,6 +243,7 @@ def run_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    batch_sys, serve_pool = build_pools(0 if args.skip_batched else BATCH_COUNT, 0 if args.skip_serving else SERVE_POOL)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -274,6 +319,8 @@ def run_gpu(args):
     kern = time_kernels(nsamg, torch, h, A, H, stream) if rank == 0 else {}
     for hh in handles.values():
         hh.close()
+    batched = run_batched(nsamg, torch, batch_sys) if batch_sys else None
+    served = run_serving(nsamg, torch, serve_pool) if serve_pool else None
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -310,6 +357,10 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * n, "entry_point": "nsamg_solve_host"},
             "gpu_launches": main_r["launches"],
         }
+        if batched:
+            line["batched"] = batched
+        if served:
+            line["served"] = served
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(A, H, rhs[0], main_r["iters"][0])
         print(json.dumps(line))
@@ -326,6 +377,144 @@ def _single_thread():
         import contextlib
         pinned = os.environ.get("OPENBLAS_NUM_THREADS") == "1"
         return contextlib.nullcontext(), 1 if pinned else (os.cpu_count() or 1)
+
+
+def run_batched(nsamg, torch, systems):
+    """Batched solves/s (one nsamg_batch_solve over all systems) against one-at-a-time FP64
+    solves of the same systems."""
+    out = {"count": len(systems), "n_total": int(sum(A.shape[0] for A, _, _ in systems)),
+           "nnz_total": int(sum(A.nnz for A, _, _ in systems))}
+    b = torch.from_numpy(np.concatenate([bb for _, _, bb in systems])).cuda()
+    for name, fp32 in (("batched_fp32v", 1), ("batched_fp64", 0)):
+        p = nsamg.default_params(restart=BATCH_RESTART, vcycle_fp32=fp32)
+        with nsamg.batch_setup([H for _, H, _ in systems], p) as h:
+            x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                x.zero_()
+                nsamg.batch_solve(h, b, x, RTOL, MAXIT)
+            torch.cuda.synchronize()
+            reps = 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                x.zero_()
+                st = nsamg.batch_solve(h, b, x, RTOL, MAXIT)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+        out[name] = {"s_per_batch": dt, "solves_per_s": len(systems) / dt,
+                     "all_converged": all(q["converged"] == 1 for q in st),
+                     "max_relres_true": max(q["relres_true"] for q in st),
+                     "iters_max": max(q["iters"] for q in st), "iters_min": min(q["iters"] for q in st)}
+    # plain FP64 one-at-a-time
+    p = nsamg.default_params(restart=BATCH_RESTART)
+    hs = [nsamg.setup_hierarchy(H, p) for _, H, _ in systems]
+    bs = [torch.from_numpy(bb).cuda() for _, _, bb in systems]
+    xs = [torch.zeros(A.shape[0], dtype=torch.float64, device="cuda") for A, _, _ in systems]
+    for k in range(len(systems)):
+        nsamg.solve(hs[k], bs[k], xs[k], RTOL, MAXIT)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv = True
+    for k in range(len(systems)):
+        xs[k].zero_()
+        st = nsamg.solve(hs[k], bs[k], xs[k], RTOL, MAXIT)
+        conv = conv and st["converged"] == 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    out["one_at_a_time_fp64"] = {"s_total": dt, "solves_per_s": len(systems) / dt, "all_converged": conv}
+    out["speedup_fp32v_vs_one_at_a_time"] = out["batched_fp32v"]["solves_per_s"] / out["one_at_a_time_fp64"]["solves_per_s"]
+    return out
+
+
+def _arrivals(n: int, rate: float, npool: int, seed: int = 3):
+    rng = np.random.default_rng([seed, 5])
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    which = rng.integers(0, npool, n)
+    return t, which
+
+
+def run_serving(nsamg, torch, pool, budget_gb: float = 80.0, slots: int = 8):
+    """Poisson-arrival request stream on resident hierarchies: server (FP32 V-cycle, continuous
+    batching) against plain FP64 one-at-a-time FIFO on the same arrival trace."""
+    nreq = SERVE_WARM + SERVE_REQS
+    t_arr, which = _arrivals(nreq, SERVE_RATE, len(pool))
+    out = {"pool": len(pool), "rate_per_s": SERVE_RATE, "requests": SERVE_REQS, "warmup": SERVE_WARM,
+           "pool_rows": int(sum(A.shape[0] for A, _ in pool))}
+    gen = torch.Generator(device="cuda")
+
+    def rhs(k, n):
+        gen.manual_seed(10_000 + k)
+        return torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=gen)
+
+    # --- server arm
+    p32 = nsamg.default_params(restart=30, vcycle_fp32=1)
+    hs = [nsamg.setup_hierarchy(H, p32) for _, H in pool]
+    torch.cuda.synchronize()
+    lat, conv, done_t = [], True, []
+    with nsamg.Server(int(budget_gb * (1 << 30)), slots) as srv:
+        live = {}
+        t0 = time.perf_counter()
+        for k in range(nreq):
+            while time.perf_counter() - t0 < t_arr[k]:
+                for q in list(live):
+                    r = srv.poll(q)
+                    if r is not None:
+                        kk = live.pop(q)[0]
+                        if kk >= SERVE_WARM:
+                            lat.append(r["t_done"] - r["t_submit"])
+                            done_t.append(r["t_done"])
+                            conv = conv and r["converged"] == 1
+                time.sleep(0.0002)
+            n = pool[which[k]][0].shape[0]
+            b = rhs(k, n)
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            tq = srv.submit(hs[which[k]], b, x)
+            live[tq] = (k, b, x)
+        for q in list(live):
+            r = srv.wait(q)
+            kk = live.pop(q)[0]
+            if kk >= SERVE_WARM:
+                lat.append(r["t_done"] - r["t_submit"])
+                done_t.append(r["t_done"])
+                conv = conv and r["converged"] == 1
+        info = srv.info()
+    for h in hs:
+        h.close()
+    span = t_arr[-1] - t_arr[SERVE_WARM]
+    lat = np.array(lat)
+    out["server_fp32v"] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                           "solves_per_s": SERVE_REQS / max(span, max(done_t) - min(done_t)),
+                           "all_converged": conv, "slots": slots, "budget_gb": budget_gb,
+                           "contexts_at_end": info["contexts"]}
+    # --- one-at-a-time FP64 FIFO
+    p64 = nsamg.default_params(restart=30)
+    hs = [nsamg.setup_hierarchy(H, p64) for _, H in pool]
+    torch.cuda.synchronize()
+    lat2, conv2 = [], True
+    t0 = time.perf_counter()
+    tdone = []
+    for k in range(nreq):
+        now = time.perf_counter() - t0
+        if now < t_arr[k]:
+            time.sleep(t_arr[k] - now)
+        n = pool[which[k]][0].shape[0]
+        b = rhs(k, n)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = nsamg.solve(hs[which[k]], b, x, RTOL, MAXIT)
+        tf = time.perf_counter() - t0
+        if k >= SERVE_WARM:
+            lat2.append(tf - t_arr[k])
+            tdone.append(tf)
+            conv2 = conv2 and st["converged"] == 1
+    for h in hs:
+        h.close()
+    lat2 = np.array(lat2)
+    out["one_at_a_time_fp64"] = {"p50_ms": float(np.percentile(lat2, 50) * 1e3),
+                                 "p99_ms": float(np.percentile(lat2, 99) * 1e3),
+                                 "solves_per_s": SERVE_REQS / max(span, tdone[-1] - t_arr[SERVE_WARM]),
+                                 "all_converged": conv2}
+    return out
 
 
 def oracle_sample(A, H, b, iters_sample: int):
@@ -462,6 +651,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nsamg", choices=["nsamg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true", help="skip the 256-system batched comparison")
+    ap.add_argument("--skip-serving", action="store_true", help="skip the Poisson-arrival serving comparison")
     ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
