@@ -644,6 +644,54 @@ def run_profile_kernel(args):
     h.close()
 
 
+C3_EDGE = 192
+
+
+def run_c3(args):
+    """27-point Q1 FE Laplacian on 192^3 interior nodes (7,077,888 rows, 189,119,224 nnz), wall-
+    normal grading to h_x/h_z,min = 100, seeded symmetric permutation then RCM. FP32 V-cycle
+    inside FP64 flexible GMRES(30) against the FP64 V-cycle; true residuals checked with the
+    oracle's FP64 SpMV, and the FP32-V solution compared with the FP64 one."""
+    import torch
+    import oracle.kernels as OK
+    from paper_2112_14681_b300 import nsamg
+    from workloads import build_hierarchy, rhs_uniform
+    from workloads.matrices import q1_27pt_graded
+    t0 = time.perf_counter()
+    A = q1_27pt_graded(args.c3_edge, aspect=100.0, seed=SEED)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H = build_hierarchy(A, ilu_levels=(), coarse_max=512, seed=SEED)
+    t_setup = time.perf_counter() - t0
+    b = rhs_uniform(A.shape[0], SEED)
+    nsamg.load()
+    db = torch.from_numpy(b).cuda()
+    res = {"workload": f"q1_27pt_graded_{args.c3_edge}^3_aspect100_rcm", "n": A.shape[0], "nnz": int(A.nnz),
+           "levels": H.info["n"], "operator_complexity": round(H.info["operator_complexity"], 3),
+           "smoother": "l1_jacobi x2", "restart": 30, "gen_s": t_gen, "setup_s": t_setup}
+    xs = {}
+    for name, fp32 in (("fp32v", 1), ("fp64", 0)):
+        p = nsamg.default_params(smoother=nsamg.JACOBI_L1, pre_sweeps=2, post_sweeps=2, restart=30, vcycle_fp32=fp32)
+        with nsamg.setup_hierarchy(H, p) as h:
+            x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            nsamg.solve(h, db, x, RTOL, 2000)
+            ts = []
+            for _ in range(3):
+                x.zero_()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                st = nsamg.solve(h, db, x, RTOL, 2000)
+                ts.append(time.perf_counter() - t1)
+            xh = x.cpu().numpy()
+        rel = float(np.linalg.norm(OK.residual(A, b, xh)) / np.linalg.norm(b))
+        xs[name] = xh
+        res[name] = {"s_per_solve": min(ts), "iters": st["iters"], "restarts": st["restarts"],
+                     "relres_true_oracle_spmv": rel, "relres_reported": st["relres_true"], "converged": st["converged"]}
+    res["x_fp32v_vs_fp64_rel"] = float(np.linalg.norm(xs["fp32v"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    res["speedup_fp32v"] = res["fp64"]["s_per_solve"] / res["fp32v"]["s_per_solve"]
+    print(json.dumps({"c3": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -656,12 +704,16 @@ def main():
     ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
+    ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
+    ap.add_argument("--c3-edge", type=int, default=C3_EDGE)
     ap.add_argument("--profile-kernel", choices=["spmv", "ilu", "gram", "update"],
                     help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":
         args.warmup = 3
-    if args.profile_kernel:
+    if args.c3:
+        run_c3(args)
+    elif args.profile_kernel:
         run_profile_kernel(args)
     elif args.profile:
         run_profile(args)

@@ -113,7 +113,15 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
     }
   }
   const double avg = n ? (double)nnz / n : 0.0;
-  d.G = avg <= 12 ? 1 : avg <= 24 ? 2 : avg <= 48 ? 4 : avg <= 96 ? 8 : 16;
+  if (n < 16384) {
+    // small levels are latency bound: give each row enough lanes that every lane handles about
+    // one entry (the FP64 issue cost of idle lanes does not matter at this size)
+    int G = 1;
+    while (G < 32 && G < avg) G <<= 1;
+    d.G = G;
+  } else {
+    d.G = avg <= 12 ? 1 : avg <= 24 ? 2 : avg <= 48 ? 4 : avg <= 96 ? 8 : 16;
+  }
   return NSAMG_OK;
 }
 
@@ -1901,12 +1909,13 @@ struct nsamg_server {
   int running = 0;
   uint64_t next_ticket = 1;
   uint64_t use_clock = 0;
-  std::mutex mu;
+  std::mutex mu;                   // queue, requests, contexts, accounting (never held in CUDA calls)
   std::condition_variable cv;
   std::deque<uint64_t> queue;
   std::unordered_map<uint64_t, ServerReq> reqs;
   std::vector<ServerCtx> ctxs;
-  std::vector<uint64_t> finished;  // tickets completed by stream callbacks, not yet processed
+  std::mutex fin_mu;               // only guards `finished`; taken by the stream callbacks
+  std::vector<uint64_t> finished;  // tickets whose graphs completed, not yet processed
   std::thread worker;
   bool stop = false;
   std::chrono::steady_clock::time_point t0;
@@ -1921,19 +1930,26 @@ struct DoneMsg {
   uint64_t ticket;
 };
 
+// Stream callback after a request's graph and state read-back: it only appends the ticket under
+// a lock that no thread holds across a CUDA call, so it can never wait on CUDA work.
 void CUDART_CB on_done(void* p) {
   DoneMsg* m = (DoneMsg*)p;
   {
-    std::lock_guard<std::mutex> lk(m->srv->mu);
+    std::lock_guard<std::mutex> lk(m->srv->fin_mu);
     m->srv->finished.push_back(m->ticket);
   }
   m->srv->cv.notify_all();
   delete m;
 }
 
-// Finish requests whose graphs completed (called with the lock held).
+// Finish requests whose graphs completed (called with `mu` held).
 void server_collect(nsamg_server* S) {
-  for (uint64_t t : S->finished) {
+  std::vector<uint64_t> done;
+  {
+    std::lock_guard<std::mutex> lk(S->fin_mu);
+    done.swap(S->finished);
+  }
+  for (uint64_t t : done) {
     auto it = S->reqs.find(t);
     if (it == S->reqs.end()) continue;
     ServerReq& r = it->second;
@@ -1955,107 +1971,125 @@ void server_collect(nsamg_server* S) {
       if (c.ctx == h) c.busy = false;
     S->running -= 1;
   }
-  S->finished.clear();
 }
 
-// Try to start the request at the head of the queue. Returns true if it started (or was
-// rejected), false if it must wait for a slot or memory.
+size_t context_need(nsamg_handle* hier) {
+  size_t v = hier->ctx_bytes;
+  for (auto& L : hier->lv) v += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
+  for (auto& L : hier->lv32) v += 6 * sizeof(float) * (size_t)L.n;
+  return v;
+}
+
+void finish_request(nsamg_server* S, ServerReq& r, int state, int status) {
+  r.state = state;
+  r.status = status;
+  r.stats.status = status;
+  r.t_done = S->now();
+}
+
+// One admission step for the head of the queue. Called with `lk` held; CUDA work (freeing
+// evicted contexts, creating a context, launching) runs with the lock released. Returns true
+// if the queue head changed (started, rejected or dropped), false if it has to wait.
 bool server_try_start(nsamg_server* S, std::unique_lock<std::mutex>& lk) {
   if (S->queue.empty() || S->running >= S->max_slots) return false;
   const uint64_t t = S->queue.front();
-  ServerReq& r = S->reqs[t];
-  if (r.state == 3) {  // cancelled while queued
+  auto found = S->reqs.find(t);
+  if (found == S->reqs.end() || found->second.state != 0) {  // cancelled (and maybe already polled)
     S->queue.pop_front();
     return true;
   }
-  ServerCtx* slot = nullptr;
-  for (auto& c : S->ctxs)
-    if (!c.busy && c.hier == r.hier) {
-      slot = &c;
+  ServerReq* r = &found->second;
+  nsamg_handle* hier = r->hier;
+  int slot = -1;
+  for (int k = 0; k < (int)S->ctxs.size(); ++k)
+    if (!S->ctxs[k].busy && S->ctxs[k].hier == hier) {
+      slot = k;
       break;
     }
-  if (!slot) {
-    // estimate the context's size from the hierarchy handle's own workspace
-    const size_t need = r.hier->ctx_bytes + [&] {
-      size_t v = 0;
-      for (auto& L : r.hier->lv) v += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
-      for (auto& L : r.hier->lv32) v += 6 * sizeof(float) * (size_t)L.n;
-      return v;
-    }();
+  if (slot < 0) {
+    const size_t need = context_need(hier);
     if (need > S->budget) {  // can never fit: reject
-      r.state = 4;
-      r.status = NSAMG_ERR_ADMISSION;
-      r.stats.status = NSAMG_ERR_ADMISSION;
-      r.t_done = S->now();
+      finish_request(S, *r, 4, NSAMG_ERR_ADMISSION);
       S->queue.pop_front();
+      S->cv.notify_all();
       return true;
     }
     std::vector<nsamg_handle*> victims;
-    while (S->used + need > S->budget) {  // evict the least recently used idle contexts
-      int victim = -1;
+    while (S->used + need > S->budget) {  // evict least recently used idle contexts
+      int v = -1;
       for (int k = 0; k < (int)S->ctxs.size(); ++k)
-        if (!S->ctxs[k].busy && (victim < 0 || S->ctxs[k].last_use < S->ctxs[victim].last_use)) victim = k;
-      if (victim < 0) break;
-      victims.push_back(S->ctxs[victim].ctx);
-      S->used -= S->ctxs[victim].ctx->ctx_bytes;
-      S->ctxs.erase(S->ctxs.begin() + victim);
+        if (!S->ctxs[k].busy && (v < 0 || S->ctxs[k].last_use < S->ctxs[v].last_use)) v = k;
+      if (v < 0) break;
+      victims.push_back(S->ctxs[v].ctx);
+      S->used -= S->ctxs[v].ctx->ctx_bytes;
+      S->ctxs.erase(S->ctxs.begin() + v);
     }
-    if (!victims.empty()) {
-      // Freeing device memory synchronises the device, and running solves signal completion
-      // through callbacks that take the lock: free without holding it.
-      lk.unlock();
-      for (nsamg_handle* v : victims) destroy_impl(v);
-      lk.lock();
+    if (S->used + need > S->budget) {
+      if (!victims.empty()) {
+        lk.unlock();
+        for (nsamg_handle* v : victims) destroy_impl(v);
+        lk.lock();
+      }
+      return false;  // wait for running solves to finish
     }
-    if (S->used + need > S->budget) return false;  // wait for running solves to finish
-    nsamg_handle* c = nullptr;
+    S->used += need;  // reserve while the context is built outside the lock
+    S->queue.pop_front();  // the request is being admitted: no longer cancellable
+    r->state = 1;
     lk.unlock();
-    const int rc = clone_context(r.hier, &c);
+    for (nsamg_handle* v : victims) destroy_impl(v);
+    nsamg_handle* c = nullptr;
+    const int rc = clone_context(hier, &c);
+    const std::string err = rc ? g_err : std::string();
     lk.lock();
-    ServerReq& rr = S->reqs[t];
+    r = &S->reqs.find(t)->second;  // a request in state 1 is never released, so it is still there
     if (rc != NSAMG_OK) {
-      rr.state = 4;
-      rr.status = rc;
-      rr.stats.status = rc;
-      rr.t_done = S->now();
-      S->last_error = g_err;
-      S->queue.pop_front();
+      S->used -= need;
+      S->last_error = err;
+      finish_request(S, *r, 4, rc);
+      S->cv.notify_all();
       return true;
     }
     S->used += c->ctx_bytes;
-    S->ctxs.push_back(ServerCtx{c, rr.hier, false, 0});
-    slot = &S->ctxs.back();
+    S->used -= need;
+    S->ctxs.push_back(ServerCtx{c, hier, false, 0});
+    slot = (int)S->ctxs.size() - 1;
+  } else {
+    S->queue.pop_front();
   }
-  ServerReq& rq = S->reqs[t];
-  nsamg_handle* h = slot->ctx;
-  slot->busy = true;
-  slot->last_use = ++S->use_clock;
-  S->queue.pop_front();
-  rq.ctx = h;
-  rq.state = 1;
-  rq.t_start = S->now();
+  // start: bookkeeping under the lock, launches outside it
+  ServerCtx& sc = S->ctxs[slot];
+  nsamg_handle* h = sc.ctx;
+  sc.busy = true;
+  sc.last_use = ++S->use_clock;
+  r->ctx = h;
+  r->state = 1;
+  r->t_start = S->now();
   S->running += 1;
   GState* hs = h->h_st;
-  hs->b = rq.b;
-  hs->x = rq.x;
-  hs->rtol = rq.rtol;
-  hs->maxit = rq.maxit;
+  hs->b = r->b;
+  hs->x = r->x;
+  hs->rtol = r->rtol;
+  hs->maxit = r->maxit;
   hs->m = h->m;
   hs->t_exact = h->p.t_exact;
+  cudaEvent_t ready = r->ready;
+  lk.unlock();
   cudaStream_t st = h->stream;
-  bool ok = (!rq.ready || cudaStreamWaitEvent(st, rq.ready, 0) == cudaSuccess) &&
-            cudaMemcpyAsync(h->st, hs, offsetof(GState, i), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-            cudaGraphLaunch(h->exec, st) == cudaSuccess &&
-            cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-            cudaLaunchHostFunc(st, on_done, new DoneMsg{S, t}) == cudaSuccess;
+  const bool ok = (!ready || cudaStreamWaitEvent(st, ready, 0) == cudaSuccess) &&
+                  cudaMemcpyAsync(h->st, hs, offsetof(GState, i), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                  cudaGraphLaunch(h->exec, st) == cudaSuccess &&
+                  cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  cudaLaunchHostFunc(st, on_done, new DoneMsg{S, t}) == cudaSuccess;
+  const std::string err = ok ? std::string() : std::string(cudaGetErrorString(cudaGetLastError()));
+  lk.lock();
   if (!ok) {
-    rq.state = 2;
-    rq.status = NSAMG_ERR_CUDA;
-    rq.stats.status = NSAMG_ERR_CUDA;
-    rq.t_done = S->now();
-    slot->busy = false;
+    ServerReq& rr = S->reqs.find(t)->second;  // a running request is not released before it finishes
+    finish_request(S, rr, 2, NSAMG_ERR_CUDA);
+    for (auto& c : S->ctxs)
+      if (c.ctx == h) c.busy = false;
     S->running -= 1;
-    S->last_error = cudaGetErrorString(cudaGetLastError());
+    S->last_error = err;
+    S->cv.notify_all();
   }
   return true;
 }
@@ -2071,7 +2105,7 @@ void server_loop(nsamg_server* S) {
       server_collect(S);
     }
     if (S->stop && S->queue.empty() && S->running == 0) break;
-    if (!progressed) S->cv.wait_for(lk, std::chrono::milliseconds(5));
+    if (!progressed) S->cv.wait_for(lk, std::chrono::milliseconds(2));
   }
 }
 
@@ -2131,7 +2165,11 @@ int nsamg_server_submit(nsamg_server* S, nsamg_handle* h, const double* d_b, dou
 
 int nsamg_server_poll(nsamg_server* S, uint64_t ticket, nsamg_stats* st, double* times) {
   if (!S) return fail(NSAMG_ERR_INVALID_ARG, "null server");
+  cudaEvent_t ev = nullptr;
+  int status;
+  {
   std::lock_guard<std::mutex> lk(S->mu);
+  server_collect(S);
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
   ServerReq& r = it->second;
@@ -2142,9 +2180,11 @@ int nsamg_server_poll(nsamg_server* S, uint64_t ticket, nsamg_stats* st, double*
     times[1] = r.t_start;
     times[2] = r.t_done;
   }
-  const int status = r.status;
-  if (r.ready) cudaEventDestroy(r.ready);
+  status = r.status;
+  ev = r.ready;
   S->reqs.erase(it);
+  }
+  if (ev) cudaEventDestroy(ev);
   if (status < 0) return fail(status, status == NSAMG_ERR_ADMISSION ? "request rejected by admission (too large for the budget)"
                                                                    : "request failed: " + S->last_error);
   return status;
@@ -2156,11 +2196,12 @@ int nsamg_server_wait(nsamg_server* S, uint64_t ticket, nsamg_stats* st, double*
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
-    S->cv.wait(lk, [&] {
+    while (true) {
       server_collect(S);
       auto jt = S->reqs.find(ticket);
-      return jt == S->reqs.end() || jt->second.state >= 2;
-    });
+      if (jt == S->reqs.end() || jt->second.state >= 2) break;
+      S->cv.wait_for(lk, std::chrono::milliseconds(2));
+    }
   }
   return nsamg_server_poll(S, ticket, st, times);
 }
@@ -2171,6 +2212,11 @@ int nsamg_server_cancel(nsamg_server* S, uint64_t ticket) {
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) return fail(NSAMG_ERR_INVALID_ARG, "unknown ticket");
   if (it->second.state != 0) return fail(NSAMG_ERR_INVALID_ARG, "request already started or finished");
+  for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+    if (*q == ticket) {
+      S->queue.erase(q);
+      break;
+    }
   it->second.state = 3;
   it->second.status = NSAMG_ERR_INVALID_ARG;
   it->second.stats.status = NSAMG_ERR_INVALID_ARG;
@@ -2194,8 +2240,8 @@ void nsamg_server_destroy(nsamg_server* S) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
     for (uint64_t t : S->queue) {  // drop queued requests
-      auto& r = S->reqs[t];
-      r.state = 3;
+      auto it = S->reqs.find(t);
+      if (it != S->reqs.end()) it->second.state = 3;
     }
     S->queue.clear();
   }

@@ -365,3 +365,26 @@ def test_fp32_vcycle_solve(name, smoother):
     ref2 = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-12)
     assert st2["converged"]
     assert np.linalg.norm(host(x2) - ref2.x) / np.linalg.norm(ref2.x) <= 1e-6
+
+
+def test_c3_type_graded_27pt_fp32_vcycle():
+    """Graded 27-point Q1 system (C3 structure at 20^3): l1-Jacobi V-cycle in FP32 inside FP64
+    flexible GMRES reaches 1e-8 with iterations within +-1 of the FP64 oracle; at 1e-12 the
+    solution agrees with the oracle's to 1e-6."""
+    from workloads.matrices import q1_27pt_graded
+    A = q1_27pt_graded(20, aspect=100.0, seed=1)
+    H = build_hierarchy(A, ilu_levels=(), coarse_max=64)
+    p = nsamg.default_params(smoother=K.JACOBI_L1, pre_sweeps=2, post_sweeps=2, restart=30, vcycle_fp32=1)
+    op = oracle_params(p)
+    b = rhs_uniform(A.shape[0], 3)
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-8, maxit=500)
+    with nsamg.setup_hierarchy(H, p) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        xs = host(x)
+        assert st["converged"] and np.linalg.norm(b - A @ xs) / np.linalg.norm(b) <= 1e-8
+        assert abs(st["iters"] - ref.iters) <= 1, (st["iters"], ref.iters)
+        x2 = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.solve(h, dev(b), x2, rtol=1e-12, maxit=1000)
+    ref2 = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-12, maxit=1000)
+    assert np.linalg.norm(host(x2) - ref2.x) / np.linalg.norm(ref2.x) <= 1e-6

@@ -24,24 +24,32 @@ inline uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-// S_i = { j != i : |a_ij| >= theta * max_{k != i} |a_ik| } stored as a flag per nonzero.
+// mode 0: S_i = { j != i : |a_ij| >= theta * max_{k != i} |a_ik| }   (absolute values)
+// mode 1: S_i = { j != i : -a_ij >= theta * max_{k != i} (-a_ik) }    (classical sign-aware form:
+//         only couplings of the opposite sign to a positive diagonal can be strong)
+// stored as a flag per nonzero. The two coincide for M-matrices.
+int g_strength_mode = 0;
+
 void strength(int n, const int* rp, const int* ci, const double* v, double theta, std::vector<char>& s) {
   s.assign(rp[n], 0);
+  const int mode = g_strength_mode;
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double mx = 0.0;
     for (int p = rp[i]; p < rp[i + 1]; ++p)
-      if (ci[p] != i) mx = std::max(mx, std::fabs(v[p]));
-    if (mx == 0.0) continue;
+      if (ci[p] != i) mx = std::max(mx, mode ? -v[p] : std::fabs(v[p]));
+    if (mx <= 0.0) continue;
     const double thr = theta * mx;
     for (int p = rp[i]; p < rp[i + 1]; ++p)
-      if (ci[p] != i && v[p] != 0.0 && std::fabs(v[p]) >= thr) s[p] = 1;
+      if (ci[p] != i && v[p] != 0.0 && (mode ? -v[p] : std::fabs(v[p])) >= thr) s[p] = 1;
   }
 }
 
 }  // namespace
 
 extern "C" {
+
+void nsw_set_strength_mode(int mode) { g_strength_mode = mode; }
 
 // PMIS C/F splitting. cf[i] = coarse index (>= 0) for C-points, -1 for F-points.
 // Returns the number of coarse points, or -1 on invalid input.
@@ -203,6 +211,69 @@ int nsw_ilu0(int n, const int* rp, const int* ci, const double* v, int* lrp, int
     urp[i + 1] = uo;
   }
   return 0;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Sparse matrix product C = A B (CSR, OpenMP over rows, Gustavson accumulation with a dense
+// marker per thread). Each row is formed by one thread in a fixed order, then its columns are
+// sorted, so the result does not depend on the thread count. Used for the Galerkin product
+// A_c = R (A P) of the hierarchy setup.
+// ------------------------------------------------------------------------------------------
+#include <omp.h>
+
+extern "C" {
+
+// Pass 1: row counts of C into crp[1..m] (crp[0] = 0, prefix-summed). Returns nnz(C).
+int64_t nsw_spgemm_count(int m, int ncols_b, const int* arp, const int* aci, const int* brp, const int* bci, int64_t* crp) {
+  std::vector<int64_t> cnt(m, 0);
+#pragma omp parallel
+  {
+    std::vector<int> mark(ncols_b, -1);
+#pragma omp for schedule(dynamic, 1024)
+    for (int i = 0; i < m; ++i) {
+      int64_t c = 0;
+      for (int p = arp[i]; p < arp[i + 1]; ++p) {
+        const int k = aci[p];
+        for (int q = brp[k]; q < brp[k + 1]; ++q) {
+          const int j = bci[q];
+          if (mark[j] != i) { mark[j] = i; ++c; }
+        }
+      }
+      cnt[i] = c;
+    }
+  }
+  crp[0] = 0;
+  for (int i = 0; i < m; ++i) crp[i + 1] = crp[i] + cnt[i];
+  return crp[m];
+}
+
+// Pass 2: columns (sorted per row) and values of C.
+void nsw_spgemm_fill(int m, int ncols_b, const int* arp, const int* aci, const double* av, const int* brp, const int* bci,
+                     const double* bv, const int64_t* crp, int* cci, double* cv) {
+#pragma omp parallel
+  {
+    std::vector<int64_t> pos(ncols_b, -1);
+    std::vector<std::pair<int, double>> row;
+#pragma omp for schedule(dynamic, 1024)
+    for (int i = 0; i < m; ++i) {
+      row.clear();
+      for (int p = arp[i]; p < arp[i + 1]; ++p) {
+        const int k = aci[p];
+        const double a = av[p];
+        for (int q = brp[k]; q < brp[k + 1]; ++q) {
+          const int j = bci[q];
+          if (pos[j] < 0) { pos[j] = (int64_t)row.size(); row.emplace_back(j, a * bv[q]); }
+          else row[pos[j]].second += a * bv[q];
+        }
+      }
+      for (auto& e : row) pos[e.first] = -1;
+      std::sort(row.begin(), row.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
+      int64_t o = crp[i];
+      for (auto& e : row) { cci[o] = e.first; cv[o] = e.second; ++o; }
+    }
+  }
 }
 
 }  // extern "C"

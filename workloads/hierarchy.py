@@ -42,6 +42,13 @@ def _load():
         lib.nsw_amg_interp.restype = ctypes.c_int64
         lib.nsw_ilu0.argtypes = [ctypes.c_int, i32p, i32p, f64p, i32p, i32p, f64p, i32p, i32p, f64p, f64p]
         lib.nsw_ilu0.restype = ctypes.c_int
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        lib.nsw_spgemm_count.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i32p, i64p]
+        lib.nsw_spgemm_count.restype = ctypes.c_int64
+        lib.nsw_spgemm_fill.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p, i32p, i32p, f64p, i64p, i32p, f64p]
+        lib.nsw_spgemm_fill.restype = None
+        lib.nsw_set_strength_mode.argtypes = [ctypes.c_int]
+        lib.nsw_set_strength_mode.restype = None
         _lib = lib
     return _lib
 
@@ -85,6 +92,26 @@ class Hierarchy:
         return sum(l.A.nnz for l in self.levels) / self.levels[0].A.nnz
 
 
+def spgemm(A: sp.csr_matrix, B: sp.csr_matrix) -> sp.csr_matrix:
+    """C = A B with the OpenMP setup library (rows sorted; result independent of thread count)."""
+    lib = _load()
+    A, B = _csr(A), _csr(B)
+    m, k = A.shape
+    if B.shape[0] != k:
+        raise ValueError("shape mismatch")
+    n = B.shape[1]
+    crp = np.empty(m + 1, np.int64)
+    nnz = lib.nsw_spgemm_count(m, n, A.indptr, A.indices, B.indptr, B.indices, crp)
+    if nnz >= 2 ** 31:
+        raise ValueError("product too large for int32 indices")
+    cci = np.empty(max(nnz, 1), np.int32)
+    cv = np.empty(max(nnz, 1), np.float64)
+    lib.nsw_spgemm_fill(m, n, A.indptr, A.indices, A.data, B.indptr, B.indices, B.data, crp, cci, cv)
+    C = sp.csr_matrix((cv[:nnz], cci[:nnz], crp.astype(np.int32)), shape=(m, n))
+    C.has_sorted_indices = True
+    return C
+
+
 def coarsen(A: sp.csr_matrix, theta: float, seed: int) -> tuple[np.ndarray, int]:
     lib = _load()
     n = A.shape[0]
@@ -126,15 +153,18 @@ def ilu0(A: sp.csr_matrix):
 
 
 def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: int = 512, seed: int = 0,
-                    ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512) -> Hierarchy:
+                    ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512, strength: str = "abs") -> Hierarchy:
     """Build the Ruge-Stuben hierarchy of A (strength theta, PMIS, BAMG-direct, Galerkin RAP).
 
     Coarsening stops when a level has at most `coarse_max` rows, when `max_levels` levels exist,
     or when a coarsening step keeps more than 90% of the points. ILU(0) factors are attached to
     the levels listed in `ilu_levels` (None for every non-coarsest level). The coarsest level
-    gets a dense inverse when it has at most `direct_max` rows.
+    gets a dense inverse when it has at most `direct_max` rows. strength="abs" compares |a_ij|
+    (Sec. 5.1 as printed); strength="neg" compares -a_ij (classical Ruge-Stuben, for matrices
+    with positive off-diagonal entries such as Q1 stiffness on high-aspect elements).
     """
     A = _csr(A)
+    _load().nsw_set_strength_mode(1 if strength == "neg" else 0)
     levels = [Level(A=A)]
     while len(levels) < max_levels and levels[-1].n > coarse_max:
         Al = levels[-1].A
@@ -143,7 +173,7 @@ def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: in
             break
         P = _csr(interpolation(Al, theta, cf, nc))
         R = _csr(P.T)
-        Ac = _csr(R @ (Al @ P))
+        Ac = _csr(spgemm(R, spgemm(Al, P)))
         levels[-1].P, levels[-1].R = P, R
         levels.append(Level(A=Ac))
     want = range(len(levels) - 1) if ilu_levels is None else ilu_levels
