@@ -243,7 +243,10 @@ def run_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    batch_sys, serve_pool = build_pools(0 if args.skip_batched else BATCH_COUNT, 0 if args.skip_serving else SERVE_POOL)
+    # the batched / served comparisons are single-GPU extras: skipped for replica runs (N > 1)
+    extras = world == 1
+    batch_sys, serve_pool = build_pools(BATCH_COUNT if extras and not args.skip_batched else 0,
+                                        SERVE_POOL if extras and not args.skip_serving else 0)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -254,9 +257,10 @@ def run_gpu(args):
     d_rhs = [torch.from_numpy(b).cuda() for b in rhs]
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
 
+    from paper_2112_14681_b300 import replicas
+
     def barrier():
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(dist)
         torch.cuda.synchronize()
 
     results = {}
@@ -288,11 +292,7 @@ def run_gpu(args):
             e1.record(stream)
             e1.synchronize()
         barrier()
-        dt = e0.elapsed_time(e1) * 1e-3
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = replicas.max_over_ranks(dist, e0.elapsed_time(e1) * 1e-3, device="cuda")
         relres = max(s["relres_true"] for s in stats[-K:])
         results[name] = {"solves": K, "time_s": dt, "solves_per_s": world * K / dt, "s_per_solve": dt / K,
                          "iters": [s["iters"] for s in stats[-K:]][:4], "max_relres_true": relres,
@@ -311,11 +311,7 @@ def run_gpu(args):
     for k in range(Ke):
         hx.zero_()
         nsamg.solve_host(h, hb[k % N_RHS], hx, RTOL, MAXIT)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
     kern = time_kernels(nsamg, torch, h, A, H, stream) if rank == 0 else {}
     for hh in handles.values():
         hh.close()
