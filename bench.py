@@ -95,6 +95,8 @@ def build_pools(nbatch: int, nserve: int, workers: int = 8):
     call in this process)."""
     import multiprocessing as mp
     from workloads import edge_sizes
+    if not nbatch and not nserve:
+        return [], []
     be = edge_sizes(nbatch, *BATCH_EDGES, seed=1) if nbatch else []
     se = edge_sizes(nserve, *SERVE_EDGES, seed=2) if nserve else []
     ctx = mp.get_context("spawn")
