@@ -621,6 +621,13 @@ def run_profile_kernel(args):
     if args.profile_kernel == "spmv":
         for _ in range(3):
             nsamg.level_spmv(h, 0, x, y)
+    elif args.profile_kernel == "l1spmv":
+        n1 = nsamg.level_size(h, 1)
+        x1 = torch.rand(n1, dtype=torch.float64, device="cuda")
+        y1 = torch.empty_like(x1)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            nsamg.level_spmv(h, 1, x1, y1)
     elif args.profile_kernel == "ilu":
         for _ in range(3):
             nsamg.level_smooth(h, 0, x, y, backward=False, x_is_zero=True)
@@ -704,7 +711,7 @@ def main():
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
     ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
     ap.add_argument("--c3-edge", type=int, default=C3_EDGE)
-    ap.add_argument("--profile-kernel", choices=["spmv", "ilu", "gram", "update"],
+    ap.add_argument("--profile-kernel", choices=["spmv", "l1spmv", "ilu", "gram", "update"],
                     help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":

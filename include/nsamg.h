@@ -78,7 +78,9 @@ typedef struct {
   int32_t vcycle_fp32;   /* 0: FP64 V-cycle. 1: FP32 matrices and vectors in the V-cycle         */
   int32_t t_exact;       /* 0: T = I - L (truncated Neumann, Algorithm 1). 1: T = (I + L)^-1    */
   int32_t use_graph;     /* 1: run each solve as one CUDA graph with device-side loop control    */
-  int32_t spmv_group;    /* threads per row for CSR kernels: 0 = autotune at setup, else 1..32  */
+  int32_t spmv_group;    /* 0: autotune at setup (CSR with 1..32 threads per row, or SELL-32-sigma
+                            for matrices with >= 16384 rows); 1..32: CSR with that many threads per
+                            row; -1: SELL-32-sigma wherever available                              */
 } nsamg_params;
 
 typedef struct {
@@ -214,7 +216,9 @@ int nsamg_server_cancel(nsamg_server* s, uint64_t ticket);
 int nsamg_server_info(nsamg_server* s, int64_t* out4);
 void nsamg_server_destroy(nsamg_server* s);
 
-/* Autotuned threads-per-row of the CSR kernels of each level (diagnostic). */
+/* Matrix layout chosen for a level's operator (diagnostic): 0 = SELL-32-sigma (one thread per
+ * row, rows sorted by length inside windows of 4096 rows, chunks of 32 stored column-major),
+ * else the number of threads per row of the CSR kernel. */
 int nsamg_level_group(nsamg_handle* h, int level);
 
 /* Kernel launches in one Arnoldi step (V-cycle, SpMV, Gram, update). A solve launches

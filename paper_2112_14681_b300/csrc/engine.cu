@@ -9,6 +9,7 @@
 #include <vector>
 #include <algorithm>
 #include <initializer_list>
+#include <type_traits>
 
 #include "nsamg.h"
 #include "kernels.cuh"
@@ -62,8 +63,19 @@ struct DCSR {
   int* ci = nullptr;
   T* v = nullptr;
   int G = 1;
+  // SELL-32-sigma copy (matrices with at least kSellMinRows rows); use_sell picks it at launch
+  int nchunks = 0;
+  int* s_perm = nullptr;
+  int* s_rlen = nullptr;
+  int64_t* s_cptr = nullptr;
+  int* s_col = nullptr;
+  T* s_val = nullptr;
+  bool use_sell = false;
   bool present() const { return n > 0; }
 };
+
+constexpr int kSellMinRows = 16384;
+constexpr int kSellSigma = 4096;  // rows sorted by length inside windows of this many rows
 
 struct HostCSR {  // host copy used while building derived matrices
   int n = 0, m = 0;
@@ -112,6 +124,51 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
       CK(cudaMemcpy(d.v, tmp.data(), sizeof(T) * nnz, cudaMemcpyHostToDevice));
     }
   }
+  if (n >= kSellMinRows && nnz > 0) {
+    // SELL-32-sigma: sort rows by length (descending, stable) inside windows of sigma rows, cut
+    // into chunks of 32 positions, store each chunk column-major.
+    const int nch = (n + 31) / 32;
+    std::vector<int> perm((size_t)nch * 32, -1), rlen((size_t)nch * 32, 0), order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int w0 = 0; w0 < n; w0 += kSellSigma) {
+      const int w1 = std::min(n, w0 + kSellSigma);
+      std::stable_sort(order.begin() + w0, order.begin() + w1,
+                       [&](int a, int b) { return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]); });
+    }
+    for (int i = 0; i < n; ++i) {
+      perm[i] = order[i];
+      rlen[i] = rp[order[i] + 1] - rp[order[i]];
+    }
+    std::vector<int64_t> cptr(nch + 1, 0);
+    for (int c = 0; c < nch; ++c) {
+      int w = 0;
+      for (int l = 0; l < 32; ++l) w = std::max(w, rlen[(size_t)c * 32 + l]);
+      cptr[c + 1] = cptr[c] + 32 * (int64_t)w;
+    }
+    std::vector<int> scol(std::max<int64_t>(cptr[nch], 1), 0);
+    std::vector<T> sval(std::max<int64_t>(cptr[nch], 1), T(0));
+    for (int c = 0; c < nch; ++c)
+      for (int l = 0; l < 32; ++l) {
+        const int row = perm[(size_t)c * 32 + l];
+        if (row < 0) continue;
+        for (int j = 0; j < rlen[(size_t)c * 32 + l]; ++j) {
+          const int64_t q = cptr[c] + (int64_t)j * 32 + l;
+          scol[q] = ci[rp[row] + j];
+          sval[q] = (T)v[rp[row] + j];
+        }
+      }
+    d.nchunks = nch;
+    CK(cudaMalloc(&d.s_perm, sizeof(int) * perm.size()));
+    CK(cudaMemcpy(d.s_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_rlen, sizeof(int) * rlen.size()));
+    CK(cudaMemcpy(d.s_rlen, rlen.data(), sizeof(int) * rlen.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_cptr, sizeof(int64_t) * cptr.size()));
+    CK(cudaMemcpy(d.s_cptr, cptr.data(), sizeof(int64_t) * cptr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_col, sizeof(int) * scol.size()));
+    CK(cudaMemcpy(d.s_col, scol.data(), sizeof(int) * scol.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_val, sizeof(T) * sval.size()));
+    CK(cudaMemcpy(d.s_val, sval.data(), sizeof(T) * sval.size(), cudaMemcpyHostToDevice));
+  }
   const double avg = n ? (double)nnz / n : 0.0;
   if (n < 16384) {
     // small levels are latency bound: give each row enough lanes that every lane handles about
@@ -140,6 +197,11 @@ void release(DCSR<T>& d) {
   cudaFree(d.rp);
   cudaFree(d.ci);
   cudaFree(d.v);
+  cudaFree(d.s_perm);
+  cudaFree(d.s_rlen);
+  cudaFree(d.s_cptr);
+  cudaFree(d.s_col);
+  cudaFree(d.s_val);
   d = DCSR<T>();
 }
 
@@ -177,19 +239,73 @@ HostCSR tri_part(const nsamg_csr& A, bool lower, const std::vector<double>* rs, 
 // ------------------------------------------------------------------------------------------
 // Row-kernel launch
 // ------------------------------------------------------------------------------------------
+// Epilogue codes instantiated at compile time (the forms the engine builds); others fall back to
+// the run-time form.
+template <int G, typename TM, typename TX, typename TY>
+void launch_csr(const RowOp<TM, TX, TY>& op, int nb, cudaStream_t s) {
+  if constexpr (std::is_same<TX, TY>::value) {
+    switch (epi_code(op)) {
+      case 0: k_row<G, 0><<<nb, kThreads, 0, s>>>(op); return;
+      case 2: k_row<G, 2><<<nb, kThreads, 0, s>>>(op); return;
+      case 3: k_row<G, 3><<<nb, kThreads, 0, s>>>(op); return;
+      case 6: k_row<G, 6><<<nb, kThreads, 0, s>>>(op); return;
+      case 7: k_row<G, 7><<<nb, kThreads, 0, s>>>(op); return;
+      case 11: k_row<G, 11><<<nb, kThreads, 0, s>>>(op); return;
+      case 16: k_row<G, 16><<<nb, kThreads, 0, s>>>(op); return;
+      case 18: k_row<G, 18><<<nb, kThreads, 0, s>>>(op); return;
+      case 19: k_row<G, 19><<<nb, kThreads, 0, s>>>(op); return;
+      case 27: k_row<G, 27><<<nb, kThreads, 0, s>>>(op); return;
+      default: break;
+    }
+  } else {
+    if (epi_code(op) == 0) {
+      k_row<G, 0><<<nb, kThreads, 0, s>>>(op);
+      return;
+    }
+  }
+  k_row<G, E_RUNTIME><<<nb, kThreads, 0, s>>>(op);
+}
+
+template <typename TM, typename TX, typename TY>
+void launch_sell(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
+  const int nb = blocks_for((int64_t)op.sell.nchunks * 32);
+  if constexpr (std::is_same<TX, TY>::value) {
+    switch (epi_code(op)) {
+      case 0: k_sell<0><<<nb, kThreads, 0, s>>>(op); return;
+      case 3: k_sell<3><<<nb, kThreads, 0, s>>>(op); return;
+      case 7: k_sell<7><<<nb, kThreads, 0, s>>>(op); return;
+      case 11: k_sell<11><<<nb, kThreads, 0, s>>>(op); return;
+      case 16: k_sell<16><<<nb, kThreads, 0, s>>>(op); return;
+      case 19: k_sell<19><<<nb, kThreads, 0, s>>>(op); return;
+      case 27: k_sell<27><<<nb, kThreads, 0, s>>>(op); return;
+      default: break;
+    }
+  } else {
+    if (epi_code(op) == 0) {
+      k_sell<0><<<nb, kThreads, 0, s>>>(op);
+      return;
+    }
+  }
+  k_sell<E_RUNTIME><<<nb, kThreads, 0, s>>>(op);
+}
+
 template <typename TM, typename TX, typename TY>
 void launch_row(const RowOp<TM, TX, TY>& op, int G, cudaStream_t s) {
   if (op.n <= 0) return;
-  if (!op.v) G = 1;
   ++g_launches;
+  if (op.v && op.sell.nchunks > 0) {
+    launch_sell(op, s);
+    return;
+  }
+  if (!op.v) G = 1;
   const int nb = blocks_for((int64_t)op.n * G);
   switch (G) {
-    case 1: k_row<1, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
-    case 2: k_row<2, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
-    case 4: k_row<4, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
-    case 8: k_row<8, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
-    case 16: k_row<16, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
-    default: k_row<32, TM, TX, TY><<<nb, kThreads, 0, s>>>(op); break;
+    case 1: launch_csr<1>(op, nb, s); break;
+    case 2: launch_csr<2>(op, nb, s); break;
+    case 4: launch_csr<4>(op, nb, s); break;
+    case 8: launch_csr<8>(op, nb, s); break;
+    case 16: launch_csr<16>(op, nb, s); break;
+    default: launch_csr<32>(op, nb, s); break;
   }
 }
 
@@ -212,13 +328,26 @@ inline VC<T> cref(const T* p) {
 }
 
 // out = [add +] [scale *] (bscale*base -/+ M src)  -- builders for the common forms
-template <typename T>
-RowOp<T, T, T> op_mat(const DCSR<T>& M, VC<T> src) {
-  RowOp<T, T, T> op;
+template <typename TM, typename TX, typename TY>
+void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
   op.n = M.n;
   op.rp = M.rp;
   op.ci = M.ci;
   op.v = M.v;
+  if (M.use_sell) {
+    op.sell.nchunks = M.nchunks;
+    op.sell.perm = M.s_perm;
+    op.sell.rlen = M.s_rlen;
+    op.sell.cptr = M.s_cptr;
+    op.sell.col = M.s_col;
+    op.sell.val = M.s_val;
+  }
+}
+
+template <typename T>
+RowOp<T, T, T> op_mat(const DCSR<T>& M, VC<T> src) {
+  RowOp<T, T, T> op;
+  set_matrix(op, M);
   op.src = src;
   return op;
 }
@@ -591,6 +720,19 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
     }
   }
   M.G = bestG;
+  if (M.nchunks > 0) {  // the SELL-32-sigma layout competes with the best CSR shape
+    M.use_sell = true;
+    auto op = op_mat(M, cref((const T*)x));
+    op.out = vref(y);
+    launch_row(op, 1, s);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; ++r) launch_row(op, 1, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    M.use_sell = ms < best;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return NSAMG_OK;
@@ -629,10 +771,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
     const auto& A = h->lv[0].A;
     RowOp<double, float, double> op;
-    op.n = A.n;
-    op.rp = A.rp;
-    op.ci = A.ci;
-    op.v = A.v;
+    set_matrix(op, A);
     op.src = cref(z);
     op.out = vref(h->w);
     op.skip = skip;
@@ -801,10 +940,7 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
     const auto& A = h->lv[0].A;
     RowOp<double, float, double> op;
-    op.n = A.n;
-    op.rp = A.rp;
-    op.ci = A.ci;
-    op.v = A.v;
+    set_matrix(op, A);
     op.src = cref(z);
     op.out = vref(h->w);
     launch_row(op, A.G, s);
@@ -842,7 +978,8 @@ int check_params(const nsamg_params& p) {
   if (p.pre_sweeps < 0 || p.post_sweeps < 0 || p.coarse_sweeps < 1) return fail(NSAMG_ERR_INVALID_ARG, "bad sweep counts");
   if (p.restart < 1 || p.restart > NSAMG_MAX_RESTART) return fail(NSAMG_ERR_INVALID_ARG, "restart out of range 1..64");
   if (p.vcycle_fp32 != 0 && p.vcycle_fp32 != 1) return fail(NSAMG_ERR_INVALID_ARG, "vcycle_fp32 must be 0 or 1");
-  if (p.spmv_group < 0 || p.spmv_group > 32 || (p.spmv_group & (p.spmv_group - 1))) return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be 0 or a power of two <= 32");
+  if (p.spmv_group < -1 || p.spmv_group > 32 || (p.spmv_group > 0 && (p.spmv_group & (p.spmv_group - 1))))
+    return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be -1, 0 or a power of two <= 32");
   return NSAMG_OK;
 }
 
@@ -911,6 +1048,10 @@ int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaS
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
     for (DCSR<T>* M : mats) {
       if (!M->present()) continue;
+      if (group == -1) {  // SELL-32-sigma wherever the matrix has it, default CSR shape elsewhere
+        M->use_sell = M->nchunks > 0;
+        continue;
+      }
       if (group) {
         M->G = group;
         continue;
@@ -1634,7 +1775,9 @@ int nsamg_launches_per_step(nsamg_handle* h) {
 
 int nsamg_level_group(nsamg_handle* h, int level) {
   int rc = level_ok(h, level);
-  return rc ? rc : (h->fp32 ? h->lv32[level].A.G : h->lv[level].A.G);
+  if (rc) return rc;
+  if (h->fp32) return h->lv32[level].A.use_sell ? 0 : h->lv32[level].A.G;
+  return h->lv[level].A.use_sell ? 0 : h->lv[level].A.G;
 }
 
 int nsamg_level_spmv(nsamg_handle* h, int level, const double* d_x, double* d_y) {

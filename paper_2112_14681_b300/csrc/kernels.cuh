@@ -30,29 +30,71 @@ __host__ __device__ inline VRef<T> vref(T* p) { VRef<T> r; r.p = p; return r; }
 //   acc_i = sum_j M_ij src_j                              (skipped when M is absent)
 //   c_i   = bscale_i * base_i  (bscale optional; base absent = 0)
 //   t_i   = neg ? c_i - acc_i : c_i + acc_i
-//   out2_i = t_i (optional), t_i *= scale_i (optional), t_i += add_i (optional), out_i = t_i
+//   t_i *= scale_i (optional), t_i += add_i (optional), out_i = t_i
 // Every SpMV, residual, smoother pass, restriction and prolongation is one launch of this.
 // TM: matrix value type, TX: source vector type, TY: type of all other vectors / accumulation.
-// G threads cooperate on one row (G = 1, 2, 4, 8, 16, 32).
+// The matrix is CSR (G threads per row, G = 1..32) or SELL-32-sigma (one thread per row, rows
+// sorted by length inside windows, 32 rows per chunk stored column-major so that every load of
+// a warp is one contiguous segment). The epilogue form is a compile-time code where it is one of
+// the forms the engine uses, so each row costs exactly the FP64 operations it needs.
 // ------------------------------------------------------------------------------------------
+enum : int { E_NEG = 1, E_BASE = 2, E_BSCALE = 4, E_SCALE = 8, E_ADD = 16, E_RUNTIME = -1 };
+
+template <typename TM>
+struct SellView {
+  int nchunks = 0;
+  const int* perm = nullptr;      // position -> row (-1 for padding lanes), nchunks * 32
+  const int* rlen = nullptr;      // entries of the row at each position (0 for padding)
+  const int64_t* cptr = nullptr;  // chunk offsets, nchunks + 1
+  const int* col = nullptr;
+  const TM* val = nullptr;
+};
+
 template <typename TM, typename TX, typename TY>
 struct RowOp {
   int n = 0;
   const int* rp = nullptr;
   const int* ci = nullptr;
   const TM* v = nullptr;
+  SellView<TM> sell;              // used instead of rp/ci/v when sell.nchunks > 0
   VRef<const TX> src;
   VRef<const TY> base;
   const TY* bscale = nullptr;
   const TY* scale = nullptr;
   VRef<const TY> add;
   VRef<TY> out;
-  VRef<TY> out2;
   int neg = 0;
   const int* skip = nullptr;  // if set and *skip != 0 the launch does nothing (stopped solve)
 };
 
-template <int G, typename TM, typename TX, typename TY>
+template <typename TM, typename TX, typename TY>
+__host__ __device__ inline int epi_code(const RowOp<TM, TX, TY>& op) {
+  return (op.neg ? E_NEG : 0) | (op.base.p ? E_BASE : 0) | (op.bscale ? E_BSCALE : 0) | (op.scale ? E_SCALE : 0) |
+         (op.add.p ? E_ADD : 0);
+}
+
+template <int EPI, typename TM, typename TX, typename TY>
+__device__ __forceinline__ void row_epilogue(const RowOp<TM, TX, TY>& op, int row, TY acc) {
+  constexpr bool rt = EPI < 0;
+  const bool neg = rt ? op.neg != 0 : (EPI & E_NEG) != 0;
+  const bool hb = rt ? op.base.p != nullptr : (EPI & E_BASE) != 0;
+  const bool hbs = rt ? op.bscale != nullptr : (EPI & E_BSCALE) != 0;
+  const bool hs = rt ? op.scale != nullptr : (EPI & E_SCALE) != 0;
+  const bool ha = rt ? op.add.p != nullptr : (EPI & E_ADD) != 0;
+  TY t;
+  if (hb) {
+    TY c = op.base.get()[row];
+    if (hbs) c *= op.bscale[row];
+    t = neg ? c - acc : c + acc;
+  } else {
+    t = neg ? -acc : acc;
+  }
+  if (hs) t *= op.scale[row];
+  if (ha) t += op.add.get()[row];
+  op.out.get()[row] = t;
+}
+
+template <int G, int EPI, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
   if (op.skip && *op.skip) return;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,14 +117,26 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
     }
     if (lane != 0) return;
   }
-  const TY* base = op.base.get();
-  TY c = TY(0);
-  if (base) c = op.bscale ? op.bscale[row] * base[row] : base[row];
-  TY t = op.neg ? c - acc : c + acc;
-  if (op.out2.p) op.out2.get()[row] = t;
-  if (op.scale) t *= op.scale[row];
-  if (op.add.p) t += op.add.get()[row];
-  op.out.get()[row] = t;
+  row_epilogue<EPI>(op, row, acc);
+}
+
+template <int EPI, typename TM, typename TX, typename TY>
+__global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
+  if (op.skip && *op.skip) return;
+  const int chunk = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (chunk >= op.sell.nchunks) return;
+  const int pos = chunk * 32 + lane;
+  const int row = __ldg(op.sell.perm + pos);
+  const int len = __ldg(op.sell.rlen + pos);
+  const TX* __restrict__ src = op.src.get();
+  const TM* __restrict__ val = op.sell.val + op.sell.cptr[chunk] + lane;
+  const int* __restrict__ col = op.sell.col + op.sell.cptr[chunk] + lane;
+  TY acc = TY(0);
+#pragma unroll 4
+  for (int j = 0; j < len; ++j) acc = fma((TY)__ldg(val + 32 * j), (TY)__ldg(src + __ldg(col + 32 * j)), acc);
+  if (row < 0) return;
+  row_epilogue<EPI>(op, row, acc);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -277,7 +277,7 @@ def level_size(h: Handle, level: int) -> int:
 
 
 def level_group(h: Handle, level: int) -> int:
-    return _check(load().nsamg_level_group(h._h, level), allow=range(1, 33))
+    return _check(load().nsamg_level_group(h._h, level), allow=range(0, 33))
 
 
 def launches_per_step(h: Handle) -> int:

@@ -49,6 +49,9 @@ CASES = {
     "p23": lambda: (pressure3d_7pt(23, seed=3), dict(coarse_max=100)),
     # deeper hierarchy with a coarsest level solved by sweeps (no dense inverse)
     "p20s": lambda: (pressure3d_7pt(20, seed=5), dict(coarse_max=600, direct_max=0)),
+    # 30^3 = 27000 rows: finest level above the SELL threshold, several sorting windows, ragged
+    # last chunk
+    "p30": lambda: (pressure3d_7pt(30, seed=8), dict(coarse_max=200)),
 }
 
 _cache = {}
@@ -72,10 +75,13 @@ def rel_err_componentwise(y, yo, bound):
     return float(np.max(np.abs(y - yo) / np.maximum(bound, 1e-300)))
 
 
+@pytest.mark.parametrize("layout", [0, -1, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_level_spmv_residual_transfer(name):
+def test_level_spmv_residual_transfer(name, layout):
     A, H = case(name)
-    with nsamg.setup_hierarchy(H, nsamg.default_params()) as h:
+    with nsamg.setup_hierarchy(H, nsamg.default_params(spmv_group=layout)) as h:
+        if layout == -1 and H.levels[0].n >= 16384:
+            assert nsamg.level_group(h, 0) == 0
         assert nsamg.num_levels(h) == H.nlevels
         rng = np.random.default_rng(1)
         for l, lev in enumerate(H.levels):
@@ -105,9 +111,11 @@ SMOOTHERS = [(K.POLY_GS, 2), (K.POLY_GS, 1), (K.POLY_GS, 4), (K.ILU0, 3), (K.HYB
 @pytest.mark.parametrize("smoother,terms", SMOOTHERS)
 @pytest.mark.parametrize("backward", [False, True])
 @pytest.mark.parametrize("x_zero", [True, False])
-def test_smoother_sweep(smoother, terms, backward, x_zero):
-    A, H = case("p23")
-    kw = dict(smoother=smoother, neumann_terms=terms, ilu_terms_L=terms, ilu_terms_U=max(1, terms - 1))
+@pytest.mark.parametrize("name,layout", [("p23", 0), ("p30", -1)])
+def test_smoother_sweep(smoother, terms, backward, x_zero, name, layout):
+    A, H = case(name)
+    kw = dict(smoother=smoother, neumann_terms=terms, ilu_terms_L=terms, ilu_terms_U=max(1, terms - 1),
+              spmv_group=layout)
     p = nsamg.default_params(**kw)
     op = oracle_params(p)
     with nsamg.setup_hierarchy(H, p) as h:
@@ -153,7 +161,7 @@ def test_coarse_solve(name):
 @pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.ILU0, K.JACOBI_L1])
 def test_vcycle(name, smoother):
     A, H = case(name)
-    p = nsamg.default_params(**params_for(smoother))
+    p = nsamg.default_params(**params_for(smoother), spmv_group=-1 if name == "p30" else 0)
     with nsamg.setup_hierarchy(H, p) as h:
         r = rhs_uniform(A.shape[0], 11)
         z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
@@ -199,7 +207,7 @@ def test_gram_and_update(n, i):
 def test_solve_matches_oracle(name, smoother, graph):
     A, H = case(name)
     m = 30
-    p = nsamg.default_params(**params_for(smoother), restart=m, use_graph=graph)
+    p = nsamg.default_params(**params_for(smoother), restart=m, use_graph=graph, spmv_group=-1 if name == "p30" else 0)
     op = oracle_params(p)
     b = rhs_uniform(A.shape[0], 0)
     ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=m, rtol=1e-8)
@@ -304,10 +312,10 @@ def gamma(k):
     return k * U32 / (1 - k * U32)
 
 
-@pytest.mark.parametrize("name", ["c1", "p23"])
+@pytest.mark.parametrize("name", ["c1", "p23", "p30"])
 def test_fp32_level_kernels(name):
     A, H = case(name)
-    p = nsamg.default_params(vcycle_fp32=1)
+    p = nsamg.default_params(vcycle_fp32=1, spmv_group=-1 if name == "p30" else 0)
     with nsamg.setup_hierarchy(H, p) as h:
         rng = np.random.default_rng(5)
         for l, lev in enumerate(H.levels):
