@@ -613,22 +613,25 @@ def run_profile_kernel(args):
     nsamg.load()
     A, H, rhs = build_inputs()
     n = A.shape[0]
-    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=1, **SMOOTHERS["hybrid_ilu0"])
+    fp32 = args.profile_kernel.endswith("32")
+    kind = args.profile_kernel[:-2] if fp32 else args.profile_kernel
+    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=-1, vcycle_fp32=int(fp32),
+                             **{k: v for k, v in SMOOTHERS["hybrid_ilu0"].items() if k != "vcycle_fp32"})
     h = nsamg.setup_hierarchy(H, p)
     x = torch.from_numpy(rhs[0]).cuda()
     y = torch.empty_like(x)
     torch.cuda.synchronize()
-    if args.profile_kernel == "spmv":
+    if kind == "spmv":
         for _ in range(3):
             nsamg.level_spmv(h, 0, x, y)
-    elif args.profile_kernel == "l1spmv":
+    elif kind == "l1spmv":
         n1 = nsamg.level_size(h, 1)
         x1 = torch.rand(n1, dtype=torch.float64, device="cuda")
         y1 = torch.empty_like(x1)
         torch.cuda.synchronize()
         for _ in range(3):
             nsamg.level_spmv(h, 1, x1, y1)
-    elif args.profile_kernel == "ilu":
+    elif kind == "ilu":
         for _ in range(3):
             nsamg.level_smooth(h, 0, x, y, backward=False, x_is_zero=True)
     else:
@@ -640,7 +643,7 @@ def run_profile_kernel(args):
         ss = torch.empty(1, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         for _ in range(3):
-            if args.profile_kernel == "gram":
+            if kind == "gram":
                 nsamg.gram(n, i, V, ld, x, o)
             else:
                 nsamg.update(n, i, V, ld, x, 1.0, hc, ss)
@@ -711,7 +714,7 @@ def main():
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
     ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
     ap.add_argument("--c3-edge", type=int, default=C3_EDGE)
-    ap.add_argument("--profile-kernel", choices=["spmv", "l1spmv", "ilu", "gram", "update"],
+    ap.add_argument("--profile-kernel", choices=["spmv", "l1spmv", "ilu", "gram", "update", "spmv32", "ilu32"],
                     help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":

@@ -71,6 +71,7 @@ struct DCSR {
   int* s_col = nullptr;
   T* s_val = nullptr;
   bool use_sell = false;
+  int sell_k = 1;  // chunks per warp
   bool present() const { return n > 0; }
 };
 
@@ -158,6 +159,8 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
         }
       }
     d.nchunks = nch;
+    const double avg_row = (double)nnz / n;
+    d.sell_k = avg_row <= 8 ? 4 : avg_row <= 16 ? 2 : 1;
     CK(cudaMalloc(&d.s_perm, sizeof(int) * perm.size()));
     CK(cudaMemcpy(d.s_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d.s_rlen, sizeof(int) * rlen.size()));
@@ -266,27 +269,40 @@ void launch_csr(const RowOp<TM, TX, TY>& op, int nb, cudaStream_t s) {
   k_row<G, E_RUNTIME><<<nb, kThreads, 0, s>>>(op);
 }
 
-template <typename TM, typename TX, typename TY>
-void launch_sell(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
-  const int nb = blocks_for((int64_t)op.sell.nchunks * 32);
+template <int EPI, int K, typename TM, typename TX, typename TY>
+void launch_sell_one(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
+  const int nb = blocks_for((int64_t)((op.sell.nchunks + K - 1) / K) * 32);
+  k_sell<EPI, K, TM, TX, TY><<<nb, kThreads, 0, s>>>(op);
+}
+
+template <int K, typename TM, typename TX, typename TY>
+void launch_sell_k(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   if constexpr (std::is_same<TX, TY>::value) {
     switch (epi_code(op)) {
-      case 0: k_sell<0><<<nb, kThreads, 0, s>>>(op); return;
-      case 3: k_sell<3><<<nb, kThreads, 0, s>>>(op); return;
-      case 7: k_sell<7><<<nb, kThreads, 0, s>>>(op); return;
-      case 11: k_sell<11><<<nb, kThreads, 0, s>>>(op); return;
-      case 16: k_sell<16><<<nb, kThreads, 0, s>>>(op); return;
-      case 19: k_sell<19><<<nb, kThreads, 0, s>>>(op); return;
-      case 27: k_sell<27><<<nb, kThreads, 0, s>>>(op); return;
+      case 0: launch_sell_one<0, K>(op, s); return;
+      case 3: launch_sell_one<3, K>(op, s); return;
+      case 7: launch_sell_one<7, K>(op, s); return;
+      case 11: launch_sell_one<11, K>(op, s); return;
+      case 16: launch_sell_one<16, K>(op, s); return;
+      case 19: launch_sell_one<19, K>(op, s); return;
+      case 27: launch_sell_one<27, K>(op, s); return;
       default: break;
     }
   } else {
     if (epi_code(op) == 0) {
-      k_sell<0><<<nb, kThreads, 0, s>>>(op);
+      launch_sell_one<0, K>(op, s);
       return;
     }
   }
-  k_sell<E_RUNTIME><<<nb, kThreads, 0, s>>>(op);
+  launch_sell_one<E_RUNTIME, K>(op, s);
+}
+
+// Chunks per warp: 4 for short rows (latency bound), 2 up to 16 entries per row, else 1.
+template <typename TM, typename TX, typename TY>
+void launch_sell(const RowOp<TM, TX, TY>& op, int K, cudaStream_t s) {
+  if (K >= 4) launch_sell_k<4>(op, s);
+  else if (K == 2) launch_sell_k<2>(op, s);
+  else launch_sell_k<1>(op, s);
 }
 
 template <typename TM, typename TX, typename TY>
@@ -294,7 +310,7 @@ void launch_row(const RowOp<TM, TX, TY>& op, int G, cudaStream_t s) {
   if (op.n <= 0) return;
   ++g_launches;
   if (op.v && op.sell.nchunks > 0) {
-    launch_sell(op, s);
+    launch_sell(op, op.sell_k, s);
     return;
   }
   if (!op.v) G = 1;
@@ -341,6 +357,7 @@ void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
     op.sell.cptr = M.s_cptr;
     op.sell.col = M.s_col;
     op.sell.val = M.s_val;
+    op.sell_k = M.sell_k;
   }
 }
 
@@ -720,18 +737,27 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
     }
   }
   M.G = bestG;
-  if (M.nchunks > 0) {  // the SELL-32-sigma layout competes with the best CSR shape
-    M.use_sell = true;
-    auto op = op_mat(M, cref((const T*)x));
-    op.out = vref(y);
-    launch_row(op, 1, s);
-    CK(cudaEventRecord(e0, s));
-    for (int r = 0; r < 5; ++r) launch_row(op, 1, s);
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    M.use_sell = ms < best;
+  if (M.nchunks > 0) {  // the SELL-32-sigma layout (1, 2 or 4 chunks per warp) competes too
+    int bestK = 0;
+    for (int K : {1, 2, 4}) {
+      M.use_sell = true;
+      M.sell_k = K;
+      auto op = op_mat(M, cref((const T*)x));
+      op.out = vref(y);
+      launch_row(op, 1, s);
+      CK(cudaEventRecord(e0, s));
+      for (int r = 0; r < 5; ++r) launch_row(op, 1, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bestK = K;
+      }
+    }
+    M.use_sell = bestK > 0;
+    if (bestK) M.sell_k = bestK;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

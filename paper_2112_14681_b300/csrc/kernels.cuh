@@ -57,6 +57,7 @@ struct RowOp {
   const int* ci = nullptr;
   const TM* v = nullptr;
   SellView<TM> sell;              // used instead of rp/ci/v when sell.nchunks > 0
+  int sell_k = 1;                 // SELL chunks per warp (host-side launch choice)
   VRef<const TX> src;
   VRef<const TY> base;
   const TY* bscale = nullptr;
@@ -120,23 +121,45 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
   row_epilogue<EPI>(op, row, acc);
 }
 
-template <int EPI, typename TM, typename TX, typename TY>
+// K chunks per warp: the K chunks' loads are interleaved in one loop so that each thread keeps
+// K independent gather chains in flight (rows of 2-7 entries are otherwise latency bound).
+template <int EPI, int K, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
   if (op.skip && *op.skip) return;
-  const int chunk = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (chunk >= op.sell.nchunks) return;
-  const int pos = chunk * 32 + lane;
-  const int row = __ldg(op.sell.perm + pos);
-  const int len = __ldg(op.sell.rlen + pos);
   const TX* __restrict__ src = op.src.get();
-  const TM* __restrict__ val = op.sell.val + op.sell.cptr[chunk] + lane;
-  const int* __restrict__ col = op.sell.col + op.sell.cptr[chunk] + lane;
-  TY acc = TY(0);
-#pragma unroll 4
-  for (int j = 0; j < len; ++j) acc = fma((TY)__ldg(val + 32 * j), (TY)__ldg(src + __ldg(col + 32 * j)), acc);
-  if (row < 0) return;
-  row_epilogue<EPI>(op, row, acc);
+  {
+    const int c0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * K;
+    if (c0 >= op.sell.nchunks) return;
+    int row[K], len[K];
+    int64_t off[K];
+    TY acc[K];
+    int jmax = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int c = c0 + k;
+      const bool ok = c < op.sell.nchunks;
+      const int pos = c * 32 + lane;
+      row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
+      len[k] = ok ? __ldg(op.sell.rlen + pos) : 0;
+      off[k] = ok ? __ldg(op.sell.cptr + c) + lane : 0;
+      acc[k] = TY(0);
+      jmax = max(jmax, len[k]);
+    }
+#pragma unroll 2
+    for (int j = 0; j < jmax; ++j) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (j < len[k]) {
+          const int64_t q = off[k] + 32 * (int64_t)j;
+          acc[k] = fma((TY)__ldg(op.sell.val + q), (TY)__ldg(src + __ldg(op.sell.col + q)), acc[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (row[k] >= 0) row_epilogue<EPI>(op, row[k], acc[k]);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
