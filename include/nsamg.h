@@ -91,6 +91,9 @@ typedef struct {
   double relres_true;     /* ||b - A x|| / ||b|| from the final true residual (eq. relres)      */
   double relres_implicit; /* |g_{k+1}| / ||b|| from the Givens recurrence at exit               */
   double bnorm;           /* ||b||                                                              */
+  double nrbe;            /* norm-wise relative backward error ||r|| / (||b|| + ||A||_inf ||x||) of
+                             the final iterate (Sec. 3)                                          */
+  double orth_loss;       /* ||I - V^T V||_F of the last cycle's basis, from sqrt(2) ||L||_F (Sec. 3) */
 } nsamg_stats;
 
 typedef struct nsamg_handle nsamg_handle;

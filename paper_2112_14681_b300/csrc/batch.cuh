@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {  // loss of orthogonality of the cycle so far (Sec. 3): ||I - V^T V||_F ~ sqrt(2)||L||_F
+    double l2 = (i == 0) ? 0.0 : st->lsum;
+    for (int j = 0; j < i; ++j) l2 = fma(st->L[i * LD + j], st->L[i * LD + j], l2);
+    st->lsum = l2;
+    st->orth_loss = sqrt(2.0 * l2);
+  }
   if (!a.ctl->t_exact) {
     for (int q = threadIdx.x; q <= i; q += blockDim.x) {
       double acc = s_r[q];
@@ -374,32 +380,38 @@ __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
   const double* x = a.ctl->x;
   const int64_t r0 = a.off[sys] + (int64_t)(blockIdx.x - a.bstart[sys]) * a.rpb;
   const int64_t r1 = min(a.off[sys + 1], r0 + a.rpb);
-  double rr = 0.0, bb = 0.0;
+  double rr = 0.0, bb = 0.0, xx = 0.0;
   for (int64_t row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
     double acc = 0.0;
     const int rb = __ldg(ra.rp + row), re = __ldg(ra.rp + row + 1);
     for (int p = rb; p < re; ++p) acc = fma(__ldg(ra.v + p), x[__ldg(ra.ci + p)], acc);
     const double bi = b[row];
     const double ri = bi - acc;
+    const double xi = x[row];
     a.V[row] = ri;
     rr = fma(ri, ri, rr);
     bb = fma(bi, bi, bb);
+    xx = fma(xi, xi, xx);
   }
   const double tr = block_sum(rr, s_tmp);
   const double tb = block_sum(bb, s_tmp);
+  const double tx = block_sum(xx, s_tmp);
   if (threadIdx.x == 0) {
-    a.partials[2 * (int64_t)blockIdx.x] = tr;
-    a.partials[2 * (int64_t)blockIdx.x + 1] = tb;
+    a.partials[3 * (int64_t)blockIdx.x] = tr;
+    a.partials[3 * (int64_t)blockIdx.x + 1] = tb;
+    a.partials[3 * (int64_t)blockIdx.x + 2] = tx;
   }
   if (last_of_system(a.sticket + sys, nb)) {
-    double pr = 0.0, pb = 0.0;
+    double pr = 0.0, pb = 0.0, px = 0.0;
     const int b0 = a.bstart[sys];
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-      pr += __ldcg(a.partials + 2 * (int64_t)(b0 + q));
-      pb += __ldcg(a.partials + 2 * (int64_t)(b0 + q) + 1);
+      pr += __ldcg(a.partials + 3 * (int64_t)(b0 + q));
+      pb += __ldcg(a.partials + 3 * (int64_t)(b0 + q) + 1);
+      px += __ldcg(a.partials + 3 * (int64_t)(b0 + q) + 2);
     }
     const double R2 = block_sum(pr, s_tmp);
     const double B2 = block_sum(pb, s_tmp);
+    const double X2 = block_sum(px, s_tmp);
     if (threadIdx.x == 0) {
       if (ra.init) {
         st->bnorm = sqrt(B2);
@@ -413,6 +425,8 @@ __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
         const double scale = st->bnorm > 0.0 ? st->bnorm : 1.0;
         const double relres = sqrt(R2) / scale;
         st->relres_true = relres;
+        const double den = st->bnorm + st->anorm_inf * sqrt(X2);
+        st->nrbe = den > 0.0 ? sqrt(R2) / den : 0.0;
         const bool finite = isfinite(R2) && isfinite(st->bnorm);
         const bool conv = finite && relres <= a.ctl->rtol;
         const bool err = !finite || st->status < 0;

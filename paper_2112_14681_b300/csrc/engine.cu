@@ -84,6 +84,16 @@ struct HostCSR {  // host copy used while building derived matrices
   std::vector<double> v;
 };
 
+double norm_inf(const nsamg_csr& A) {
+  double mx = 0.0;
+  for (int i = 0; i < A.nrows; ++i) {
+    double r = 0.0;
+    for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) r += std::fabs(A.val[q]);
+    mx = std::max(mx, r);
+  }
+  return mx;
+}
+
 int validate(const nsamg_csr& A, bool square, bool need_diag, const char* name) {
   if (A.nrows <= 0) return fail(NSAMG_ERR_INVALID_ARG, std::string(name) + ": empty matrix");
   if (!A.rowptr || (A.nnz > 0 && (!A.col || !A.val))) return fail(NSAMG_ERR_INVALID_ARG, std::string(name) + ": null array");
@@ -419,6 +429,7 @@ struct nsamg_handle {
   int launches_per_step = 0;
   struct BatchData* batch = nullptr;  // set for handles made by nsamg_batch_setup
   bool shared_mats = false;           // a solver context: matrices belong to another handle
+  double anorm_inf = 0.0;             // ||A_0||_inf (for the backward error)
   size_t ctx_bytes = 0;               // device bytes of the per-solve workspace (server accounting)
 };
 
@@ -1135,7 +1146,7 @@ int alloc_workspace(nsamg_handle* h) {
   h->update_blocks = 8 * sms;
   const int resid_blocks = blocks_for((int64_t)h->n * 32);
   h->partial_cap = std::max<int64_t>({(int64_t)h->gram_blocks * 2 * (kMaxM + 1), (int64_t)h->update_blocks,
-                                      2 * (int64_t)resid_blocks});
+                                      3 * (int64_t)resid_blocks});
   CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
@@ -1163,6 +1174,7 @@ int finish_graph(nsamg_handle* h) {
 
 // Host-side description of a batch (concatenated systems) handed to setup_impl.
 struct BatchInit {
+  std::vector<double> anorm;         // ||A_0||_inf per system
   std::vector<int64_t> off;          // nsys + 1 finest-level row offsets
   std::vector<int64_t> coff;         // nsys + 1 coarsest-level row offsets
   std::vector<int64_t> cblk;         // nsys offsets of each dense inverse block
@@ -1223,6 +1235,8 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     }
   }
   if ((rc = alloc_workspace(h))) return rc;
+  h->anorm_inf = norm_inf(H->levels[0].A);
+  CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
   if (bi && (rc = setup_batch_data(h, *bi))) return rc;
   // Threads per row: fixed by the caller or tuned on the device.
   if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, h->stream))) return rc;
@@ -1296,6 +1310,9 @@ int clone_context(nsamg_handle* parent, nsamg_handle** out) {
   if ((rc = clone_level_vectors(parent->lv, h->lv))) return bail(rc);
   if ((rc = clone_level_vectors(parent->lv32, h->lv32))) return bail(rc);
   if ((rc = alloc_workspace(h))) return bail(rc);
+  h->anorm_inf = parent->anorm_inf;
+  if (cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(NSAMG_ERR_CUDA, "state"));
   size_t vec_bytes = 0;
   for (auto& L : h->lv) vec_bytes += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
   for (auto& L : h->lv32) vec_bytes += 6 * sizeof(float) * (size_t)L.n;
@@ -1329,7 +1346,7 @@ int setup_batch_data(nsamg_handle* h, const BatchInit& bi) {
     }
     B->nblocks[k] = bs[B->nsys];
     if ((rc = upload_raw(bs, &B->d_bstart[k]))) return rc;
-    const int64_t per = (k == BatchData::kGram) ? 2 * (kMaxM + 1) : 2;
+    const int64_t per = (k == BatchData::kGram) ? 2 * (kMaxM + 1) : 3;
     maxpart = std::max<int64_t>(maxpart, per * B->nblocks[k]);
   }
   CK(cudaMalloc(&B->partials, sizeof(double) * maxpart));
@@ -1339,6 +1356,8 @@ int setup_batch_data(nsamg_handle* h, const BatchInit& bi) {
   CK(cudaMemset(B->d_gticket, 0, sizeof(unsigned) * 4));
   CK(cudaMalloc(&B->d_st, sizeof(GState) * B->nsys));
   CK(cudaMemset(B->d_st, 0, sizeof(GState) * B->nsys));
+  for (int sI = 0; sI < B->nsys && sI < (int)bi.anorm.size(); ++sI)
+    CK(cudaMemcpy(&B->d_st[sI].anorm_inf, &bi.anorm[sI], sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMallocHost(&B->h_st, sizeof(GState) * B->nsys));
   CK(cudaMalloc(&B->d_ctl, sizeof(BatchCtl)));
   CK(cudaMemset(B->d_ctl, 0, sizeof(BatchCtl)));
@@ -1476,6 +1495,8 @@ int solve_batch_impl(nsamg_handle* h, const double* d_b, double* d_x, double rto
       stats[sI].status = status;
       stats[sI].relres_true = g.relres_true;
       stats[sI].relres_implicit = g.relres_implicit;
+      stats[sI].nrbe = g.nrbe;
+      stats[sI].orth_loss = g.orth_loss;
       stats[sI].bnorm = g.bnorm;
     }
     if (status < 0) worst = status;
@@ -1630,6 +1651,8 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
     stats->status = status;
     stats->relres_true = hs->relres_true;
     stats->relres_implicit = hs->relres_implicit;
+    stats->nrbe = hs->nrbe;
+    stats->orth_loss = hs->orth_loss;
     stats->bnorm = hs->bnorm;
   }
   if (status < 0) return fail(status, status == NSAMG_ERR_NONFINITE ? "non-finite value in the iteration" : "solve failed");
@@ -1943,6 +1966,7 @@ int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_par
   bi.off.push_back(0);
   bi.coff.push_back(0);
   for (int sI = 0; sI < count; ++sI) {
+    bi.anorm.push_back(norm_inf(hs[sI].levels[0].A));
     bi.off.push_back(bi.off.back() + hs[sI].levels[0].A.nrows);
     const int nc = hs[sI].levels[nl - 1].A.nrows;
     bi.coff.push_back(bi.coff.back() + nc);
@@ -2132,6 +2156,8 @@ void server_collect(nsamg_server* S) {
     r.stats.status = status;
     r.stats.relres_true = g->relres_true;
     r.stats.relres_implicit = g->relres_implicit;
+    r.stats.nrbe = g->nrbe;
+    r.stats.orth_loss = g->orth_loss;
     r.stats.bnorm = g->bnorm;
     r.status = status;
     r.state = 2;

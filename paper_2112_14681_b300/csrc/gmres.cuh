@@ -201,6 +201,12 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {  // loss of orthogonality of the cycle so far (Sec. 3): ||I - V^T V||_F ~ sqrt(2)||L||_F
+    double l2 = (i == 0) ? 0.0 : st->lsum;
+    for (int j = 0; j < i; ++j) l2 = fma(st->L[i * LD + j], st->L[i * LD + j], l2);
+    st->lsum = l2;
+    st->orth_loss = sqrt(2.0 * l2);
+  }
   if (!st->t_exact) {
     // h = (I - L) r: row q of L times r, one thread per row.
     for (int q = threadIdx.x; q <= i; q += blockDim.x) {
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int row = (int)(gid / G);
   const int lane = (int)(gid & (G - 1));
-  double rr = 0.0, bb = 0.0;
+  double rr = 0.0, bb = 0.0, xx = 0.0;
   if (row < a.n) {
     double acc = 0.0;
     const int rb = __ldg(a.rp + row), re = __ldg(a.rp + row + 1);
@@ -421,25 +427,31 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
     if (lane == 0) {
       const double bi = b[row];
       const double ri = bi - acc;
+      const double xi = x[row];
       a.r[row] = ri;
       rr = ri * ri;
       bb = bi * bi;
+      xx = xi * xi;
     }
   }
   const double tr = block_sum(rr, s_tmp);
   const double tb = block_sum(bb, s_tmp);
+  const double tx = block_sum(xx, s_tmp);
   if (threadIdx.x == 0) {
-    a.scr.partials[2 * (int64_t)blockIdx.x] = tr;
-    a.scr.partials[2 * (int64_t)blockIdx.x + 1] = tb;
+    a.scr.partials[3 * (int64_t)blockIdx.x] = tr;
+    a.scr.partials[3 * (int64_t)blockIdx.x + 1] = tb;
+    a.scr.partials[3 * (int64_t)blockIdx.x + 2] = tx;
   }
   if (!last_block(a.scr.ticket)) return;
-  double pr = 0.0, pb = 0.0;
+  double pr = 0.0, pb = 0.0, px = 0.0;
   for (int bI = threadIdx.x; bI < (int)gridDim.x; bI += blockDim.x) {
-    pr += __ldcg(a.scr.partials + 2 * (int64_t)bI);
-    pb += __ldcg(a.scr.partials + 2 * (int64_t)bI + 1);
+    pr += __ldcg(a.scr.partials + 3 * (int64_t)bI);
+    pb += __ldcg(a.scr.partials + 3 * (int64_t)bI + 1);
+    px += __ldcg(a.scr.partials + 3 * (int64_t)bI + 2);
   }
   const double R2 = block_sum(pr, s_tmp);
   const double B2 = block_sum(pb, s_tmp);
+  const double X2 = block_sum(px, s_tmp);
   if (threadIdx.x == 0) {
     if (a.init) {
       st->bnorm = sqrt(B2);
@@ -453,6 +465,9 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
     const double scale = st->bnorm > 0.0 ? st->bnorm : 1.0;
     const double relres = sqrt(R2) / scale;
     st->relres_true = relres;
+    // norm-wise relative backward error (Sec. 3): ||r|| / (||b|| + ||A||_inf ||x||)
+    const double den = st->bnorm + st->anorm_inf * sqrt(X2);
+    st->nrbe = den > 0.0 ? sqrt(R2) / den : 0.0;
     const bool finite = isfinite(R2) && isfinite(st->bnorm);
     const bool conv = finite && relres <= st->rtol;
     const bool err = !finite || st->status < 0;

@@ -219,6 +219,10 @@ struct GState {
   double bnorm;
   double relres_true;
   double relres_implicit;
+  double anorm_inf;   // ||A||_inf of the finest operator (set at setup)
+  double nrbe;        // ||r|| / (||b|| + ||A||_inf ||x||) of the last true residual
+  double lsum;        // sum of squares of the L entries of the current cycle
+  double orth_loss;   // sqrt(2 lsum): ||I - V^T V||_F of the last cycle (diagonal terms ~ eps)
   // Arnoldi / least-squares data (row-major with stride kMaxM + 1)
   double beta[kMaxM + 1];
   double invbeta[kMaxM + 1];

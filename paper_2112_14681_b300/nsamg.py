@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("relres_true", ctypes.c_double), ("relres_implicit", ctypes.c_double),
-                ("bnorm", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("nrbe", ctypes.c_double), ("orth_loss", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -396,3 +396,22 @@ def test_c3_type_graded_27pt_fp32_vcycle():
         nsamg.solve(h, dev(b), x2, rtol=1e-12, maxit=1000)
     ref2 = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=30, rtol=1e-12, maxit=1000)
     assert np.linalg.norm(host(x2) - ref2.x) / np.linalg.norm(ref2.x) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["c1", "p23"])
+def test_backward_error_and_orthogonality_diagnostics(name):
+    """NRBE (Sec. 3: ||r|| / (||b|| + ||A||_inf ||x||)) matches the value computed from the
+    returned x on the host; the loss of orthogonality of the last cycle is O(eps * kappa(B))."""
+    A, H = case(name)
+    b = rhs_uniform(A.shape[0], 0)
+    with nsamg.setup_hierarchy(H, nsamg.default_params()) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        xs = host(x)
+    r = b - A @ xs
+    nrbe = np.linalg.norm(r) / (np.linalg.norm(b) + abs(A).sum(axis=1).max() * np.linalg.norm(xs))
+    assert st["nrbe"] == pytest.approx(nrbe, rel=1e-6)
+    assert 0.0 < st["orth_loss"] <= 1e3 * np.finfo(float).eps / st["relres_implicit"]
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, K.SmootherParams()), m=30, rtol=1e-8)
+    ref_loss = np.sqrt(2.0) * np.linalg.norm(ref.L)
+    assert st["orth_loss"] == pytest.approx(ref_loss, rel=0.5, abs=1e-15)
