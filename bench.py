@@ -60,6 +60,16 @@ def build_inputs():
     return A, H, rhs
 
 
+def ilut_variant(H, droptol: float = 1e-2, lfil: int = 5):
+    """The same hierarchy with ILUT(droptol, lfil) + Ruiz factors on the finest level (Alg. 2)."""
+    import copy
+    from workloads.hierarchy import Hierarchy, ilut
+    l0 = copy.copy(H.levels[0])
+    l0.ilu_L, l0.ilu_U, l0.ilu_dr, l0.ilu_dc = ilut(l0.A, droptol, lfil)
+    l0.ilu_dinv, l0.ilu_form = None, 1
+    return Hierarchy(levels=[l0] + H.levels[1:], coarse_inv=H.coarse_inv, theta=H.theta, seed=H.seed, info=H.info)
+
+
 # Batched workload (C4): 256 independent 7-point systems, cube edge ~ U{16..64}, 4 levels each.
 BATCH_COUNT = 256
 BATCH_EDGES = (16, 64)
@@ -114,6 +124,8 @@ SMOOTHERS = {
     "hybrid_ilu0_fp32v": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1,
                               vcycle_fp32=1),
     "poly_gs_fp32v": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1, vcycle_fp32=1),
+    # ILUT(1e-2, 5) with Ruiz-scaled U and 3 + 3 Jacobi terms on the finest level (Alg. 2)
+    "hybrid_ilut": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
 }
 
 
@@ -267,9 +279,10 @@ def run_gpu(args):
 
     results = {}
     handles = {}
+    Ht = ilut_variant(H)
     for name, kw in SMOOTHERS.items():
         p = nsamg.default_params(restart=RESTART, **kw)
-        handles[name] = nsamg.setup_hierarchy(H, p, stream=stream.cuda_stream)
+        handles[name] = nsamg.setup_hierarchy(Ht if name == "hybrid_ilut" else H, p, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     main = "hybrid_ilu0"
     for name, h in handles.items():

@@ -52,11 +52,18 @@ typedef struct {
 
 /* One level of a Ruge-Stuben hierarchy built on the host (input generation).
  * A: level operator A_l. P: prolongation n_l x n_{l+1}; R = P^T: restriction n_{l+1} x n_l
- * (both absent on the coarsest level). ilu_L / ilu_U / ilu_dinv: optional ILU(0) factors with
- * A_l ~ (I + L_s) diag(1/ilu_dinv) (I + U_s) (Sec. 5.3.2); ilu_L.nrows = 0 when absent. */
+ * (both absent on the coarsest level). Optional incomplete factors (ilu_L.nrows = 0 when absent):
+ *   ilu_form 0, ILU(0) in row-scaled LDU form (Sec. 5.3.2): A_l ~ (I + L_s) diag(1/ilu_dinv)
+ *     (I + U_s), ilu_L = L_s strictly lower, ilu_U = U_s strictly upper; ilu_dr/ilu_dc unused.
+ *   ilu_form 1, ILUT with Ruiz scaling (Algorithm 2): A_l ~ (I + L_s) U, ilu_L = L_s, ilu_U = U
+ *     upper with its diagonal, ilu_dr / ilu_dc the row / column scalings of U (D_r U D_c has
+ *     unit row and column maxima; NULL = no scaling); ilu_dinv unused. */
 typedef struct {
   nsamg_csr A, P, R, ilu_L, ilu_U;
   const double* ilu_dinv;
+  int32_t ilu_form;
+  const double* ilu_dr;
+  const double* ilu_dc;
 } nsamg_level_desc;
 
 typedef struct {

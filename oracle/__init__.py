@@ -6,7 +6,8 @@ CUDA path; both sides receive the same inputs from the `workloads` generators.
 
 Contents (each function cites the passage it restates):
   kernels  -- SpMV, splitting A = L + D + U, smoother sweeps (polynomial Gauss-Seidel, ILU(0)
-              with Neumann-series triangular solves, l1-Jacobi) in a "definition" mode
+              with Neumann-series triangular solves, ILUT with Jacobi iterations and Ruiz
+              scaling (Algorithm 2), l1-Jacobi) in a "definition" mode
               (explicit truncated power sums) and a "direct" mode (forward/backward
               substitution), restriction, prolongation, coarse solve, Gram reduction and
               basis update of the one-reduce Arnoldi step.

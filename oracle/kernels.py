@@ -138,6 +138,34 @@ def ilu0_sweep(Ls, Us, dinv, A, b, x, terms_L: int, terms_U: int, mode: str = "d
     return x + v
 
 
+def ilut_sweep(Ls, U, dr, dc, A, b, x, terms_L: int, terms_U: int, mode: str = "definition"):
+    """One ILUT smoother sweep with Jacobi triangular iterations and Ruiz scaling (Algorithm 2),
+    applied to the residual equation: x <- x + v with r = b - A x and
+      y^(k) = y^(k-1) + (r - L y^(k-1)),  L = I + L_s, y^(0) = 0, k = 1..terms_L;
+      U~ = D_r U D_c, y~ = D_r y, D = diag(U~)^-1;
+      v^(k) = v^(k-1) + D (y~ - U~ v^(k-1)), v^(0) = 0, k = 1..terms_U;  v = D_c v.
+    (U v = y is equivalent to U~ (D_c^-1 v) = D_r y, which fixes where D_r and D_c act.)
+    direct: y = L^-1 r and v = U^-1 y by substitution (the limit of both iterations)."""
+    r = residual(A, b, x)
+    n = r.size
+    I = sp.identity(n, format="csr")
+    Lfull = sp.csr_matrix(I + Ls)
+    if mode == "direct":
+        y = spla.spsolve_triangular(Lfull, r, lower=True, unit_diagonal=True)
+        v = spla.spsolve_triangular(sp.csr_matrix(U), y, lower=False)
+        return x + v
+    y = np.zeros(n)
+    for _ in range(terms_L):
+        y = y + (r - Lfull @ y)
+    Ut = sp.csr_matrix(sp.diags(dr) @ U @ sp.diags(dc))
+    yt = dr * y
+    Dinv = 1.0 / Ut.diagonal()
+    v = np.zeros(n)
+    for _ in range(terms_U):
+        v = v + Dinv * (yt - Ut @ v)
+    return x + dc * v
+
+
 def l1_jacobi_sweep(A, b, x):
     """x <- x + D_l1^-1 (b - A x) (Sec. 5.3.1, Jacobi in non-compact form, with l1 diagonal)."""
     return x + residual(A, b, x) / l1_diagonal(A)

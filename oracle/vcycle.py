@@ -19,10 +19,11 @@ def level_smoother(H, l: int, p: K.SmootherParams) -> str:
     lev = H.levels[l]
     if p.smoother == K.JACOBI_L1:
         return "jacobi"
+    kind = "ilut" if getattr(lev, "ilu_form", 0) == 1 else "ilu"
     if p.smoother == K.ILU0 and lev.ilu_L is not None:
-        return "ilu"
+        return kind
     if p.smoother == K.HYBRID_ILU0 and l == 0 and lev.ilu_L is not None:
-        return "ilu"
+        return kind
     return "poly"
 
 
@@ -31,6 +32,9 @@ def smooth(H, l: int, b, x, p: K.SmootherParams, backward: bool):
     kind = level_smoother(H, l, p)
     if kind == "ilu":
         return K.ilu0_sweep(lev.ilu_L, lev.ilu_U, lev.ilu_dinv, lev.A, b, x, p.ilu_terms_L, p.ilu_terms_U, p.mode)
+    if kind == "ilut":
+        return K.ilut_sweep(lev.ilu_L, lev.ilu_U, lev.ilu_dr, lev.ilu_dc, lev.A, b, x, p.ilu_terms_L, p.ilu_terms_U,
+                            p.mode)
     if kind == "jacobi":
         return K.l1_jacobi_sweep(lev.A, b, x)
     return K.poly_gs_sweep(lev.A, b, x, p.neumann_terms, backward=backward, mode=p.mode)

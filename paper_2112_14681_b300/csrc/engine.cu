@@ -394,6 +394,7 @@ struct Level {
   T* dinv = nullptr;
   T* dl1inv = nullptr;
   T* idinv = nullptr;
+  T* idc = nullptr;  // column scaling applied to the U-series result (ILUT with Ruiz), or null
   T *b = nullptr, *x = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
   char kind = 'p';  // 'p' poly GS, 'i' ILU, 'j' l1-Jacobi
 };
@@ -585,6 +586,7 @@ void sweep_ilu(Level<T>& L, VC<T> b, VRef<T> x, bool x_zero, int tL, int tU, con
   if (tU == 1) {
     auto op = op_vec<T>(L.n);
     op.base = cref((const T*)f);
+    op.bscale = L.idc;
     if (!x_zero) op.add = cref(x);
     op.out = x;
     run(op, 1, c);
@@ -596,6 +598,7 @@ void sweep_ilu(Level<T>& L, VC<T> b, VRef<T> x, bool x_zero, int tL, int tU, con
     op.base = cref((const T*)f);
     op.neg = 1;
     if (last) {
+      op.scale = L.idc;  // x (+)= D_c v for ILUT with Ruiz scaling
       if (!x_zero) op.add = cref(x);
       op.out = x;
     } else {
@@ -1065,9 +1068,37 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
     const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
     if (want_ilu && D.ilu_L.nrows > 0 && l < nl - 1) {
       if ((rc = upload(D.ilu_L, L.iL))) return rc;
-      if ((rc = upload(D.ilu_U, L.iU))) return rc;
-      std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
-      if ((rc = upload_vec(idv, &L.idinv))) return rc;
+      if (D.ilu_form == 0) {
+        if ((rc = upload(D.ilu_U, L.iU))) return rc;
+        std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
+        if ((rc = upload_vec(idv, &L.idinv))) return rc;
+      } else {
+        // Algorithm 2: Jacobi on U~ = D_r U D_c with D = diag(U~)^-1, i.e. v <- D D_r y - (D U~_strict) v,
+        // then x += D_c v. Pre-scale here: U_hat = D U~_strict, f-scaling D D_r, column scaling D_c.
+        const nsamg_csr& U = D.ilu_U;
+        std::vector<double> dr(L.n, 1.0), dc(L.n, 1.0), fs(L.n), dg(L.n, 0.0);
+        if (D.ilu_dr) dr.assign(D.ilu_dr, D.ilu_dr + L.n);
+        if (D.ilu_dc) dc.assign(D.ilu_dc, D.ilu_dc + L.n);
+        HostCSR uh;
+        uh.n = uh.m = L.n;
+        uh.rp.assign(L.n + 1, 0);
+        for (int i = 0; i < L.n; ++i) {
+          for (int64_t q = U.rowptr[i]; q < U.rowptr[i + 1]; ++q)
+            if (U.col[q] == i) dg[i] = dr[i] * U.val[q] * dc[i];
+          if (dg[i] == 0.0) return fail(NSAMG_ERR_BAD_MATRIX, "level " + std::to_string(l) + ": zero diagonal in the ILUT factor U");
+          fs[i] = dr[i] / dg[i];
+          for (int64_t q = U.rowptr[i]; q < U.rowptr[i + 1]; ++q) {
+            const int j = U.col[q];
+            if (j <= i) continue;
+            uh.ci.push_back(j);
+            uh.v.push_back(dr[i] * U.val[q] * dc[j] / dg[i]);
+          }
+          uh.rp[i + 1] = (int)uh.ci.size();
+        }
+        if ((rc = upload(uh, L.iU))) return rc;
+        if ((rc = upload_vec(fs, &L.idinv))) return rc;
+        if ((rc = upload_vec(dc, &L.idc))) return rc;
+      }
       L.ilu = true;
     }
     L.kind = (p.smoother == NSAMG_SMOOTHER_JACOBI_L1) ? 'j' : (L.ilu ? 'i' : 'p');
@@ -1117,7 +1148,7 @@ void release_levels(std::vector<Level<T>>& lvs) {
   for (auto& L : lvs) {
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
     for (DCSR<T>* M : mats) release(*M);
-    T* vecs[] = {L.dinv, L.dl1inv, L.idinv, L.b, L.x, L.r, L.t1, L.t2, L.t3};
+    T* vecs[] = {L.dinv, L.dl1inv, L.idinv, L.idc, L.b, L.x, L.r, L.t1, L.t2, L.t3};
     for (T* v : vecs) cudaFree(v);
   }
   lvs.clear();
@@ -1215,7 +1246,8 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     if (D.ilu_L.nrows > 0) {
       if ((rc = validate(D.ilu_L, true, false, (nm + " ilu_L").c_str()))) return rc;
       if ((rc = validate(D.ilu_U, true, false, (nm + " ilu_U").c_str()))) return rc;
-      if (!D.ilu_dinv || D.ilu_L.nrows != D.A.nrows || D.ilu_U.nrows != D.A.nrows)
+      if (D.ilu_form != 0 && D.ilu_form != 1) return fail(NSAMG_ERR_INVALID_ARG, nm + ": ilu_form must be 0 or 1");
+      if ((D.ilu_form == 0 && !D.ilu_dinv) || D.ilu_L.nrows != D.A.nrows || D.ilu_U.nrows != D.A.nrows)
         return fail(NSAMG_ERR_BAD_MATRIX, nm + ": ILU factor dimensions");
     }
   }
@@ -1986,7 +2018,8 @@ int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_par
         P.push_back(&D.P);
         R.push_back(&D.R);
       }
-      has_ilu = has_ilu && D.ilu_L.nrows > 0 && D.ilu_dinv;
+      has_ilu = has_ilu && D.ilu_L.nrows > 0 && D.ilu_form == hs[0].levels[l].ilu_form &&
+                (D.ilu_form == 1 || D.ilu_dinv);
       iL.push_back(&D.ilu_L);
       iU.push_back(&D.ilu_U);
     }
@@ -2000,13 +2033,28 @@ int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_par
     if (has_ilu) {
       O.ilu_L = concat_csr(iL, store);
       O.ilu_U = concat_csr(iU, store);
-      store.dbls.emplace_back();
-      auto& d = store.dbls.back();
+      O.ilu_form = hs[0].levels[l].ilu_form;
+      auto cat = [&](const double* const* ptrs, double dflt) {
+        store.dbls.emplace_back();
+        auto& d = store.dbls.back();
+        for (int sI = 0; sI < count; ++sI) {
+          const int nr = hs[sI].levels[l].A.nrows;
+          if (ptrs[sI]) d.insert(d.end(), ptrs[sI], ptrs[sI] + nr);
+          else d.insert(d.end(), nr, dflt);
+        }
+        return d.data();
+      };
+      std::vector<const double*> pd(count), pr(count), pc(count);
       for (int sI = 0; sI < count; ++sI) {
-        const nsamg_level_desc& D = hs[sI].levels[l];
-        d.insert(d.end(), D.ilu_dinv, D.ilu_dinv + D.A.nrows);
+        pd[sI] = hs[sI].levels[l].ilu_dinv;
+        pr[sI] = hs[sI].levels[l].ilu_dr;
+        pc[sI] = hs[sI].levels[l].ilu_dc;
       }
-      O.ilu_dinv = d.data();
+      if (O.ilu_form == 0) O.ilu_dinv = cat(pd.data(), 1.0);
+      else {
+        O.ilu_dr = cat(pr.data(), 1.0);
+        O.ilu_dc = cat(pc.data(), 1.0);
+      }
     }
   }
   nsamg_hierarchy_desc H{};

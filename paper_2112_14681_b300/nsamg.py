@@ -31,7 +31,8 @@ class Csr(ctypes.Structure):
 
 
 class LevelDesc(ctypes.Structure):
-    _fields_ = [("A", Csr), ("P", Csr), ("R", Csr), ("ilu_L", Csr), ("ilu_U", Csr), ("ilu_dinv", ctypes.c_void_p)]
+    _fields_ = [("A", Csr), ("P", Csr), ("R", Csr), ("ilu_L", Csr), ("ilu_U", Csr), ("ilu_dinv", ctypes.c_void_p),
+                ("ilu_form", ctypes.c_int32), ("ilu_dr", ctypes.c_void_p), ("ilu_dc", ctypes.c_void_p)]
 
 
 class HierarchyDesc(ctypes.Structure):
@@ -171,6 +172,13 @@ def _hierarchy_desc(hierarchy, keep: list) -> HierarchyDesc:
             d = np.ascontiguousarray(lev.ilu_dinv, dtype=np.float64)
             keep.append(d)
             arr[l].ilu_dinv = d.ctypes.data
+        arr[l].ilu_form = int(getattr(lev, "ilu_form", 0))
+        for fld in ("ilu_dr", "ilu_dc"):
+            vec = getattr(lev, fld, None)
+            if vec is not None:
+                d = np.ascontiguousarray(vec, dtype=np.float64)
+                keep.append(d)
+                setattr(arr[l], fld, d.ctypes.data)
     desc = HierarchyDesc()
     desc.nlevels = len(levels)
     desc.levels = arr

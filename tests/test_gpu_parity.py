@@ -52,6 +52,8 @@ CASES = {
     # 30^3 = 27000 rows: finest level above the SELL threshold, several sorting windows, ragged
     # last chunk
     "p30": lambda: (pressure3d_7pt(30, seed=8), dict(coarse_max=200)),
+    # ILUT(1e-2, 5) factors with Ruiz-scaled U on every level (Algorithm 2)
+    "p23t": lambda: (pressure3d_7pt(23, seed=3), dict(coarse_max=100, ilu="ilut", droptol=1e-2, lfil=5)),
 }
 
 _cache = {}
@@ -111,7 +113,7 @@ SMOOTHERS = [(K.POLY_GS, 2), (K.POLY_GS, 1), (K.POLY_GS, 4), (K.ILU0, 3), (K.HYB
 @pytest.mark.parametrize("smoother,terms", SMOOTHERS)
 @pytest.mark.parametrize("backward", [False, True])
 @pytest.mark.parametrize("x_zero", [True, False])
-@pytest.mark.parametrize("name,layout", [("p23", 0), ("p30", -1)])
+@pytest.mark.parametrize("name,layout", [("p23", 0), ("p30", -1), ("p23t", 0)])
 def test_smoother_sweep(smoother, terms, backward, x_zero, name, layout):
     A, H = case(name)
     kw = dict(smoother=smoother, neumann_terms=terms, ilu_terms_L=terms, ilu_terms_U=max(1, terms - 1),
@@ -129,6 +131,9 @@ def test_smoother_sweep(smoother, terms, backward, x_zero, name, layout):
             kind = level_smoother(H, l, op)
             if kind == "ilu":
                 want = K.ilu0_sweep(lev.ilu_L, lev.ilu_U, lev.ilu_dinv, lev.A, b, x0, op.ilu_terms_L, op.ilu_terms_U)
+            elif kind == "ilut":
+                want = K.ilut_sweep(lev.ilu_L, lev.ilu_U, lev.ilu_dr, lev.ilu_dc, lev.A, b, x0, op.ilu_terms_L,
+                                    op.ilu_terms_U)
             elif kind == "jacobi":
                 want = K.l1_jacobi_sweep(lev.A, b, x0)
             else:

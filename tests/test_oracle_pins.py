@@ -155,6 +155,50 @@ def test_ilu_full_series_is_exact_substitution():
     np.testing.assert_allclose(got_d, want, rtol=1e-11, atol=1e-12)
 
 
+@pytest.mark.parametrize("row", _read_golden("ilu_tridiag3.txt"), ids=lambda r: r[0])
+def test_ilut_unscaled_equals_ldu_golden(row):
+    """Without Ruiz scaling, Jacobi with D = diag(U)^-1 on U v = y is the LDU Neumann series:
+    the ILUT sweep on the exact tridiagonal LU reproduces the ILU golden values (Algorithm 2 and
+    its row-scaling footnote)."""
+    from workloads.hierarchy import ilut
+    _, tl, tu, *vals = row
+    A = tridiag(3)
+    Ls, U, _, _ = ilut(A, droptol=0.0, lfil=3, ruiz=False)
+    np.testing.assert_allclose(U.toarray(), [[2, -1, 0], [0, 1.5, -1], [0, 0, 4 / 3]], atol=1e-15)
+    x = K.ilut_sweep(Ls, U, np.ones(3), np.ones(3), A, np.ones(3), np.zeros(3), int(tl), int(tu))
+    np.testing.assert_allclose(x, np.array(vals, float), atol=1e-15)
+
+
+def test_ilut_full_series_is_exact_and_scaling_invariant():
+    """n Jacobi terms solve both triangular systems exactly (nilpotent iteration matrices), so the
+    result is (LU)^-1 r whatever the Ruiz scaling."""
+    from workloads.hierarchy import ilut
+    A = pressure3d_7pt(4, seed=6)
+    n = A.shape[0]
+    Ls, U, dr, dc = ilut(A, droptol=1e-3, lfil=4)
+    b = np.random.default_rng(2).uniform(-1, 1, n)
+    LU = (np.eye(n) + Ls.toarray()) @ U.toarray()
+    want = np.linalg.solve(LU, b)
+    got = K.ilut_sweep(Ls, U, dr, dc, A, b, np.zeros(n), n, n)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-12)
+    got1 = K.ilut_sweep(Ls, U, np.ones(n), np.ones(n), A, b, np.zeros(n), n, n)
+    np.testing.assert_allclose(got1, want, rtol=1e-10, atol=1e-12)
+    direct = K.ilut_sweep(Ls, U, dr, dc, A, b, np.zeros(n), 1, 1, mode="direct")
+    np.testing.assert_allclose(direct, want, rtol=1e-10, atol=1e-12)
+    assert not np.allclose(K.ilut_sweep(Ls, U, dr, dc, A, b, np.zeros(n), 2, 2), want, rtol=1e-6)
+
+
+def test_ilut_complete_factorisation_and_ruiz():
+    """ILUT with no dropping is the exact LU; Ruiz scaling gives unit row and column maxima."""
+    from workloads.hierarchy import ilut
+    A = pressure3d_7pt(5, seed=2)
+    n = A.shape[0]
+    Ls, U, dr, dc = ilut(A, droptol=0.0, lfil=n)
+    np.testing.assert_allclose(((sp.identity(n) + Ls) @ U - A).toarray(), 0.0, atol=1e-12)
+    Ut = abs(sp.diags(dr) @ U @ sp.diags(dc))
+    assert np.all(np.abs(Ut.max(axis=1).toarray() - 1) < 0.1) and np.all(np.abs(Ut.max(axis=0).toarray() - 1) < 0.1)
+
+
 def test_l1_jacobi_dense():
     A = random_spd(16, 4)
     Ad = A.toarray()
@@ -179,6 +223,14 @@ def _dense_smoother(A, kind, p, backward, lev):
         SL = sum(np.linalg.matrix_power(-Ls, j) for j in range(p.ilu_terms_L))
         SU = sum(np.linalg.matrix_power(-Us, j) for j in range(p.ilu_terms_U))
         return SU @ np.diag(lev.ilu_dinv) @ SL
+    if kind == "ilut":
+        Ls = lev.ilu_L.toarray()
+        Ut = np.diag(lev.ilu_dr) @ lev.ilu_U.toarray() @ np.diag(lev.ilu_dc)
+        Dm = np.diag(1.0 / np.diag(Ut))
+        G = np.eye(n) - Dm @ Ut
+        SL = sum(np.linalg.matrix_power(-Ls, j) for j in range(p.ilu_terms_L))
+        SU = sum(np.linalg.matrix_power(G, j) for j in range(p.ilu_terms_U)) @ Dm
+        return np.diag(lev.ilu_dc) @ SU @ np.diag(lev.ilu_dr) @ SL
     Dinv = np.diag(1.0 / np.diag(Ad))
     T = np.triu(Ad, 1) if backward else np.tril(Ad, -1)
     G = -Dinv @ T
@@ -204,13 +256,16 @@ def _dense_vcycle_operator(H, p, l=0):
     return (I - E) @ np.linalg.inv(Ad)
 
 
-@pytest.mark.parametrize("smoother,terms,sweeps", [(K.POLY_GS, 2, 1), (K.POLY_GS, 3, 2), (K.JACOBI_L1, 1, 2),
-                                                   (K.HYBRID_ILU0, 2, 1), (K.ILU0, 2, 1)])
-def test_vcycle_matches_closed_form_operator(smoother, terms, sweeps):
+@pytest.mark.parametrize("smoother,terms,sweeps,ilu", [(K.POLY_GS, 2, 1, "ilu0"), (K.POLY_GS, 3, 2, "ilu0"),
+                                                       (K.JACOBI_L1, 1, 2, "ilu0"), (K.HYBRID_ILU0, 2, 1, "ilu0"),
+                                                       (K.ILU0, 2, 1, "ilu0"), (K.HYBRID_ILU0, 3, 1, "ilut"),
+                                                       (K.ILU0, 2, 1, "ilut")])
+def test_vcycle_matches_closed_form_operator(smoother, terms, sweeps, ilu):
     A = pressure3d_7pt(4, seed=2)  # n = 64
-    H = build_hierarchy(A, max_levels=3, coarse_max=8, ilu_levels=None)
+    H = build_hierarchy(A, max_levels=3, coarse_max=8, ilu_levels=None, ilu=ilu, droptol=1e-3, lfil=4)
     assert H.nlevels == 3 and H.coarse_inv is not None
-    p = K.SmootherParams(smoother=smoother, neumann_terms=terms, pre_sweeps=sweeps, post_sweeps=sweeps)
+    p = K.SmootherParams(smoother=smoother, neumann_terms=terms, pre_sweeps=sweeps, post_sweeps=sweeps,
+                         ilu_terms_L=terms, ilu_terms_U=terms)
     n = A.shape[0]
     Mv = np.column_stack([vcycle(H, e, p) for e in np.eye(n)])
     Md = _dense_vcycle_operator(H, p)

@@ -277,3 +277,126 @@ void nsw_spgemm_fill(int m, int ncols_b, const int* arp, const int* aci, const d
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// ILUT(droptol, lfil) (dual-threshold incomplete LU, row by row) and Ruiz scaling of U, the
+// factorisation and scaling of the ILUT smoother of Algorithm 2 (Sec. 5.3.3).
+//   A ~ (I + L_s) U, L_s strictly lower, U upper with its diagonal.
+//   In row i: tau_i = droptol * ||a_i||_2; multipliers below tau_i are dropped; after the
+//   elimination entries below tau_i are dropped and at most lfil entries (largest magnitude)
+//   are kept in each of the L and strict-U parts; the diagonal is always kept.
+// Output arrays are sized by the caller with the bounds n*lfil (L) and n*(lfil+1) (U); the
+// function returns 0 and the actual counts, or -(i+1) on a zero pivot in row i.
+// ------------------------------------------------------------------------------------------
+#include <set>
+
+extern "C" {
+
+int nsw_ilut(int n, const int* rp, const int* ci, const double* v, double droptol, int lfil, int* lrp, int* lci,
+             double* lv, int* urp, int* uci, double* uv, int64_t* counts) {
+  std::vector<double> w(n, 0.0);
+  std::vector<char> used(n, 0);
+  std::vector<int> nz;
+  std::vector<int64_t> urow(n + 1, 0);  // filled progressively
+  int64_t lo = 0, uo = 0;
+  lrp[0] = 0;
+  urp[0] = 0;
+  std::vector<int> udiag(n, -1);
+  for (int i = 0; i < n; ++i) {
+    double nrm = 0.0;
+    nz.clear();
+    std::set<int> lower;  // pending lower columns in increasing order
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      w[j] = v[p];
+      used[j] = 1;
+      nz.push_back(j);
+      nrm += v[p] * v[p];
+      if (j < i) lower.insert(j);
+    }
+    const double tau = droptol * std::sqrt(nrm);
+    while (!lower.empty()) {
+      const int k = *lower.begin();
+      lower.erase(lower.begin());
+      const double piv = uv[udiag[k]];
+      double lik = w[k] / piv;
+      if (std::fabs(lik) < tau) {
+        w[k] = 0.0;
+        continue;
+      }
+      w[k] = lik;
+      for (int q = udiag[k] + 1; q < urp[k + 1]; ++q) {
+        const int j = uci[q];
+        if (!used[j]) {
+          used[j] = 1;
+          w[j] = 0.0;
+          nz.push_back(j);
+          if (j < i) lower.insert(j);
+        }
+        w[j] -= lik * uv[q];
+      }
+    }
+    // split, drop small entries, keep the lfil largest per part
+    std::vector<std::pair<double, int>> L, U;
+    double diag = 0.0;
+    bool has_diag = false;
+    for (int j : nz) {
+      const double x = w[j];
+      if (j == i) { diag = x; has_diag = true; }
+      else if (x != 0.0 && std::fabs(x) >= tau) (j < i ? L : U).emplace_back(-std::fabs(x), j);
+      used[j] = 0;
+    }
+    auto keep = [&](std::vector<std::pair<double, int>>& part) {
+      if ((int)part.size() > lfil) {
+        std::nth_element(part.begin(), part.begin() + lfil, part.end());
+        part.resize(lfil);
+      }
+      std::sort(part.begin(), part.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.second < b.second; });
+    };
+    keep(L);
+    keep(U);
+    if (!has_diag || diag == 0.0) return -(i + 1);
+    for (auto& e : L) { lci[lo] = e.second; lv[lo] = w[e.second]; ++lo; }
+    lrp[i + 1] = (int)lo;
+    udiag[i] = (int)uo;
+    uci[uo] = i; uv[uo] = diag; ++uo;
+    for (auto& e : U) { uci[uo] = e.second; uv[uo] = w[e.second]; ++uo; }
+    urp[i + 1] = (int)uo;
+    for (int j : nz) w[j] = 0.0;
+  }
+  counts[0] = lo;
+  counts[1] = uo;
+  return 0;
+}
+
+// Ruiz equilibration of a (square, sparse) matrix M: find positive D_r, D_c with every row and
+// column of D_r M D_c having largest magnitude 1 (to `tol`), by repeated division with the
+// square roots of the current row and column maxima. Returns the sweeps used.
+int nsw_ruiz(int n, const int* rp, const int* ci, const double* v, double tol, int maxit, double* dr, double* dc) {
+  std::vector<double> rmax(n), cmax(n);
+  for (int i = 0; i < n; ++i) dr[i] = dc[i] = 1.0;
+  int it = 0;
+  for (; it < maxit; ++it) {
+    std::fill(rmax.begin(), rmax.end(), 0.0);
+    std::fill(cmax.begin(), cmax.end(), 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const double a = std::fabs(dr[i] * v[p] * dc[ci[p]]);
+        rmax[i] = std::max(rmax[i], a);
+        cmax[ci[p]] = std::max(cmax[ci[p]], a);
+      }
+    double dev = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (rmax[i] > 0) dev = std::max(dev, std::fabs(1.0 - rmax[i]));
+      if (cmax[i] > 0) dev = std::max(dev, std::fabs(1.0 - cmax[i]));
+    }
+    if (dev <= tol) break;
+    for (int i = 0; i < n; ++i) {
+      if (rmax[i] > 0) dr[i] /= std::sqrt(rmax[i]);
+      if (cmax[i] > 0) dc[i] /= std::sqrt(cmax[i]);
+    }
+  }
+  return it;
+}
+
+}  // extern "C"

@@ -49,6 +49,11 @@ def _load():
         lib.nsw_spgemm_fill.restype = None
         lib.nsw_set_strength_mode.argtypes = [ctypes.c_int]
         lib.nsw_set_strength_mode.restype = None
+        lib.nsw_ilut.argtypes = [ctypes.c_int, i32p, i32p, f64p, ctypes.c_double, ctypes.c_int, i32p, i32p, f64p, i32p,
+                                 i32p, f64p, i64p]
+        lib.nsw_ilut.restype = ctypes.c_int
+        lib.nsw_ruiz.argtypes = [ctypes.c_int, i32p, i32p, f64p, ctypes.c_double, ctypes.c_int, f64p, f64p]
+        lib.nsw_ruiz.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -68,8 +73,11 @@ class Level:
     P: sp.csr_matrix | None = None  # n_l x n_{l+1}
     R: sp.csr_matrix | None = None  # n_{l+1} x n_l
     ilu_L: sp.csr_matrix | None = None  # strictly lower L_s
-    ilu_U: sp.csr_matrix | None = None  # strictly upper U_s (rows scaled by 1/u_ii)
-    ilu_dinv: np.ndarray | None = None  # 1/u_ii
+    ilu_U: sp.csr_matrix | None = None  # ILU(0): strictly upper U_s (rows scaled by 1/u_ii); ILUT: U with diagonal
+    ilu_dinv: np.ndarray | None = None  # ILU(0): 1/u_ii
+    ilu_form: int = 0  # 0: ILU(0) in row-scaled LDU form; 1: ILUT with Ruiz scalings ilu_dr, ilu_dc
+    ilu_dr: np.ndarray | None = None
+    ilu_dc: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -152,13 +160,38 @@ def ilu0(A: sp.csr_matrix):
     return _csr(L), _csr(U), dinv
 
 
+def ilut(A: sp.csr_matrix, droptol: float = 1e-2, lfil: int = 5, ruiz: bool = True, ruiz_tol: float = 1e-3,
+         ruiz_maxit: int = 50):
+    """ILUT(droptol, lfil) factors A ~ (I + L_s) U and Ruiz scalings D_r, D_c of U
+    (Algorithm 2). Returns (L_s, U with diagonal, dr, dc); dr = dc = 1 without Ruiz."""
+    lib = _load()
+    A = _csr(A)
+    n = A.shape[0]
+    lrp, urp = np.empty(n + 1, np.int32), np.empty(n + 1, np.int32)
+    lci, lv = np.empty(max(n * lfil, 1), np.int32), np.empty(max(n * lfil, 1), np.float64)
+    uci, uv = np.empty(n * (lfil + 1), np.int32), np.empty(n * (lfil + 1), np.float64)
+    counts = np.zeros(2, np.int64)
+    rc = lib.nsw_ilut(n, A.indptr, A.indices, A.data, float(droptol), int(lfil), lrp, lci, lv, urp, uci, uv, counts)
+    if rc != 0:
+        raise ValueError(f"ILUT zero pivot in row {-rc - 1}")
+    nl, nu = int(counts[0]), int(counts[1])
+    L = _csr(sp.csr_matrix((lv[:nl].copy(), lci[:nl].copy(), lrp), shape=(n, n)))
+    U = _csr(sp.csr_matrix((uv[:nu].copy(), uci[:nu].copy(), urp), shape=(n, n)))
+    dr, dc = np.ones(n), np.ones(n)
+    if ruiz:
+        lib.nsw_ruiz(n, U.indptr, U.indices, U.data, float(ruiz_tol), int(ruiz_maxit), dr, dc)
+    return L, U, dr, dc
+
+
 def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: int = 512, seed: int = 0,
-                    ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512, strength: str = "abs") -> Hierarchy:
+                    ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512, strength: str = "abs",
+                    ilu: str = "ilu0", droptol: float = 1e-2, lfil: int = 5) -> Hierarchy:
     """Build the Ruge-Stuben hierarchy of A (strength theta, PMIS, BAMG-direct, Galerkin RAP).
 
     Coarsening stops when a level has at most `coarse_max` rows, when `max_levels` levels exist,
     or when a coarsening step keeps more than 90% of the points. ILU(0) factors are attached to
-    the levels listed in `ilu_levels` (None for every non-coarsest level). The coarsest level
+    the levels listed in `ilu_levels` (None for every non-coarsest level); ilu="ilut" attaches
+    ILUT(droptol, lfil) factors with Ruiz scalings of U instead (Algorithm 2). The coarsest level
     gets a dense inverse when it has at most `direct_max` rows. strength="abs" compares |a_ij|
     (Sec. 5.1 as printed); strength="neg" compares -a_ij (classical Ruge-Stuben, for matrices
     with positive off-diagonal entries such as Q1 stiffness on high-aspect elements).
@@ -179,7 +212,12 @@ def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: in
     want = range(len(levels) - 1) if ilu_levels is None else ilu_levels
     for l in want:
         if 0 <= l < len(levels) - 1:
-            levels[l].ilu_L, levels[l].ilu_U, levels[l].ilu_dinv = ilu0(levels[l].A)
+            if ilu == "ilut":
+                lev = levels[l]
+                lev.ilu_L, lev.ilu_U, lev.ilu_dr, lev.ilu_dc = ilut(lev.A, droptol, lfil)
+                lev.ilu_form = 1
+            else:
+                levels[l].ilu_L, levels[l].ilu_U, levels[l].ilu_dinv = ilu0(levels[l].A)
     H = Hierarchy(levels=levels, theta=theta, seed=seed)
     if levels[-1].n <= direct_max:
         H.coarse_inv = np.ascontiguousarray(np.linalg.inv(levels[-1].A.toarray()))
