@@ -69,6 +69,7 @@ __device__ __forceinline__ bool last_of_system(unsigned* tk, int nb) {
 // Gram for every active system (Algorithm 1 steps 6-11 per system).
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
+  pdl_enter();
   __shared__ double s_vt[kGramTile];
   __shared__ double s_w[kGramTile];
   __shared__ double red[2 * (kMaxM + 1)];
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
 // Update + Givens per active system; the last block of the launch advances the batch step.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads) k_bupdate(BatchArgs a) {
+  pdl_enter();
   __shared__ double s_h[kMaxM + 1];
   __shared__ double s_red[kRedThreads / 32];
   __shared__ int s_sys;
@@ -336,6 +338,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bupdate(BatchArgs a) {
 // x += sum_j coef_j Z[:, j] for each system over its rows (k_s columns of its last cycle).
 template <typename TZ>
 __global__ void __launch_bounds__(kRedThreads) k_bxupdate(BatchArgs a, const TZ* Z, int64_t ldz) {
+  pdl_enter();
   __shared__ double s_c[kMaxM];
   __shared__ int s_sys;
   if (threadIdx.x == 0) s_sys = find_system(a.bstart, a.nsys, blockIdx.x);
@@ -367,6 +370,7 @@ struct BResidArgs {
 };
 
 __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
+  pdl_enter();
   BatchArgs& a = ra.ba;
   __shared__ double s_tmp[kRedThreads / 32];
   __shared__ int s_sys;
@@ -461,6 +465,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
 template <typename TC, typename T>
 __global__ void k_bdense_gemv(int nrows, const int* row_sys, const int64_t* coff, const int64_t* cblk,
                               const TC* __restrict__ C, VRef<const T> bref, VRef<T> zref, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;

@@ -2,6 +2,7 @@
 // GMRES(m) loop (run as one CUDA graph with device-side WHILE conditionals, or as a plain
 // launch loop), and the per-kernel entry points.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <cmath>
 #include <mutex>
@@ -51,6 +52,32 @@ constexpr int kThreads = 256;
 thread_local int64_t g_launches = 0;
 
 inline int blocks_for(int64_t threads) { return (int)std::max<int64_t>(1, (threads + kThreads - 1) / kThreads); }
+
+// Every kernel is launched with programmatic dependent launch allowed: each kernel starts by
+// waiting for its predecessor grid (griddepcontrol.wait) and then lets its own successor be
+// scheduled, so launch latency overlaps the predecessor's last wave. NSAMG_PDL=0 turns it off.
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("NSAMG_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ------------------------------------------------------------------------------------------
 // Device CSR
@@ -258,31 +285,31 @@ template <int G, typename TM, typename TX, typename TY>
 void launch_csr(const RowOp<TM, TX, TY>& op, int nb, cudaStream_t s) {
   if constexpr (std::is_same<TX, TY>::value) {
     switch (epi_code(op)) {
-      case 0: k_row<G, 0><<<nb, kThreads, 0, s>>>(op); return;
-      case 2: k_row<G, 2><<<nb, kThreads, 0, s>>>(op); return;
-      case 3: k_row<G, 3><<<nb, kThreads, 0, s>>>(op); return;
-      case 6: k_row<G, 6><<<nb, kThreads, 0, s>>>(op); return;
-      case 7: k_row<G, 7><<<nb, kThreads, 0, s>>>(op); return;
-      case 11: k_row<G, 11><<<nb, kThreads, 0, s>>>(op); return;
-      case 16: k_row<G, 16><<<nb, kThreads, 0, s>>>(op); return;
-      case 18: k_row<G, 18><<<nb, kThreads, 0, s>>>(op); return;
-      case 19: k_row<G, 19><<<nb, kThreads, 0, s>>>(op); return;
-      case 27: k_row<G, 27><<<nb, kThreads, 0, s>>>(op); return;
+      case 0: launch_k(k_row<G, 0, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 2: launch_k(k_row<G, 2, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 3: launch_k(k_row<G, 3, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 6: launch_k(k_row<G, 6, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 7: launch_k(k_row<G, 7, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 11: launch_k(k_row<G, 11, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 16: launch_k(k_row<G, 16, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 18: launch_k(k_row<G, 18, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 19: launch_k(k_row<G, 19, TM, TX, TY>, nb, kThreads, s, op); return;
+      case 27: launch_k(k_row<G, 27, TM, TX, TY>, nb, kThreads, s, op); return;
       default: break;
     }
   } else {
     if (epi_code(op) == 0) {
-      k_row<G, 0><<<nb, kThreads, 0, s>>>(op);
+      launch_k(k_row<G, 0, TM, TX, TY>, nb, kThreads, s, op);
       return;
     }
   }
-  k_row<G, E_RUNTIME><<<nb, kThreads, 0, s>>>(op);
+  launch_k(k_row<G, E_RUNTIME, TM, TX, TY>, nb, kThreads, s, op);
 }
 
 template <int EPI, int K, typename TM, typename TX, typename TY>
 void launch_sell_one(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   const int nb = blocks_for((int64_t)((op.sell.nchunks + K - 1) / K) * 32);
-  k_sell<EPI, K, TM, TX, TY><<<nb, kThreads, 0, s>>>(op);
+  launch_k(k_sell<EPI, K, TM, TX, TY>, nb, kThreads, s, op);
 }
 
 template <int K, typename TM, typename TX, typename TY>
@@ -674,12 +701,12 @@ void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c
     BatchData* B = h->batch;
     ++g_launches;
     const int nb = (B->ncrows * 32 + kThreads - 1) / kThreads;
-    k_bdense_gemv<T, T><<<nb, kThreads, 0, c.s>>>(B->ncrows, B->d_row_sys, B->d_coff, B->d_cblk,
+    launch_k(k_bdense_gemv<T, T>, nb, kThreads, c.s, B->ncrows, B->d_row_sys, B->d_coff, B->d_cblk,
                                                   bcoarse_ptr(B, (T*)nullptr), b, x, c.skip);
   } else if (C) {
     ++g_launches;
     const int nb = (L.n * 32 + kThreads - 1) / kThreads;
-    k_dense_gemv<T, T><<<nb, kThreads, 0, c.s>>>(L.n, C, b, x, c.skip);
+    launch_k(k_dense_gemv<T, T>, nb, kThreads, c.s, L.n, C, b, x, c.skip);
   } else {
     smooth(h, L, b, x, false, true, h->p.coarse_sweeps, c);
   }
@@ -803,7 +830,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
     // stores Z), outer product w = A z_i with the FP64 matrix.
     Level<float>& L0 = h->lv32[0];
     ++g_launches;
-    k_cast<double, float><<<8 * 148, kThreads, 0, s>>>(h->n, b, vref(L0.b), skip);
+    launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), skip);
     VRef<float> z;
     z.p = h->Z32;
     z.sel = sel;
@@ -824,7 +851,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ga.w = h->w;
   ga.st = h->st;
   ga.scr = h->scr;
-  k_gram<<<h->gram_blocks, kGramThreads, 0, s>>>(ga);
+  launch_k(k_gram, h->gram_blocks, kGramThreads, s, ga);
   g_launches += 2;
   UpdateArgs ua{};
   ua.n = h->n;
@@ -835,13 +862,13 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ua.cond_inner = cond_inner;
   ua.scr = h->scr;
   ua.scr.ticket = h->scr.ticket + 1;
-  k_update<<<h->update_blocks, kRedThreads, 0, s>>>(ua);
+  launch_k(k_update, h->update_blocks, kRedThreads, s, ua);
 }
 
 void enqueue_xupdate(nsamg_handle* h, cudaStream_t s) {
   ++g_launches;
-  if (h->fp32) k_xupdate<float><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z32, h->ld, h->st);
-  else k_xupdate<double><<<h->update_blocks, kRedThreads, 0, s>>>(h->n, h->Z, h->ld, h->st);
+  if (h->fp32) launch_k(k_xupdate<float>, h->update_blocks, kRedThreads, s, h->n, h->Z32, h->ld, h->st);
+  else launch_k(k_xupdate<double>, h->update_blocks, kRedThreads, s, h->n, h->Z, h->ld, h->st);
 }
 
 void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
@@ -862,12 +889,12 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   const int nb = blocks_for((int64_t)A.n * G);
   ++g_launches;
   switch (G) {
-    case 1: k_resid<1><<<nb, kRedThreads, 0, s>>>(ra); break;
-    case 2: k_resid<2><<<nb, kRedThreads, 0, s>>>(ra); break;
-    case 4: k_resid<4><<<nb, kRedThreads, 0, s>>>(ra); break;
-    case 8: k_resid<8><<<nb, kRedThreads, 0, s>>>(ra); break;
-    case 16: k_resid<16><<<nb, kRedThreads, 0, s>>>(ra); break;
-    default: k_resid<32><<<nb, kRedThreads, 0, s>>>(ra); break;
+    case 1: launch_k(k_resid<1>, nb, kRedThreads, s, ra); break;
+    case 2: launch_k(k_resid<2>, nb, kRedThreads, s, ra); break;
+    case 4: launch_k(k_resid<4>, nb, kRedThreads, s, ra); break;
+    case 8: launch_k(k_resid<8>, nb, kRedThreads, s, ra); break;
+    case 16: launch_k(k_resid<16>, nb, kRedThreads, s, ra); break;
+    default: launch_k(k_resid<32>, nb, kRedThreads, s, ra); break;
   }
 }
 
@@ -972,7 +999,7 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
   } else {
     Level<float>& L0 = h->lv32[0];
     ++g_launches;
-    k_cast<double, float><<<8 * 148, kThreads, 0, s>>>(h->n, b, vref(L0.b), nullptr);
+    launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), nullptr);
     VRef<float> z;
     z.p = h->Z32;
     z.sel = sel;
@@ -986,17 +1013,17 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     launch_row(op, A.G, s);
   }
   g_launches += 2;
-  k_bgram<<<B->nblocks[BatchData::kGram], kGramThreads, 0, s>>>(batch_args(h, BatchData::kGram, 0, 0));
-  k_bupdate<<<B->nblocks[BatchData::kUpdate], kRedThreads, 0, s>>>(batch_args(h, BatchData::kUpdate, 0, cond_inner));
+  launch_k(k_bgram, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
+  launch_k(k_bupdate, B->nblocks[BatchData::kUpdate], kRedThreads, s, batch_args(h, BatchData::kUpdate, 0, cond_inner));
 }
 
 void enqueue_bxupdate(nsamg_handle* h, cudaStream_t s) {
   BatchData* B = h->batch;
   ++g_launches;
   if (h->fp32)
-    k_bxupdate<float><<<B->nblocks[BatchData::kX], kRedThreads, 0, s>>>(batch_args(h, BatchData::kX, 0, 0), h->Z32, h->ld);
+    launch_k(k_bxupdate<float>, B->nblocks[BatchData::kX], kRedThreads, s, batch_args(h, BatchData::kX, 0, 0), h->Z32, h->ld);
   else
-    k_bxupdate<double><<<B->nblocks[BatchData::kX], kRedThreads, 0, s>>>(batch_args(h, BatchData::kX, 0, 0), h->Z, h->ld);
+    launch_k(k_bxupdate<double>, B->nblocks[BatchData::kX], kRedThreads, s, batch_args(h, BatchData::kX, 0, 0), h->Z, h->ld);
 }
 
 void enqueue_bresid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
@@ -1009,7 +1036,7 @@ void enqueue_bresid(nsamg_handle* h, cudaStream_t s, int init, unsigned long lon
   ra.v = A.v;
   ra.init = init;
   ++g_launches;
-  k_bresid<<<B->nblocks[BatchData::kResid], kRedThreads, 0, s>>>(ra);
+  launch_k(k_bresid, B->nblocks[BatchData::kResid], kRedThreads, s, ra);
 }
 
 int check_params(const nsamg_params& p) {
@@ -1576,11 +1603,11 @@ int level_ok(nsamg_handle* h, int level) {
 }
 
 void to32(nsamg_handle* h, const double* a, float* b, int64_t n) {
-  k_cast<double, float><<<blocks_for(n), kThreads, 0, h->stream>>>(n, cref(a), vref(b), nullptr);
+  launch_k(k_cast<double, float>, blocks_for(n), kThreads, h->stream, n, cref(a), vref(b), nullptr);
 }
 
 void to64(nsamg_handle* h, const float* a, double* b, int64_t n) {
-  k_cast<float, double><<<blocks_for(n), kThreads, 0, h->stream>>>(n, cref(a), vref(b), nullptr);
+  launch_k(k_cast<float, double>, blocks_for(n), kThreads, h->stream, n, cref(a), vref(b), nullptr);
 }
 
 // Standalone scratch for nsamg_gram / nsamg_update (one per device, allocated on first use).
@@ -1920,7 +1947,7 @@ int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d
   ga.i_standalone = i;
   ga.out = d_out;
   ga.scr = scr;
-  k_gram<<<2 * sms, kGramThreads, 0, (cudaStream_t)stream>>>(ga);
+  launch_k(k_gram, 2 * sms, kGramThreads, (cudaStream_t)stream, ga);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
@@ -1946,7 +1973,7 @@ int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const d
   ga.i_standalone = i;
   ga.out = d_out;
   ga.scr = scr;
-  k_gram<<<blocks, kGramThreads, 0, (cudaStream_t)stream>>>(ga);
+  launch_k(k_gram, blocks, kGramThreads, (cudaStream_t)stream, ga);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
@@ -1973,7 +2000,7 @@ int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, 
   ua.sumsq_out = d_sumsq;
   ua.scr = scr;
   ua.scr.ticket = scr.ticket + 1;
-  k_update<<<8 * sms, kRedThreads, 0, (cudaStream_t)stream>>>(ua);
+  launch_k(k_update, 8 * sms, kRedThreads, (cudaStream_t)stream, ua);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }

@@ -76,6 +76,7 @@ struct GramArgs {
 };
 
 __global__ void __launch_bounds__(kGramThreads) k_gram(GramArgs a) {
+  pdl_enter();
   __shared__ double s_vt[kGramTile];
   __shared__ double s_w[kGramTile];
   __shared__ double red[2 * (kMaxM + 1)];
@@ -251,6 +252,7 @@ struct UpdateArgs {
 };
 
 __global__ void __launch_bounds__(kRedThreads) k_update(UpdateArgs a) {
+  pdl_enter();
   __shared__ double s_h[kMaxM + 1];
   __shared__ double s_red[kRedThreads / 32];
   GState* st = a.st;
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(UpdateArgs a) {
 // ------------------------------------------------------------------------------------------
 template <typename TZ>
 __global__ void __launch_bounds__(kRedThreads) k_xupdate(int64_t n, const TZ* Z, int64_t ldz, GState* st) {
+  pdl_enter();
   __shared__ double s_c[kMaxM];
   if (st->done && st->status < 0) return;
   const int k = st->k;
@@ -406,6 +409,7 @@ struct ResidArgs {
 
 template <int G>
 __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
+  pdl_enter();
   __shared__ double s_tmp[kRedThreads / 32];
   GState* st = a.st;
   const int was_done = a.init ? 0 : st->done;  // an error earlier in the cycle already ended the solve

@@ -14,6 +14,13 @@ constexpr int kMaxM = 64;  // largest restart length (matches NSAMG_MAX_RESTART)
 
 // A vector argument: either a plain pointer or column `*sel` of a column-major block with
 // leading dimension ld (used to aim V-cycle kernels at V[:, i] / Z[:, i] inside a CUDA graph).
+// Programmatic dependent launch: wait until the predecessor grid has completed and its writes
+// are visible, then allow the successor grid to be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
 struct VRef {
   T* p = nullptr;
@@ -97,6 +104,7 @@ __device__ __forceinline__ void row_epilogue(const RowOp<TM, TX, TY>& op, int ro
 
 template <int G, int EPI, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
+  pdl_enter();
   if (op.skip && *op.skip) return;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int row = (int)(gid / G);
@@ -125,6 +133,7 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
 // K independent gather chains in flight (rows of 2-7 entries are otherwise latency bound).
 template <int EPI, int K, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
+  pdl_enter();
   if (op.skip && *op.skip) return;
   const int lane = threadIdx.x & 31;
   const TX* __restrict__ src = op.src.get();
@@ -167,6 +176,7 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
 // ------------------------------------------------------------------------------------------
 template <typename TA, typename TB>
 __global__ void k_cast(int64_t n, VRef<const TA> a, VRef<TB> b, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const TA* pa = a.get();
   TB* pb = b.get();
@@ -176,6 +186,7 @@ __global__ void k_cast(int64_t n, VRef<const TA> a, VRef<TB> b, const int* skip)
 
 template <typename T>
 __global__ void k_fill(int64_t n, T* a, T v) {
+  pdl_enter();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
 }
 
@@ -183,6 +194,7 @@ __global__ void k_fill(int64_t n, T* a, T v) {
 // per row, fixed-order reduction.
 template <typename TC, typename T>
 __global__ void k_dense_gemv(int n, const TC* __restrict__ C, VRef<const T> bref, VRef<T> zref, const int* skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
