@@ -628,7 +628,7 @@ def run_profile_kernel(args):
     n = A.shape[0]
     fp32 = args.profile_kernel.endswith("32")
     kind = args.profile_kernel[:-2] if fp32 else args.profile_kernel
-    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=-1, vcycle_fp32=int(fp32),
+    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=0, vcycle_fp32=int(fp32),
                              **{k: v for k, v in SMOOTHERS["hybrid_ilu0"].items() if k != "vcycle_fp32"})
     h = nsamg.setup_hierarchy(H, p)
     x = torch.from_numpy(rhs[0]).cuda()

@@ -197,7 +197,9 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
       }
     d.nchunks = nch;
     const double avg_row = (double)nnz / n;
-    d.sell_k = avg_row <= 8 ? 4 : avg_row <= 16 ? 2 : 1;
+    // FP64 rows are FP64-issue bound (one chunk per warp keeps registers and occupancy);
+    // FP32 rows are latency bound and interleave several chunks
+    d.sell_k = sizeof(T) == sizeof(double) ? 1 : (avg_row <= 8 ? 4 : avg_row <= 16 ? 2 : 1);
     CK(cudaMalloc(&d.s_perm, sizeof(int) * perm.size()));
     CK(cudaMemcpy(d.s_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d.s_rlen, sizeof(int) * rlen.size()));
@@ -752,6 +754,27 @@ void vcycle(nsamg_handle* h, std::vector<Level<T>>& lv, int l, VC<T> b, VRef<T> 
 // Autotuning of threads-per-row for large CSR matrices (timed SpMV with each group size).
 // ------------------------------------------------------------------------------------------
 template <typename T>
+float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  auto op = op_mat(M, cref((const T*)x));
+  op.out = vref(y);
+  launch_row(op, G, s);
+  launch_row(op, G, s);
+  float best = 1e30f;
+  for (int round = 0; round < 3; ++round) {
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 4; ++r) launch_row(op, G, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  return best;
+}
+
+// Timed choice among CSR with G = 1, 2, ..., 32 threads per row and SELL-32-sigma with 1, 2 or
+// 4 chunks per warp (best of three rounds of four launches each, after two untimed launches).
+template <typename T>
 int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
   if (M.n < 20000 || M.nnz == 0) return NSAMG_OK;
   cudaEvent_t e0, e1;
@@ -759,50 +782,59 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
   CK(cudaEventCreate(&e1));
   const int cands[] = {1, 2, 4, 8, 16, 32};
   float best = 1e30f;
-  int bestG = M.G;
+  int bestG = M.G, bestK = 0;
   const double avg = (double)M.nnz / M.n;
+  M.use_sell = false;
   for (int G : cands) {
     if (G > 2 * avg + 2) break;
-    auto op = op_mat(M, cref((const T*)x));
-    op.out = vref(y);
-    launch_row(op, G, s);
-    CK(cudaEventRecord(e0, s));
-    for (int r = 0; r < 5; ++r) launch_row(op, G, s);
-    CK(cudaEventRecord(e1, s));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
+    const float ms = time_spmv(M, x, y, G, s, e0, e1);
     if (ms < best) {
       best = ms;
       bestG = G;
     }
   }
-  M.G = bestG;
-  if (M.nchunks > 0) {  // the SELL-32-sigma layout (1, 2 or 4 chunks per warp) competes too
-    int bestK = 0;
+  if (M.nchunks > 0) {
     for (int K : {1, 2, 4}) {
       M.use_sell = true;
       M.sell_k = K;
-      auto op = op_mat(M, cref((const T*)x));
-      op.out = vref(y);
-      launch_row(op, 1, s);
-      CK(cudaEventRecord(e0, s));
-      for (int r = 0; r < 5; ++r) launch_row(op, 1, s);
-      CK(cudaEventRecord(e1, s));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
+      const float ms = time_spmv(M, x, y, 1, s, e0, e1);
       if (ms < best) {
         best = ms;
         bestK = K;
       }
     }
-    M.use_sell = bestK > 0;
-    if (bestK) M.sell_k = bestK;
   }
+  M.G = bestG;
+  M.use_sell = bestK > 0;
+  if (bestK) M.sell_k = bestK;
+  CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return NSAMG_OK;
+}
+
+// Brings the GPU to its working clock before timed tuning (an idle GPU ramps up over the first
+// milliseconds of work, which would bias the first candidates).
+template <typename T>
+void tune_warmup(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
+  if (M.n == 0) return;
+  auto op = op_mat(M, cref((const T*)x));
+  op.out = vref(y);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float total = 0.f;
+  for (int it = 0; it < 200 && total < 30.f; ++it) {
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 10; ++r) launch_row(op, M.G, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1139,6 +1171,7 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
 template <typename T>
 int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaStream_t s) {
   int rc;
+  if (group == 0 && !lvs.empty() && lvs[0].A.n >= 20000) tune_warmup(lvs[0].A, big_x, big_y, s);
   for (auto& L : lvs) {
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
     for (DCSR<T>* M : mats) {
