@@ -634,6 +634,7 @@ def run_profile_kernel(args):
     x = torch.from_numpy(rhs[0]).cuda()
     y = torch.empty_like(x)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile_kernel")
     if kind == "spmv":
         for _ in range(3):
             nsamg.level_spmv(h, 0, x, y)
@@ -661,7 +662,8 @@ def run_profile_kernel(args):
             else:
                 nsamg.update(n, i, V, ld, x, 1.0, hc, ss)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_kernel": args.profile_kernel, "n": n}))
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_kernel": args.profile_kernel, "n": n, "level0_layout": nsamg.level_group(h, 0)}))
     h.close()
 
 
