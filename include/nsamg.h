@@ -226,6 +226,15 @@ int nsamg_server_cancel(nsamg_server* s, uint64_t ticket);
 int nsamg_server_info(nsamg_server* s, int64_t* out4);
 void nsamg_server_destroy(nsamg_server* s);
 
+/* ILU(0) factors of A computed on the current device by fixed-point sweeps (the iteration the
+ * paper's conclusions propose for a cheaper setup): with the products l_ik u_kj (k < min(i, j))
+ * of every entry of pattern(A),
+ *   i > j: l_ij = (a_ij - sum_k l_ik u_kj) / u_jj,   i <= j: u_ij = a_ij - sum_k l_ik u_kj,
+ * applied `sweeps` times in Jacobi fashion from l = a_ij / a_jj, u = a_ij. The exact ILU(0) is
+ * the fixed point. A: host CSR (validated); lu_out: host array of nnz(A) values on A's pattern
+ * (strictly lower entries = L_s, the rest = U with its diagonal). Blocks on `stream`. */
+int nsamg_ilu0_fixed_point(const nsamg_csr* A, int sweeps, double* lu_out, void* stream);
+
 /* Matrix layout chosen for a level's operator (diagnostic): 0 = SELL-32-sigma (one thread per
  * row, rows sorted by length inside windows of 4096 rows, chunks of 32 stored column-major),
  * else the number of threads per row of the CSR kernel. */

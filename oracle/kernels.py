@@ -226,3 +226,39 @@ def project(Lrows: np.ndarray, r: np.ndarray, T_mode: str = "trunc") -> np.ndarr
             h[q] = r[q] - np.dot(Lrows[q, :q], h[:q])
         return h
     raise ValueError("T_mode must be 'trunc' or 'exact'")
+
+
+def ilu0_fixed_point_sweep(A: sp.csr_matrix, Ls: sp.csr_matrix, U: sp.csr_matrix):
+    """One Jacobi-style fixed-point sweep for the ILU(0) factors on pattern(A) (the fixed-point
+    ILU the paper's conclusions propose for the setup), written with the sparse product
+    M = L_s U restricted to the pattern:
+      i > j:  l_ij = (a_ij - (M_ij - l_ij u_jj)) / u_jj      (sum over k < j only)
+      i <= j: u_ij = a_ij - M_ij                               (sum over k < i)
+    Returns the new (L_s, U) on the pattern of A."""
+    A = sp.csr_matrix(A)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    cols = A.indices
+    M = sp.csr_matrix(Ls @ U)
+    m = np.asarray(M[rows, cols]).ravel()
+    l = np.asarray(Ls[rows, cols]).ravel()
+    u = np.asarray(U[rows, cols]).ravel()
+    ud = U.diagonal()
+    lower = rows > cols
+    new = np.where(lower, (A.data - (m - l * ud[cols])) / ud[cols], A.data - m)
+    shape = A.shape
+    Ln = sp.csr_matrix((np.where(lower, new, 0.0), (rows, cols)), shape=shape)
+    Un = sp.csr_matrix((np.where(lower, 0.0, new), (rows, cols)), shape=shape)
+    Ln.eliminate_zeros()
+    Un.eliminate_zeros()
+    return Ln, Un
+
+
+def ilu0_fixed_point(A: sp.csr_matrix, sweeps: int):
+    """`sweeps` fixed-point sweeps from l_ij = a_ij / a_jj (i > j), u_ij = a_ij (i <= j)."""
+    A = sp.csr_matrix(A)
+    d = A.diagonal()
+    Ls = sp.csr_matrix(sp.tril(A, -1) @ sp.diags(1.0 / d))
+    U = sp.csr_matrix(sp.triu(A, 0))
+    for _ in range(sweeps):
+        Ls, U = ilu0_fixed_point_sweep(A, Ls, U)
+    return Ls, U

@@ -61,7 +61,7 @@ EXPORTS = [
     "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
-    "nsamg_server_info", "nsamg_server_destroy",
+    "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
 ]
 
 _lib = None
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         "nsamg_server_cancel": (i32, [vp, ctypes.c_uint64]),
         "nsamg_server_info": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "nsamg_server_destroy": (None, [vp]),
+        "nsamg_ilu0_fixed_point": (i32, [ctypes.POINTER(Csr), i32, vp, vp]),
         "nsamg_destroy": (None, [vp]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
@@ -149,6 +150,9 @@ def _csr_desc(M, keep: list) -> Csr:
     if M is None:
         return c
     M = M.tocsr()
+    if not M.has_sorted_indices:  # the ABI requires sorted columns; sort a copy
+        M = M.copy()
+        M.sort_indices()
     rp = np.ascontiguousarray(M.indptr, dtype=np.int32)
     ci = np.ascontiguousarray(M.indices, dtype=np.int32)
     v = np.ascontiguousarray(M.data, dtype=np.float64)
@@ -334,6 +338,16 @@ def gram_noalloc(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
 
 def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
     _check(load().nsamg_update(int(n), int(i), _ptr(V), int(ldv), _ptr(w), float(beta), _ptr(h), _ptr(sumsq), stream))
+
+
+def ilu0_fixed_point(A, sweeps: int, stream=None) -> np.ndarray:
+    """ILU(0) values on A's pattern after `sweeps` fixed-point sweeps on the GPU
+    (strictly lower entries: L_s; the others: U with its diagonal)."""
+    keep: list = []
+    c = _csr_desc(A, keep)
+    out = np.empty(A.nnz, np.float64)
+    _check(load().nsamg_ilu0_fixed_point(ctypes.byref(c), int(sweeps), out.ctypes.data, stream))
+    return out
 
 
 def status_str(s: int) -> str:

@@ -420,3 +420,64 @@ def test_backward_error_and_orthogonality_diagnostics(name):
     ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, K.SmootherParams()), m=30, rtol=1e-8)
     ref_loss = np.sqrt(2.0) * np.linalg.norm(ref.L)
     assert st["orth_loss"] == pytest.approx(ref_loss, rel=0.5, abs=1e-15)
+
+
+def test_checkpoint_and_resume():
+    """A stopped solve is resumed by calling solve again from the saved x (x and the true residual
+    fully define the state at a restart): the resumed run reaches the tolerance, and a run that
+    restarts at the same column count gives the same x."""
+    A, H = case("p23")
+    b = rhs_uniform(A.shape[0], 21)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(restart=5)) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st1 = nsamg.solve(h, dev(b), x, rtol=1e-10, maxit=5)
+        assert st1["status"] == nsamg.NOT_CONVERGED and st1["iters"] == 5
+        saved = host(x).copy()
+        x2 = dev(saved)
+        st2 = nsamg.solve(h, dev(b), x2, rtol=1e-10, maxit=500)
+        assert st2["converged"]
+        x3 = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st3 = nsamg.solve(h, dev(b), x3, rtol=1e-10, maxit=500)
+    assert st3["iters"] == st1["iters"] + st2["iters"]
+    assert np.array_equal(host(x2), host(x3))
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 3, 8])
+def test_ilu0_fixed_point_on_gpu(sweeps):
+    """GPU fixed-point ILU(0) sweeps equal the oracle's sweeps on the same pattern."""
+    A = pressure3d_7pt(20, seed=11)
+    got = nsamg.ilu0_fixed_point(A, sweeps)
+    Ls, U = K.ilu0_fixed_point(A, sweeps)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    want = np.asarray((Ls + U)[rows, A.indices]).ravel()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_solve_with_gpu_computed_ilu0_factors():
+    """Hierarchy whose finest ILU(0) factors come from 30 GPU fixed-point sweeps: the hybrid
+    V-cycle solve converges like the one with host-computed factors."""
+    import copy
+    A, H = case("p23")
+    vals = nsamg.ilu0_fixed_point(H.levels[0].A, 30)
+    A0 = H.levels[0].A
+    rows = np.repeat(np.arange(A0.shape[0]), np.diff(A0.indptr))
+    lower = rows > A0.indices
+    Lm = sp.csr_matrix((np.where(lower, vals, 0.0), A0.indices.copy(), A0.indptr.copy()), shape=A0.shape)
+    Um = sp.csr_matrix((np.where(lower, 0.0, vals), A0.indices.copy(), A0.indptr.copy()), shape=A0.shape)
+    Lm.eliminate_zeros()
+    Um.eliminate_zeros()
+    d = Um.diagonal()
+    H2 = copy.copy(H)
+    H2.levels = [copy.copy(l) for l in H.levels]
+    H2.levels[0].ilu_L = sp.csr_matrix(Lm)
+    H2.levels[0].ilu_U = sp.csr_matrix(sp.diags(1.0 / d) @ sp.triu(Um, 1))
+    H2.levels[0].ilu_dinv = 1.0 / d
+    np.testing.assert_allclose(H2.levels[0].ilu_dinv, H.levels[0].ilu_dinv, rtol=1e-10)
+    b = rhs_uniform(A.shape[0], 5)
+    p = nsamg.default_params(smoother=K.HYBRID_ILU0)
+    with nsamg.setup_hierarchy(H2, p) as h2, nsamg.setup_hierarchy(H, p) as h1:
+        x1 = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        x2 = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        s1 = nsamg.solve(h1, dev(b), x1, rtol=1e-8)
+        s2 = nsamg.solve(h2, dev(b), x2, rtol=1e-8)
+    assert s2["converged"] and abs(s1["iters"] - s2["iters"]) <= 1

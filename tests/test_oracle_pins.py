@@ -199,6 +199,23 @@ def test_ilut_complete_factorisation_and_ruiz():
     assert np.all(np.abs(Ut.max(axis=1).toarray() - 1) < 0.1) and np.all(np.abs(Ut.max(axis=0).toarray() - 1) < 0.1)
 
 
+def test_ilu0_fixed_point_has_the_ilu0_factors_as_fixed_point_and_converges():
+    """The exact ILU(0) factors satisfy the fixed-point equations on the pattern (one sweep returns
+    them), and the Jacobi-style sweeps reach them in finitely many steps."""
+    A = pressure3d_7pt(5, seed=9)
+    n = A.shape[0]
+    Ls0, Us0, dinv0 = ilu0(A)
+    U0 = sp.csr_matrix(sp.diags(1.0 / dinv0) @ (sp.identity(n) + Us0))
+    Ls1, U1 = K.ilu0_fixed_point_sweep(A, Ls0, U0)
+    np.testing.assert_allclose(Ls1.toarray(), Ls0.toarray(), atol=1e-14)
+    np.testing.assert_allclose(U1.toarray(), U0.toarray(), atol=1e-13)
+    Ls, U = K.ilu0_fixed_point(A, n)
+    np.testing.assert_allclose(Ls.toarray(), Ls0.toarray(), atol=1e-13)
+    np.testing.assert_allclose(U.toarray(), U0.toarray(), atol=1e-12)
+    Ls3, U3 = K.ilu0_fixed_point(A, 3)
+    assert abs(U3 - U0).max() > 1e-6  # three sweeps are not converged yet
+
+
 def test_l1_jacobi_dense():
     A = random_spd(16, 4)
     Ad = A.toarray()
