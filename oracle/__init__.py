@@ -12,11 +12,14 @@ Contents (each function cites the passage it restates):
               substitution), restriction, prolongation, coarse solve, Gram reduction and
               basis update of the one-reduce Arnoldi step.
   vcycle   -- one Ruge-Stuben V-cycle with zero initial guess.
+  setup    -- the Ruge-Stuben setup of Sec. 5.1 (strength, PMIS with SplitMix64 weights,
+              BAMG-direct interpolation, Galerkin product, coarse inverse, fixed-point ILU(0)
+              factors) that the GPU setup computes.
   gmres    -- classical right-preconditioned MGS-GMRES(m) (Saad-Schultz) and a plain
               restatement of the one-reduce truncated-Neumann MGS-GMRES (Algorithm 1) with
               T = I - L or T = (I + L)^-1.
 
 All arithmetic is float64 (numpy / scipy.sparse library primitives for products).
 """
-from . import kernels, vcycle, gmres  # noqa: F401
+from . import kernels, vcycle, gmres, setup  # noqa: F401
 from .kernels import SmootherParams  # noqa: F401
