@@ -235,6 +235,69 @@ void nsamg_server_destroy(nsamg_server* s);
  * (strictly lower entries = L_s, the rest = U with its diagonal). Blocks on `stream`. */
 int nsamg_ilu0_fixed_point(const nsamg_csr* A, int sweeps, double* lu_out, void* stream);
 
+/* ---- Ruge-Stuben setup on the GPU (Sec. 5.1) ------------------------------------------------
+ * The paper's conclusions name a GPU setup as the next step; these calls build the hierarchy the
+ * solve phase consumes with every step on the current device:
+ *   strength  S_i = { j != i : m(a_ij) >= theta max_{k != i} m(a_ik) }, m = |.| (strength_mode 0,
+ *             as printed in Sec. 5.1) or -(.) (strength_mode 1, the classical sign-aware form);
+ *   PMIS      (Sec. 5.1) weights lambda_i = |S^T_i| + u_i, u_i the top 53 bits of one SplitMix64
+ *             step from the state seed_l ^ (0xA24BAED4963EE407 (i + 1)), seed_l = seed + 7919 (l + 1)
+ *             for level l; rounds select the undecided points that no undecided point of
+ *             S_i u S^T_i outranks in (lambda, index); undecided points that strongly depend on a
+ *             new C-point become F; points that influence no one start as F; F-points left without
+ *             a strong C-neighbour are then promoted to C (they influence no point, so the
+ *             order of promotion does not matter);
+ *   BAMG-direct interpolation, closed form of eq. (bamgdir) with f = 1:
+ *             w_ij = -(a_ij + beta_i / n_{C_i^s}) / (a_ii + sum_{k weak} a_ik), beta_i the sum of
+ *             the strong F-couplings; C rows are unit rows;
+ *   Galerkin  R = P^T, A_c = R (A P) (Sec. 5, eq. A_k); each entry of a product is summed in the
+ *             order of the left operand's row, with products and sums rounded separately;
+ *   ILU(0)    `ilu_sweeps` fixed-point sweeps (as nsamg_ilu0_fixed_point) on every level l < L-1
+ *             whose bit is set in `ilu_levels`, stored in the row-scaled LDU form of
+ *             nsamg_level_desc (ilu_form 0, U_s = diag(U)^-1 strict_upper(U), dinv = 1/u_ii);
+ *   coarse    dense inverse of the coarsest operator by Gauss-Jordan with partial pivoting when it
+ *             has at most `direct_max` rows.
+ * Coarsening stops when a level has at most `coarse_max` rows, at `max_levels` levels, or when a
+ * step keeps no point or at least 90% of them. */
+typedef struct {
+  double theta;          /* strength threshold, 0 <= theta <= 1 (default 0.25)                 */
+  int32_t strength_mode; /* 0: |a_ij|, 1: -a_ij                                                */
+  int32_t max_levels;    /* >= 1 (default 25)                                                   */
+  int32_t coarse_max;    /* >= 1 (default 512)                                                  */
+  int32_t direct_max;    /* 0..8192 (default 512)                                               */
+  uint64_t seed;         /* PMIS seed (default 0)                                               */
+  uint64_t ilu_levels;   /* bit l: ILU(0) factors on level l (default 1: the finest level)      */
+  int32_t ilu_sweeps;    /* fixed-point sweeps, >= 0 (default 3)                                */
+  int32_t pad;
+} nsamg_amg_options;
+
+typedef struct nsamg_amg nsamg_amg;
+
+void nsamg_amg_default_options(nsamg_amg_options* o);
+
+/* Build the hierarchy of A (host CSR, validated like nsamg_setup_hierarchy's input: square,
+ * sorted columns, nonzero diagonal, finite values) on the current device, on `cuda_stream`.
+ * Blocks until done. The hierarchy lives in device memory owned by *out.
+ * Errors: INVALID_ARG (null pointer, option out of range), BAD_MATRIX (validation; a row whose
+ * interpolation is undefined; a singular coarsest operator; a matrix beyond 2^31 - 1 entries),
+ * OOM, CUDA. On error *out is NULL. */
+int nsamg_amg_build(const nsamg_csr* A, const nsamg_amg_options* opt, void* cuda_stream, nsamg_amg** out);
+int nsamg_amg_num_levels(const nsamg_amg* g);
+/* Level l: rows, nonzeros of A_l, coarse points chosen on it (0 on a level that was not
+ * coarsened) and PMIS rounds taken. Any output pointer may be NULL. */
+int nsamg_amg_level_info(const nsamg_amg* g, int l, int32_t* n, int64_t* nnz, int32_t* nc, int32_t* pmis_rounds);
+/* Host copies of level l's splitting: cf (n_l entries: coarse index, or -1 for F) and the strength
+ * flags (nnz(A_l) bytes, 1 = strong, in CSR order). Either pointer may be NULL. INVALID_ARG on a
+ * level that was not coarsened. */
+int nsamg_amg_level_splitting(const nsamg_amg* g, int l, int32_t* cf, uint8_t* strong);
+/* Host copy of the whole hierarchy as a nsamg_hierarchy_desc; the arrays are owned by g and stay
+ * valid until the next export or nsamg_amg_destroy. */
+int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out);
+/* nsamg_amg_export followed by nsamg_setup_hierarchy: a solver handle for the GPU-built hierarchy
+ * (the handle owns its own copies; g may be destroyed afterwards). */
+int nsamg_amg_setup_solver(nsamg_amg* g, const nsamg_params* p, void* cuda_stream, nsamg_handle** out);
+void nsamg_amg_destroy(nsamg_amg* g);
+
 /* Matrix layout chosen for a level's operator (diagnostic): 0 = SELL-32-sigma (one thread per
  * row, rows sorted by length inside windows of 4096 rows, chunks of 32 stored column-major),
  * else the number of threads per row of the CSR kernel. */

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnsamg.so")
 SOURCES = ["engine.cu"]
-HEADERS = ["kernels.cuh", "gmres.cuh"]
+HEADERS = ["kernels.cuh", "gmres.cuh", "batch.cuh", "setup.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-v"]
 

@@ -2148,84 +2148,6 @@ int nsamg_batch_offsets(nsamg_handle* h, int64_t* out) {
   return NSAMG_OK;
 }
 
-int nsamg_ilu0_fixed_point(const nsamg_csr* A, int sweeps, double* lu_out, void* stream) {
-  if (!A || !lu_out || sweeps < 0) return fail(NSAMG_ERR_INVALID_ARG, "bad arguments");
-  int rc = validate(*A, true, true, "ilu0 A");
-  if (rc) return rc;
-  const int n = A->nrows;
-  const int64_t nnz = A->nnz;
-  // host: pair lists (position of l_ik, position of u_kj) for every entry, diagonal positions
-  std::vector<int> row(nnz);
-  std::vector<int64_t> dpos(n, -1), pstart(nnz + 1, 0), pik, pkj;
-  std::vector<double> init(nnz);
-  for (int i = 0; i < n; ++i)
-    for (int64_t q = A->rowptr[i]; q < A->rowptr[i + 1]; ++q) {
-      row[q] = i;
-      if (A->col[q] == i) dpos[i] = q;
-    }
-  for (int i = 0; i < n; ++i)
-    for (int64_t q = A->rowptr[i]; q < A->rowptr[i + 1]; ++q) {
-      const int j = A->col[q];
-      const int kmax = std::min(i, j);
-      for (int64_t r = A->rowptr[i]; r < A->rowptr[i + 1] && A->col[r] < kmax; ++r) {
-        const int k = A->col[r];
-        const int* b = A->col + A->rowptr[k];
-        const int* e = A->col + A->rowptr[k + 1];
-        const int* f = std::lower_bound(b, e, j);
-        if (f != e && *f == j) {
-          pik.push_back(r);
-          pkj.push_back(A->rowptr[k] + (f - b));
-        }
-      }
-      pstart[q + 1] = (int64_t)pik.size();
-      // initial guess: l = a_ij / a_jj below the diagonal, u = a_ij on and above it
-      init[q] = (j < i) ? A->val[q] / A->val[dpos[j]] : A->val[q];
-    }
-  cudaStream_t s = (cudaStream_t)stream;
-  int *d_row = nullptr, *d_col = nullptr;
-  int64_t *d_ps = nullptr, *d_ik = nullptr, *d_kj = nullptr, *d_dp = nullptr;
-  double *d_a = nullptr, *d_x = nullptr, *d_y = nullptr;
-  const size_t np = std::max<size_t>(pik.size(), 1);
-  auto cleanup = [&] {
-    cudaFree(d_row); cudaFree(d_col); cudaFree(d_ps); cudaFree(d_ik); cudaFree(d_kj); cudaFree(d_dp);
-    cudaFree(d_a); cudaFree(d_x); cudaFree(d_y);
-  };
-  auto ok = [&](cudaError_t e) {
-    if (e != cudaSuccess) {
-      cleanup();
-      cuda_fail(e, "nsamg_ilu0_fixed_point");
-      return false;
-    }
-    return true;
-  };
-  if (!ok(cudaMalloc(&d_row, sizeof(int) * nnz)) || !ok(cudaMalloc(&d_col, sizeof(int) * nnz)) ||
-      !ok(cudaMalloc(&d_ps, sizeof(int64_t) * (nnz + 1))) || !ok(cudaMalloc(&d_ik, sizeof(int64_t) * np)) ||
-      !ok(cudaMalloc(&d_kj, sizeof(int64_t) * np)) || !ok(cudaMalloc(&d_dp, sizeof(int64_t) * n)) ||
-      !ok(cudaMalloc(&d_a, sizeof(double) * nnz)) || !ok(cudaMalloc(&d_x, sizeof(double) * nnz)) ||
-      !ok(cudaMalloc(&d_y, sizeof(double) * nnz)))
-    return NSAMG_ERR_OOM;
-  if (!ok(cudaMemcpyAsync(d_row, row.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s)) ||
-      !ok(cudaMemcpyAsync(d_col, A->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, s)) ||
-      !ok(cudaMemcpyAsync(d_ps, pstart.data(), sizeof(int64_t) * (nnz + 1), cudaMemcpyHostToDevice, s)) ||
-      (!pik.empty() && !ok(cudaMemcpyAsync(d_ik, pik.data(), sizeof(int64_t) * pik.size(), cudaMemcpyHostToDevice, s))) ||
-      (!pkj.empty() && !ok(cudaMemcpyAsync(d_kj, pkj.data(), sizeof(int64_t) * pkj.size(), cudaMemcpyHostToDevice, s))) ||
-      !ok(cudaMemcpyAsync(d_dp, dpos.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s)) ||
-      !ok(cudaMemcpyAsync(d_a, A->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s)) ||
-      !ok(cudaMemcpyAsync(d_x, init.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s)))
-    return NSAMG_ERR_CUDA;
-  const int nb = (int)std::min<int64_t>(blocks_for(nnz), 148 * 16);
-  for (int it = 0; it < sweeps; ++it) {
-    launch_k(k_ilu_fp_sweep, nb, kThreads, s, nnz, (const int*)d_row, (const int*)d_col, (const double*)d_a,
-             (const int64_t*)d_ps, (const int64_t*)d_ik, (const int64_t*)d_kj, (const int64_t*)d_dp, (const double*)d_x, d_y);
-    std::swap(d_x, d_y);
-  }
-  if (!ok(cudaMemcpyAsync(lu_out, d_x, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s)) || !ok(cudaStreamSynchronize(s)) ||
-      !ok(cudaGetLastError()))
-    return NSAMG_ERR_CUDA;
-  cleanup();
-  return NSAMG_OK;
-}
-
 void nsamg_destroy(nsamg_handle* h) { destroy_impl(h); }
 
 const char* nsamg_status_str(int s) {
@@ -2636,3 +2558,5 @@ void nsamg_server_destroy(nsamg_server* S) {
 }
 
 }  // extern "C"
+
+#include "setup.cuh"

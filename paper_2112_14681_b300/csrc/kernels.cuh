@@ -208,27 +208,6 @@ __global__ void k_dense_gemv(int n, const TC* __restrict__ C, VRef<const T> bref
 }
 
 // ------------------------------------------------------------------------------------------
-// ILU(0) by fixed-point sweeps (setup on the GPU; the paper's conclusions point to this
-// iteration to cut the setup cost). For every entry (i, j) of the pattern of A, with the
-// products l_ik u_kj (k < min(i, j)) listed as pairs of entry positions:
-//   i > j:  l_ij = (a_ij - sum l_ik u_kj) / u_jj        i <= j:  u_ij = a_ij - sum l_ik u_kj
-// One Jacobi-style sweep reads `old` and writes `nw` (deterministic); the exact ILU(0) factors
-// are its fixed point.
-// ------------------------------------------------------------------------------------------
-__global__ void k_ilu_fp_sweep(int64_t nnz, const int* __restrict__ row, const int* __restrict__ col,
-                               const double* __restrict__ a, const int64_t* __restrict__ pstart,
-                               const int64_t* __restrict__ pik, const int64_t* __restrict__ pkj,
-                               const int64_t* __restrict__ dpos, const double* __restrict__ old, double* __restrict__ nw) {
-  pdl_enter();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = a[e];
-    for (int64_t q = pstart[e]; q < pstart[e + 1]; ++q) s = fma(-old[pik[q]], old[pkj[q]], s);
-    const int i = row[e], j = col[e];
-    nw[e] = (i > j) ? s / old[dpos[j]] : s;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
 // GMRES device state (one per handle, in device memory).
 // ------------------------------------------------------------------------------------------
 struct GState {

@@ -45,6 +45,12 @@ class Params(ctypes.Structure):
                                                "use_graph", "spmv_group")]
 
 
+class AmgOptions(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("strength_mode", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("coarse_max", ctypes.c_int32), ("direct_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("ilu_levels", ctypes.c_uint64), ("ilu_sweeps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("relres_true", ctypes.c_double), ("relres_implicit", ctypes.c_double),
@@ -62,6 +68,8 @@ EXPORTS = [
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
     "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
+    "nsamg_amg_default_options", "nsamg_amg_build", "nsamg_amg_num_levels", "nsamg_amg_level_info",
+    "nsamg_amg_level_splitting", "nsamg_amg_export", "nsamg_amg_setup_solver", "nsamg_amg_destroy",
 ]
 
 _lib = None
@@ -106,6 +114,15 @@ def load(path: str = LIB_PATH):
         "nsamg_server_info": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "nsamg_server_destroy": (None, [vp]),
         "nsamg_ilu0_fixed_point": (i32, [ctypes.POINTER(Csr), i32, vp, vp]),
+        "nsamg_amg_default_options": (None, [ctypes.POINTER(AmgOptions)]),
+        "nsamg_amg_build": (i32, [ctypes.POINTER(Csr), ctypes.POINTER(AmgOptions), vp, ctypes.POINTER(vp)]),
+        "nsamg_amg_num_levels": (i32, [vp]),
+        "nsamg_amg_level_info": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "nsamg_amg_level_splitting": (i32, [vp, i32, vp, vp]),
+        "nsamg_amg_export": (i32, [vp, ctypes.POINTER(HierarchyDesc)]),
+        "nsamg_amg_setup_solver": (i32, [vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
+        "nsamg_amg_destroy": (None, [vp]),
         "nsamg_destroy": (None, [vp]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
@@ -348,6 +365,132 @@ def ilu0_fixed_point(A, sweeps: int, stream=None) -> np.ndarray:
     out = np.empty(A.nnz, np.float64)
     _check(load().nsamg_ilu0_fixed_point(ctypes.byref(c), int(sweeps), out.ctypes.data, stream))
     return out
+
+
+def amg_default_options(**overrides) -> AmgOptions:
+    o = AmgOptions()
+    load().nsamg_amg_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k) or k == "pad":
+            raise KeyError(k)
+        setattr(o, k, float(v) if k == "theta" else int(v))
+    return o
+
+
+def _csr_from_desc(c: Csr):
+    """Copy a host CSR described by the library into a scipy matrix (None when absent)."""
+    import scipy.sparse as sp
+    if c.nrows == 0:
+        return None
+    n, nnz = int(c.nrows), int(c.nnz)
+    rp = np.ctypeslib.as_array(ctypes.cast(c.rowptr, ctypes.POINTER(ctypes.c_int32)), (n + 1,)).copy()
+    if nnz:
+        ci = np.ctypeslib.as_array(ctypes.cast(c.col, ctypes.POINTER(ctypes.c_int32)), (nnz,)).copy()
+        v = np.ctypeslib.as_array(ctypes.cast(c.val, ctypes.POINTER(ctypes.c_double)), (nnz,)).copy()
+    else:
+        ci, v = np.zeros(0, np.int32), np.zeros(0)
+    M = sp.csr_matrix((v, ci, rp), shape=(n, int(c.ncols)))
+    M.has_sorted_indices = True
+    return M
+
+
+class ExportedLevel:
+    """One level of a GPU-built hierarchy copied to the host (the attributes setup_hierarchy reads)."""
+
+    def __init__(self, d: LevelDesc):
+        self.A, self.P, self.R = _csr_from_desc(d.A), _csr_from_desc(d.P), _csr_from_desc(d.R)
+        self.ilu_L, self.ilu_U = _csr_from_desc(d.ilu_L), _csr_from_desc(d.ilu_U)
+        n = self.A.shape[0]
+        self.ilu_dinv = (np.ctypeslib.as_array(ctypes.cast(d.ilu_dinv, ctypes.POINTER(ctypes.c_double)), (n,)).copy()
+                         if d.ilu_dinv else None)
+        self.ilu_form, self.ilu_dr, self.ilu_dc = 0, None, None
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+
+class ExportedHierarchy:
+    def __init__(self, levels, coarse_inv):
+        self.levels, self.coarse_inv = levels, coarse_inv
+
+    @property
+    def nlevels(self) -> int:
+        return len(self.levels)
+
+
+class GpuHierarchy:
+    """Ruge-Stuben hierarchy of A built on the GPU (nsamg_amg_build)."""
+
+    def __init__(self, A, options: AmgOptions | None = None, stream=None):
+        lib = load()
+        keep: list = []
+        self.options = options or amg_default_options()
+        c = _csr_desc(A, keep)
+        g = ctypes.c_void_p()
+        _check(lib.nsamg_amg_build(ctypes.byref(c), ctypes.byref(self.options),
+                                   None if stream is None else ctypes.c_void_p(stream), ctypes.byref(g)))
+        self._g = g
+
+    @property
+    def nlevels(self) -> int:
+        return int(load().nsamg_amg_num_levels(self._g))
+
+    def level_info(self, l: int) -> dict:
+        n, nc, rounds = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        _check(load().nsamg_amg_level_info(self._g, int(l), ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nc),
+                                           ctypes.byref(rounds)))
+        return {"n": n.value, "nnz": nnz.value, "nc": nc.value, "pmis_rounds": rounds.value}
+
+    def splitting(self, l: int):
+        """(cf, strong): coarse index or -1 per point; strength flag per entry of A_l."""
+        info = self.level_info(l)
+        cf = np.empty(info["n"], np.int32)
+        strong = np.empty(max(info["nnz"], 1), np.uint8)
+        _check(load().nsamg_amg_level_splitting(self._g, int(l), cf.ctypes.data, strong.ctypes.data))
+        return cf, strong[:info["nnz"]].astype(bool)
+
+    def export(self) -> ExportedHierarchy:
+        d = HierarchyDesc()
+        _check(load().nsamg_amg_export(self._g, ctypes.byref(d)))
+        levels = [ExportedLevel(d.levels[l]) for l in range(d.nlevels)]
+        cinv = None
+        if d.coarse_inv:
+            nc = levels[-1].n
+            cinv = np.ctypeslib.as_array(ctypes.cast(d.coarse_inv, ctypes.POINTER(ctypes.c_double)), (nc, nc)).copy()
+        return ExportedHierarchy(levels, cinv)
+
+    def setup_solver(self, params: Params | None = None, stream=None) -> Handle:
+        h = Handle.__new__(Handle)
+        h.params = params or default_params()
+        hp = ctypes.c_void_p()
+        _check(load().nsamg_amg_setup_solver(self._g, ctypes.byref(h.params),
+                                             None if stream is None else ctypes.c_void_p(stream), ctypes.byref(hp)))
+        h._h = hp
+        h.n = self.level_info(0)["n"]
+        return h
+
+    def close(self):
+        if getattr(self, "_g", None):
+            load().nsamg_amg_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def amg_build(A, options: AmgOptions | None = None, stream=None) -> GpuHierarchy:
+    return GpuHierarchy(A, options, stream)
 
 
 def status_str(s: int) -> str:

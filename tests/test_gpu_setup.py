@@ -1,0 +1,162 @@
+"""GPU Ruge-Stuben setup (nsamg_amg_build) against the setup oracle, level by level: strength
+flags and the PMIS splitting bit-exact, interpolation weights and Galerkin products within
+1e-14 relative (the products are summed in the same order as a sequential row-by-row product, so
+they also equal the host input generator's bitwise), fixed-point ILU(0) factors and the coarse
+inverse within their rounding bounds; a solve on the GPU-built hierarchy converges."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle.setup as OS
+from workloads import build_hierarchy, pressure3d_7pt, q1_27pt_graded, rhs_uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2112_14681_b300 import nsamg  # noqa: E402
+
+
+def zero_rowsum(n, seed, density=0.01):
+    rng = np.random.default_rng(seed)
+    B = sp.random(n, n, density=density, random_state=rng, format="csr")
+    B.data = -np.where(rng.random(B.nnz) < 0.3, rng.uniform(0.01, 0.05, B.nnz), rng.uniform(0.5, 1.0, B.nnz))
+    B.setdiag(0.0)
+    B.eliminate_zeros()
+    chain = sp.diags([-np.ones(n - 1), -np.ones(n - 1)], [-1, 1], format="csr")
+    B = sp.csr_matrix(B + chain)
+    A = sp.csr_matrix(B - sp.diags(np.asarray(B.sum(axis=1)).ravel()) + 1e-3 * sp.eye(n))
+    A.sort_indices()
+    return A
+
+
+CASES = {
+    # 3D variable-coefficient 7-point, ragged size (7^3 * 8 + ...): several levels
+    "p21": lambda: (pressure3d_7pt(21, seed=4), dict(coarse_max=100, seed=3), "abs"),
+    # Q1 27-point graded stiffness, sign-aware strength: rows of 100+ entries on level 1
+    "q12": lambda: (q1_27pt_graded(12), dict(coarse_max=100, seed=1, strength_mode=1), "neg"),
+    # random nonsymmetric with weak couplings
+    "z3000": lambda: (zero_rowsum(3000, 2), dict(coarse_max=50, seed=9), "abs"),
+}
+_built = {}
+
+
+def built(name):
+    if name not in _built:
+        A, kw, mode = CASES[name]()
+        A = sp.csr_matrix(A)
+        A.sort_indices()
+        opt = nsamg.amg_default_options(ilu_levels=0b11, ilu_sweeps=4, direct_max=512, **kw)
+        g = nsamg.amg_build(A, opt)
+        _built[name] = (A, kw, mode, g, g.export())
+    return _built[name]
+
+
+def rel_close(got, want, rtol):
+    scale = max(np.max(np.abs(want)), 1e-300)
+    return np.max(np.abs(got - want)) <= rtol * scale
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_levels_match_the_oracle(name):
+    A, kw, mode, g, H = built(name)
+    seed = kw["seed"]
+    assert H.nlevels >= 3
+    for l, lev in enumerate(H.levels[:-1]):
+        Al = lev.A
+        # strength flags and PMIS splitting: bit-exact (decisions taken in float64 on both sides)
+        cf, strong = g.splitting(l)
+        s_or = OS.strength(Al, 0.25, mode)
+        assert np.array_equal(strong, s_or), l
+        cf_or, nc_or = OS.pmis(Al, s_or, seed + 7919 * (l + 1))
+        assert np.array_equal(cf, cf_or), l
+        assert g.level_info(l)["nc"] == nc_or == lev.P.shape[1]
+        # interpolation: same pattern, weights within rounding of the closed form
+        P_or = OS.bamg_direct(Al, s_or, cf_or, nc_or)
+        assert np.array_equal(lev.P.indptr, P_or.indptr) and np.array_equal(lev.P.indices, P_or.indices)
+        assert rel_close(lev.P.data, P_or.data, 1e-14)
+        # restriction is the exact transpose; the Galerkin product within 1e-14 of scipy's
+        R_or, Ac_or = OS.galerkin(Al, lev.P)
+        assert np.array_equal(lev.R.indptr, R_or.indptr) and np.array_equal(lev.R.indices, R_or.indices)
+        assert np.array_equal(lev.R.data, R_or.data)
+        Ac = H.levels[l + 1].A
+        assert abs(Ac - Ac_or).max() <= 1e-14 * abs(Ac_or).max(), l
+        # the GPU keeps entries that cancel to zero, scipy may drop them: never fewer entries
+        assert Ac.nnz >= Ac_or.nnz
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ilu_factors_and_coarse_inverse(name):
+    A, kw, mode, g, H = built(name)
+    for l in (0, 1):
+        lev = H.levels[l]
+        Ls, Us, dinv = OS.ilu0_factors(lev.A, 4)
+        assert np.array_equal(lev.ilu_L.indptr, Ls.indptr) and np.array_equal(lev.ilu_L.indices, Ls.indices)
+        assert np.array_equal(lev.ilu_U.indptr, Us.indptr) and np.array_equal(lev.ilu_U.indices, Us.indices)
+        assert rel_close(lev.ilu_L.data, Ls.data, 1e-12) and rel_close(lev.ilu_U.data, Us.data, 1e-12)
+        assert rel_close(lev.ilu_dinv, dinv, 1e-12)
+    assert H.levels[2].ilu_L is None
+    Ac = H.levels[-1].A
+    want = OS.coarse_inverse(Ac)
+    cond = np.linalg.cond(Ac.toarray())
+    assert np.max(np.abs(H.coarse_inv - want)) <= 64 * np.finfo(float).eps * cond * np.max(np.abs(want))
+
+
+def test_gpu_setup_equals_the_host_generator_bitwise():
+    """Same splitting, same P, and the same coarse operators bit for bit as the C++ host setup
+    (both sum each product entry in the order of the left operand's row, without fused
+    multiply-adds)."""
+    A = pressure3d_7pt(24, seed=7)
+    Hh = build_hierarchy(A, theta=0.25, coarse_max=100, seed=5, ilu_levels=())
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=100, seed=5, ilu_levels=0)) as g:
+        H = g.export()
+    assert H.nlevels == Hh.nlevels
+    for a, b in zip(H.levels, Hh.levels):
+        assert np.array_equal(a.A.indptr, b.A.indptr) and np.array_equal(a.A.indices, b.A.indices)
+        assert np.array_equal(a.A.data, b.A.data)
+        if b.P is not None:
+            assert np.array_equal(a.P.indices, b.P.indices) and np.array_equal(a.P.data, b.P.data)
+
+
+def test_solve_on_the_gpu_built_hierarchy():
+    A = pressure3d_7pt(32, seed=2)
+    b = rhs_uniform(A.shape[0], 3)
+    p = nsamg.default_params(smoother=nsamg.HYBRID_ILU0)
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=512, ilu_sweeps=3)) as g:
+        h = g.setup_solver(p)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    st = nsamg.solve(h, torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=300)
+    torch.cuda.synchronize()
+    assert st["converged"]
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xh) / np.linalg.norm(b) <= 1e-8
+    Hh = build_hierarchy(A, theta=0.25, coarse_max=512, seed=0, ilu_levels=(0,))
+    with nsamg.setup_hierarchy(Hh, p) as h2:
+        x2 = torch.zeros_like(x)
+        st2 = nsamg.solve(h2, torch.from_numpy(b).cuda(), x2, rtol=1e-8, maxit=300)
+    assert abs(st["iters"] - st2["iters"]) <= 2
+    h.close()
+
+
+def test_bad_inputs():
+    with pytest.raises(nsamg.NsamgError) as e:
+        nsamg.amg_build(pressure3d_7pt(6), nsamg.amg_default_options(theta=2.0))
+    assert e.value.status == -1
+    # exactly singular coarsest operator (no coarsening: 2 rows <= coarse_max)
+    S = sp.csr_matrix(np.ones((2, 2)))
+    with pytest.raises(nsamg.NsamgError) as e:
+        nsamg.amg_build(S, nsamg.amg_default_options())
+    assert e.value.status == -2
+    # missing diagonal: rejected before any upload
+    B = sp.csr_matrix(np.array([[0.0, 1.0], [1.0, 2.0]]))
+    B.eliminate_zeros()
+    with pytest.raises(nsamg.NsamgError) as e:
+        nsamg.amg_build(B, nsamg.amg_default_options())
+    assert e.value.status == -2
+
+
+def test_no_coarsening_when_small():
+    A = pressure3d_7pt(6, seed=1)
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=1000)) as g:
+        H = g.export()
+        assert H.nlevels == 1 and H.levels[0].P is None
+        assert np.allclose(H.coarse_inv @ A.toarray(), np.eye(A.shape[0]), atol=1e-10)

@@ -143,6 +143,9 @@ def _check_pmis(mod):
         for i in np.flatnonzero(cf2 < 0):
             assert np.any(cf2[S.indices[S.indptr[i]:S.indptr[i + 1]]] >= 0), i
         assert np.all(cf2[cf >= 0] >= 0)  # promotion only adds C-points
+        # a promoted point influences no one (so the order of promotion cannot matter)
+        infl = np.diff(sp.csr_matrix(S.T).indptr)
+        assert np.all(infl[(cf2 >= 0) & (cf < 0)] == 0)
 
 
 def test_pmis_equals_sequential_characterisation():
