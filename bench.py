@@ -55,9 +55,53 @@ def peaks():
 def build_inputs():
     from workloads import build_hierarchy, pressure3d_7pt, rhs_uniform
     A = pressure3d_7pt(EDGE, sigma=1.0, seed=SEED)
+    t0 = time.perf_counter()
     H = build_hierarchy(A, theta=0.25, coarse_max=512, seed=SEED, ilu_levels=(0,))
+    H.info["host_setup_s"] = time.perf_counter() - t0
     rhs = [rhs_uniform(A.shape[0], SEED + k) for k in range(N_RHS)]
     return A, H, rhs
+
+
+def time_gpu_setup(nsamg, torch, A, H, reps: int = 3) -> dict:
+    """The same hierarchy built on the GPU (nsamg_amg_build): wall time per build (after one
+    warm-up build), whether every level operator equals the host generator's bit for bit, and a
+    solve on it (the finest ILU(0) factors from 3 fixed-point sweeps)."""
+    opt = nsamg.amg_default_options(theta=0.25, coarse_max=512, seed=SEED, ilu_levels=1, ilu_sweeps=3)
+    nsamg.amg_build(A, opt).close()
+    ts = []
+    for k in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = nsamg.amg_build(A, opt)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        if k < reps - 1:
+            g.close()
+    E = g.export()
+    same = E.nlevels == H.nlevels and all(
+        np.array_equal(a.A.indptr, b.A.indptr) and np.array_equal(a.A.indices, b.A.indices)
+        and np.array_equal(a.A.data, b.A.data) for a, b in zip(E.levels, H.levels))
+    t0 = time.perf_counter()
+    h = g.setup_solver(nsamg.default_params(restart=RESTART, **SMOOTHERS["hybrid_ilu0"]))
+    t_solver = time.perf_counter() - t0
+    rounds = [g.level_info(l)["pmis_rounds"] for l in range(g.nlevels - 1)]
+    g.close()
+    b = torch.from_numpy(rhs_for_setup_check(A.shape[0])).cuda()
+    x = torch.zeros_like(b)
+    st = nsamg.solve(h, b, x, RTOL, MAXIT)
+    h.close()
+    return {"host_generator_s": round(H.info.get("host_setup_s", float("nan")), 4),
+            "gpu_amg_build_s": round(float(np.median(ts)), 4), "gpu_amg_build_all_s": [round(t, 4) for t in ts],
+            "levels_bitwise_equal_host": bool(same),
+            "pmis_rounds": rounds,
+            "solver_setup_from_gpu_hierarchy_s": round(t_solver, 3),
+            "solve_on_gpu_hierarchy": {"iters": st["iters"], "relres_true": st["relres_true"],
+                                       "converged": bool(st["converged"])}}
+
+
+def rhs_for_setup_check(n):
+    from workloads import rhs_uniform
+    return rhs_uniform(n, SEED)
 
 
 def ilut_variant(H, droptol: float = 1e-2, lfil: int = 5):
@@ -328,6 +372,7 @@ def run_gpu(args):
         nsamg.solve_host(h, hb[k % N_RHS], hx, RTOL, MAXIT)
     t_e2e = replicas.max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
     kern = time_kernels(nsamg, torch, h, A, H, stream) if rank == 0 else {}
+    setup_t = time_gpu_setup(nsamg, torch, A, H) if rank == 0 and extras else None
     for hh in handles.values():
         hh.close()
     batched = run_batched(nsamg, torch, batch_sys) if batch_sys else None
@@ -368,6 +413,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * n, "entry_point": "nsamg_solve_host"},
             "gpu_launches": main_r["launches"],
         }
+        if setup_t:
+            line["setup"] = setup_t
         if batched:
             line["batched"] = batched
         if served:

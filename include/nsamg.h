@@ -101,6 +101,9 @@ typedef struct {
   double nrbe;            /* norm-wise relative backward error ||r|| / (||b|| + ||A||_inf ||x||) of
                              the final iterate (Sec. 3)                                          */
   double orth_loss;       /* ||I - V^T V||_F of the last cycle's basis, from sqrt(2) ||L||_F (Sec. 3) */
+  double sk_norm;         /* ||S_k||_2 of the last cycle, S_k = (I + U_k)^-1 U_k with U_k the strictly
+                             upper part of V_k^T V_k (Sec. 3); 1 means the basis became linearly
+                             dependent (see nsamg_sknorm)                                        */
 } nsamg_stats;
 
 typedef struct nsamg_handle nsamg_handle;
@@ -180,6 +183,16 @@ int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, 
  * race and give wrong results, so serialise them. */
 int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out,
                        void* stream);
+
+/* ||S_k||_2 for the k x k strictly lower matrix L_k (device, row-major, leading dimension ld >= k;
+ * only the entries below the diagonal are read): S_k = (I + L_k^T)^-1 L_k^T, the matrix of Paige,
+ * Rozloznik and Strakos that Sec. 3 uses to detect the loss of linear independence of the Krylov
+ * basis (||S_k||_2 = 1 exactly when the columns of V_k are dependent). The solve computes it on the
+ * last cycle's L (nsamg_stats.sk_norm); this entry runs the same kernel on caller data.
+ * Method: S_k by back substitution, then power iteration on S_k^T S_k until the Rayleigh quotient
+ * changes by at most 1e-15 relative (300 iterations at most); deterministic. Writes one double to
+ * d_out on `stream` (asynchronous). 1 <= k <= NSAMG_MAX_RESTART, else INVALID_ARG. */
+int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream);
 
 /* ---- batched solves of many independent systems ----------------------------------------
  * nsamg_batch_setup: `count` host hierarchies with the same number of levels (and either all or

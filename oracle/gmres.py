@@ -208,3 +208,15 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
             V[:, k] = vt / Hm[k, k - 1]
         Vout, Zout, Hout = V[:, : k + 1].copy(), Z[:, :k].copy(), Hm[: k + 1, :k].copy()
         Lout = Lm[:k, :k].copy()
+
+def sk_norm(L: np.ndarray) -> float:
+    """||S_k||_2 with S_k = (I + U_k)^-1 U_k and U_k = L^T, the strictly upper part of V_k^T V_k
+    (Sec. 3, after Paige, Rozloznik and Strakos): 0 for an orthonormal basis, 1 exactly when the
+    columns of V_k are linearly dependent."""
+    L = np.tril(np.asarray(L, dtype=np.float64), -1)
+    k = L.shape[0]
+    if k == 0:
+        return 0.0
+    U = L.T
+    S = np.linalg.solve(np.eye(k) + U, U)
+    return float(np.linalg.norm(S, 2))

@@ -442,6 +442,8 @@ __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
         st->done = fin ? 1 : 0;
         if (!fin) st->cycles += 1;
       }
+      if (ra.init) st->klast = 0;
+      else if (st->k > 0) st->klast = st->k;
       st->i = 0;
       st->k = 0;
       st->stop = st->done;

@@ -930,13 +930,23 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   }
 }
 
+// ||S_k||_2 of every solve's last cycle (one block per system).
+void enqueue_sknorm(nsamg_handle* h, cudaStream_t s) {
+  ++g_launches;
+  if (h->batch)
+    launch_k(k_sknorm_states, h->batch->nsys, kSkThreads, s, h->batch->d_st);
+  else
+    launch_k(k_sknorm_states, 1, kSkThreads, s, h->st);
+}
+
 using ResidFn = std::function<void(cudaStream_t, int, unsigned long long, unsigned long long)>;
 using StepFn = std::function<void(cudaStream_t, unsigned long long)>;
 using XFn = std::function<void(cudaStream_t)>;
 
 // One CUDA graph per solve: init residual -> WHILE(outer) { WHILE(inner) { step }, x-update,
 // residual }. Kernels set the two conditions from the device.
-int build_graph_fn(nsamg_handle* h, const ResidFn& enq_resid, const StepFn& enq_step, const XFn& enq_x) {
+int build_graph_fn(nsamg_handle* h, const ResidFn& enq_resid, const StepFn& enq_step, const XFn& enq_x,
+                   const XFn& enq_final) {
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
@@ -976,6 +986,10 @@ int build_graph_fn(nsamg_handle* h, const ResidFn& enq_resid, const StepFn& enq_
   enq_x(cs);
   enq_resid(cs, 0, (unsigned long long)hout, (unsigned long long)hin);
   CK(cudaStreamEndCapture(cs, &outer_body));
+  // after the last cycle: the per-solve diagnostics
+  CK(cudaStreamBeginCaptureToGraph(cs, g, &outer, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  enq_final(cs);
+  CK(cudaStreamEndCapture(cs, &g));
   CK(cudaGraphInstantiate(&h->exec, g, 0));
   h->graph = g;
   cudaStreamDestroy(cs);
@@ -985,7 +999,8 @@ int build_graph_fn(nsamg_handle* h, const ResidFn& enq_resid, const StepFn& enq_
 int build_graph(nsamg_handle* h) {
   return build_graph_fn(
       h, [h](cudaStream_t s, int init, unsigned long long co, unsigned long long ci) { enqueue_resid(h, s, init, co, ci); },
-      [h](cudaStream_t s, unsigned long long ci) { enqueue_step(h, s, ci); }, [h](cudaStream_t s) { enqueue_xupdate(h, s); });
+      [h](cudaStream_t s, unsigned long long ci) { enqueue_step(h, s, ci); }, [h](cudaStream_t s) { enqueue_xupdate(h, s); },
+      [h](cudaStream_t s) { enqueue_sknorm(h, s); });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1341,7 +1356,8 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     if (p.use_graph) {
       rc = build_graph_fn(
           h, [h](cudaStream_t s, int init, unsigned long long co, unsigned long long ci) { enqueue_bresid(h, s, init, co, ci); },
-          [h](cudaStream_t s, unsigned long long ci) { enqueue_bstep(h, s, ci); }, [h](cudaStream_t s) { enqueue_bxupdate(h, s); });
+          [h](cudaStream_t s, unsigned long long ci) { enqueue_bstep(h, s, ci); }, [h](cudaStream_t s) { enqueue_bxupdate(h, s); },
+          [h](cudaStream_t s) { enqueue_sknorm(h, s); });
       if (rc) return rc;
     } else {
       cudaGraph_t tmp;
@@ -1571,6 +1587,7 @@ int solve_batch_impl(nsamg_handle* h, const double* d_b, double* d_x, double rto
       enqueue_bxupdate(h, s);
       enqueue_bresid(h, s, 0, 0, 0);
     }
+    enqueue_sknorm(h, s);
   }
   CK(cudaMemcpyAsync(B->h_st, B->d_st, sizeof(GState) * B->nsys, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1589,6 +1606,7 @@ int solve_batch_impl(nsamg_handle* h, const double* d_b, double* d_x, double rto
       stats[sI].relres_implicit = g.relres_implicit;
       stats[sI].nrbe = g.nrbe;
       stats[sI].orth_loss = g.orth_loss;
+      stats[sI].sk_norm = g.sk_norm;
       stats[sI].bnorm = g.bnorm;
     }
     if (status < 0) worst = status;
@@ -1730,6 +1748,7 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
       enqueue_xupdate(h, s);
       enqueue_resid(h, s, 0, 0, 0);
     }
+    enqueue_sknorm(h, s);
   }
   CK(cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1745,6 +1764,7 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
     stats->relres_implicit = hs->relres_implicit;
     stats->nrbe = hs->nrbe;
     stats->orth_loss = hs->orth_loss;
+    stats->sk_norm = hs->sk_norm;
     stats->bnorm = hs->bnorm;
   }
   if (status < 0) return fail(status, status == NSAMG_ERR_NONFINITE ? "non-finite value in the iteration" : "solve failed");
@@ -2148,6 +2168,14 @@ int nsamg_batch_offsets(nsamg_handle* h, int64_t* out) {
   return NSAMG_OK;
 }
 
+int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream) {
+  if (!d_L || !d_out || k < 1 || k > NSAMG_MAX_RESTART || ld < k) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_sknorm: bad arguments");
+  ++g_launches;
+  launch_k(k_sknorm_matrix, 1, kSkThreads, (cudaStream_t)stream, d_L, ld, k, d_out);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
 void nsamg_destroy(nsamg_handle* h) { destroy_impl(h); }
 
 const char* nsamg_status_str(int s) {
@@ -2266,6 +2294,7 @@ void server_collect(nsamg_server* S) {
     r.stats.relres_implicit = g->relres_implicit;
     r.stats.nrbe = g->nrbe;
     r.stats.orth_loss = g->orth_loss;
+    r.stats.sk_norm = g->sk_norm;
     r.stats.bnorm = g->bnorm;
     r.status = status;
     r.state = 2;

@@ -482,6 +482,8 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
     if (!finite) st->status = -6;
     else if (!err) st->status = conv ? 0 : 1;
     st->done = stop_all ? 1 : 0;
+    if (a.init) st->klast = 0;
+    else if (st->k > 0) st->klast = st->k;
     st->i = 0;
     st->k = 0;
     st->stop = stop_all ? 1 : 0;
@@ -489,6 +491,96 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
     set_cond(a.cond_outer, stop_all ? 0 : 1);
     set_cond(a.cond_inner, stop_all ? 0 : 1);
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// ||S_k||_2 of the last cycle, S_k = (I + U_k)^-1 U_k with U_k = L_k^T the strictly upper part of
+// V_k^T V_k (Sec. 3: the basis has lost linear independence exactly when ||S_k||_2 = 1).
+// One block: column c of S by back substitution (thread c), then power iteration on S^T S with
+// the Rayleigh quotient ||S x||^2 (||x|| = 1), stopped when it changes by <= 1e-15 relative or
+// after kSkIters iterations. Fixed-order sums: the result is deterministic.
+// ------------------------------------------------------------------------------------------
+constexpr int kSkThreads = 64;
+constexpr int kSkIters = 300;
+
+__device__ double sk_norm_block(const double* __restrict__ L, int ld, int k) {
+  __shared__ double S[kMaxM][kMaxM + 1];
+  __shared__ double x[kMaxM], y[kMaxM];
+  __shared__ double s_val, s_prev;
+  __shared__ int s_stop;
+  const int t = threadIdx.x;
+  if (k <= 1) return 0.0;
+  if (t < k) {
+    const int c = t;
+    for (int r = c; r < k; ++r) S[r][c] = 0.0;
+    for (int r = c - 1; r >= 0; --r) {
+      double acc = L[c * ld + r];  // U[r][c]
+      for (int j = r + 1; j < c; ++j) acc = fma(-L[j * ld + r], S[j][c], acc);
+      S[r][c] = acc;
+    }
+    x[c] = 1.0 + 0.5 * (double)((c * 37) % 64) / 64.0;  // fixed start with no special direction
+  }
+  if (t == 0) {
+    s_prev = -1.0;
+    s_stop = 0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double q = 0.0;
+    for (int c = 0; c < k; ++c) q = fma(x[c], x[c], q);
+    s_val = 1.0 / sqrt(q);
+  }
+  __syncthreads();
+  if (t < k) x[t] *= s_val;
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < kSkIters; ++it) {
+    if (t < k) {  // y = S x (S strictly upper: columns > r)
+      double acc = 0.0;
+      for (int c = t + 1; c < k; ++c) acc = fma(S[t][c], x[c], acc);
+      y[t] = acc;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double q = 0.0;
+      for (int r = 0; r < k; ++r) q = fma(y[r], y[r], q);
+      s_val = q;  // Rayleigh quotient of S^T S
+    }
+    __syncthreads();
+    lam = s_val;
+    if (t < k) {  // x <- S^T y (rows < c)
+      double acc = 0.0;
+      for (int r = 0; r < t; ++r) acc = fma(S[r][t], y[r], acc);
+      x[t] = acc;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double q = 0.0;
+      for (int c = 0; c < k; ++c) q = fma(x[c], x[c], q);
+      const bool done = q == 0.0 || fabs(lam - s_prev) <= 1e-15 * lam;
+      s_prev = lam;
+      s_stop = done ? 1 : 0;
+      s_val = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    if (t < k) x[t] *= s_val;
+    __syncthreads();
+  }
+  return sqrt(lam);
+}
+
+__global__ void k_sknorm_states(GState* __restrict__ states) {
+  pdl_enter();
+  GState* st = states + blockIdx.x;
+  const double v = sk_norm_block(st->L, kMaxM + 1, min(st->klast, kMaxM));
+  if (threadIdx.x == 0) st->sk_norm = v;
+}
+
+__global__ void k_sknorm_matrix(const double* __restrict__ L, int ld, int k, double* __restrict__ out) {
+  pdl_enter();
+  const double v = sk_norm_block(L, ld, k);
+  if (threadIdx.x == 0) *out = v;
 }
 
 }  // namespace nsamg

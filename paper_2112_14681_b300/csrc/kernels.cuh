@@ -228,6 +228,8 @@ struct GState {
   int cycles;     // restart cycles started
   int status;     // 0 ok, 1 not converged, <0 error
   int converged;
+  int klast;      // Arnoldi vectors of the last finished cycle (rows of L it filled)
+  int pad1;
   double bnorm;
   double relres_true;
   double relres_implicit;
@@ -235,6 +237,7 @@ struct GState {
   double nrbe;        // ||r|| / (||b|| + ||A||_inf ||x||) of the last true residual
   double lsum;        // sum of squares of the L entries of the current cycle
   double orth_loss;   // sqrt(2 lsum): ||I - V^T V||_F of the last cycle (diagonal terms ~ eps)
+  double sk_norm;     // ||S_k||_2, S_k = (I + L^T)^-1 L^T, of the last cycle
   // Arnoldi / least-squares data (row-major with stride kMaxM + 1)
   double beta[kMaxM + 1];
   double invbeta[kMaxM + 1];

@@ -54,7 +54,8 @@ class AmgOptions(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("relres_true", ctypes.c_double), ("relres_implicit", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("nrbe", ctypes.c_double), ("orth_loss", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("nrbe", ctypes.c_double), ("orth_loss", ctypes.c_double),
+                ("sk_norm", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,7 +69,7 @@ EXPORTS = [
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
     "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
-    "nsamg_amg_default_options", "nsamg_amg_build", "nsamg_amg_num_levels", "nsamg_amg_level_info",
+    "nsamg_sknorm", "nsamg_amg_default_options", "nsamg_amg_build", "nsamg_amg_num_levels", "nsamg_amg_level_info",
     "nsamg_amg_level_splitting", "nsamg_amg_export", "nsamg_amg_setup_solver", "nsamg_amg_destroy",
 ]
 
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH):
         "nsamg_server_info": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "nsamg_server_destroy": (None, [vp]),
         "nsamg_ilu0_fixed_point": (i32, [ctypes.POINTER(Csr), i32, vp, vp]),
+        "nsamg_sknorm": (i32, [vp, i32, i32, vp, vp]),
         "nsamg_amg_default_options": (None, [ctypes.POINTER(AmgOptions)]),
         "nsamg_amg_build": (i32, [ctypes.POINTER(Csr), ctypes.POINTER(AmgOptions), vp, ctypes.POINTER(vp)]),
         "nsamg_amg_num_levels": (i32, [vp]),
@@ -314,8 +316,9 @@ def launches_per_step(h: Handle) -> int:
 
 
 def solve_launches(h: Handle, stats: dict) -> int:
-    """Kernel launches of a finished solve: 1 + iters * per_step + 2 * cycles."""
-    return 1 + stats["iters"] * launches_per_step(h) + 2 * (stats["restarts"] + 1)
+    """Kernel launches of a finished solve: initial residual + iters * per_step + 2 per cycle
+    (x-update, residual) + the final ||S_k||_2 kernel."""
+    return 2 + stats["iters"] * launches_per_step(h) + 2 * (stats["restarts"] + 1)
 
 
 def level_spmv(h: Handle, level: int, x, y) -> None:
@@ -355,6 +358,16 @@ def gram_noalloc(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
 
 def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
     _check(load().nsamg_update(int(n), int(i), _ptr(V), int(ldv), _ptr(w), float(beta), _ptr(h), _ptr(sumsq), stream))
+
+
+def sknorm(L, k: int | None = None, out=None, stream=None) -> float:
+    """||S_k||_2 of the strictly lower part of the device matrix L (torch, row-major)."""
+    import torch
+    k = int(L.shape[0] if k is None else k)
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=L.device)
+    _check(load().nsamg_sknorm(_ptr(L), int(L.stride(0)), k, _ptr(out), stream))
+    return float(out.cpu()[0])
 
 
 def ilu0_fixed_point(A, sweeps: int, stream=None) -> np.ndarray:

@@ -82,6 +82,8 @@ def test_batch_solve_matches_oracle_per_system(fp32, smoother, graph):
         assert abs(st["iters"] - ref.iters) <= 1, (k, st["iters"], ref.iters)
         if not fp32:
             assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+        # per-system ||S_k||_2 of the last cycle: tiny (the basis stays independent), nonzero
+        assert 0.0 < st["sk_norm"] <= st["orth_loss"] < 1e-6
 
 
 def test_batch_mixed_progress_and_restarts():
@@ -102,6 +104,7 @@ def test_batch_mixed_progress_and_restarts():
         xg = x.cpu().numpy()
     assert stats[1]["iters"] == 0 and stats[1]["converged"] and np.all(xg[off[1]:off[2]] == 0)
     assert stats[2]["iters"] == 0 and stats[2]["converged"]
+    assert stats[1]["sk_norm"] == 0.0 and stats[2]["sk_norm"] == 0.0  # no cycle ran
     for k in (0, 3, 4, 5):
         A = S[k][0]
         xs = xg[off[k]:off[k + 1]]

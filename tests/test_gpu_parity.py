@@ -420,6 +420,36 @@ def test_backward_error_and_orthogonality_diagnostics(name):
     ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, K.SmootherParams()), m=30, rtol=1e-8)
     ref_loss = np.sqrt(2.0) * np.linalg.norm(ref.L)
     assert st["orth_loss"] == pytest.approx(ref_loss, rel=0.5, abs=1e-15)
+    # ||S_k||_2 of the same cycle: the same order as the oracle's, and at most ||L||_F / (1 - ||L||_F)
+    from oracle.gmres import sk_norm
+    lf = st["orth_loss"] / np.sqrt(2.0)
+    assert 0.0 < st["sk_norm"] <= lf / (1.0 - lf) * (1 + 1e-12)
+    assert st["sk_norm"] == pytest.approx(sk_norm(ref.L), rel=0.5, abs=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 33, 64])
+@pytest.mark.parametrize("kind", ["random", "orthonormal", "dependent"])
+def test_sknorm_kernel_matches_oracle(k, kind):
+    """nsamg_sknorm on caller data against the oracle's definition (dense solve + 2-norm)."""
+    from oracle.gmres import sk_norm
+    rng = np.random.default_rng(100 + k)
+    n = 300
+    W = rng.standard_normal((n, k))
+    if kind == "orthonormal":
+        W = np.linalg.qr(W)[0]
+    elif kind == "dependent" and k >= 3:
+        W[:, -1] = W[:, :2] @ rng.standard_normal(2)
+    W /= np.linalg.norm(W, axis=0)
+    ld = 65
+    Lh = np.zeros((k, ld))
+    Lh[:, :k] = np.tril(W.T @ W, -1)
+    Lh[:, k:] = 7.0  # beyond the k x k block: must be ignored
+    Lh[np.arange(k), np.arange(k)] = 3.0  # diagonal: ignored too
+    got = nsamg.sknorm(dev(Lh), k)
+    want = sk_norm(np.tril(W.T @ W, -1))
+    assert got == pytest.approx(want, rel=1e-10, abs=1e-14)
+    if kind == "dependent" and k >= 3:
+        assert got == pytest.approx(1.0, abs=1e-8)
 
 
 def test_checkpoint_and_resume():

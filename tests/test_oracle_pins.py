@@ -470,7 +470,30 @@ MUTANTS = [
     ("oracle.kernels", "t = -(T @ t) / d", "t = (T @ t) / d", "polygs"),        # sign of the Neumann term
     ("oracle.kernels", "T = U if backward else L", "T = L if backward else U", "polygs"),  # transposed operand
     ("oracle.kernels", "f = dinv * y\n        t = f.copy()", "f = y\n        t = f.copy()", "ilu"),  # D_U^-1 dropped
+    ("oracle.gmres", "S = np.linalg.solve(np.eye(k) + U, U)", "S = U", "sknorm"),  # (I + U)^-1 dropped
 ]
+
+
+def _check_sknorm(fn):
+    # k = 2: U = [[0, a], [0, 0]], (I + U)^-1 U = U, so ||S||_2 = |a|
+    assert fn(np.array([[0.0, 0.0], [0.3, 0.0]])) == pytest.approx(0.3, rel=1e-14)
+    rng = np.random.default_rng(4)
+    n, k = 200, 12
+    V = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    assert fn(np.tril(V.T @ V, -1)) <= 1e-14  # orthonormal basis
+    W = rng.standard_normal((n, k))
+    W[:, -1] = W[:, :4] @ rng.standard_normal(4)  # last column dependent on the first four
+    W /= np.linalg.norm(W, axis=0)
+    assert fn(np.tril(W.T @ W, -1)) == pytest.approx(1.0, abs=1e-9)  # dependence: ||S||_2 = 1
+    W2 = rng.standard_normal((n, k))
+    W2 /= np.linalg.norm(W2, axis=0)
+    assert 0.0 < fn(np.tril(W2.T @ W2, -1)) < 1.0 - 1e-3  # independent: below 1
+
+
+def test_sknorm_pins():
+    """Sec. 3: ||S_k||_2 is 0 for an orthonormal basis and reaches 1 exactly at linear dependence."""
+    from oracle.gmres import sk_norm
+    _check_sknorm(sk_norm)
 
 
 def _mutated(modname, old, new):
@@ -491,6 +514,10 @@ def test_planted_mistake_is_caught(modname, old, new, pin):
     if pin == "project":
         with pytest.raises(AssertionError):
             _check_projection(ns["project"])
+        return
+    if pin == "sknorm":
+        with pytest.raises(AssertionError):
+            _check_sknorm(ns["sk_norm"])
         return
     if pin == "lrows":
         with pytest.raises(AssertionError):
