@@ -14,6 +14,7 @@ TEST INFRASTRUCTURE ONLY (see the package header): nothing on the product path i
   bamg_direct     BAMG-direct interpolation with f = 1, closed form of eq. (bamgdir):
                   w_ij = -(a_ij + beta_i / n_{C_i^s}) / (a_ii + sum_{k weak} a_ik),
                   beta_i = sum of the strong F-neighbour couplings
+  mm_ext          MM-ext interpolation W = -[(D_FF + D_gamma)^-1 (A^s_FF + D_beta)] [D_beta^-1 A^s_FC]
   galerkin        R = P^T, A_c = R (A P)  (Sec. 5, eq. A_k)
   coarse_inverse  dense inverse of the coarsest operator
   ilu0_factors    ILU(0) by fixed-point sweeps (kernels.ilu0_fixed_point) in the row-scaled LDU
@@ -164,6 +165,46 @@ def bamg_direct(A: sp.csr_matrix, s: np.ndarray, cf: np.ndarray, nc: int) -> sp.
     return P
 
 
+def mm_ext(A: sp.csr_matrix, s: np.ndarray, cf: np.ndarray, nc: int) -> sp.csr_matrix:
+    """MM-ext interpolation (Sec. 5.1): with A = D + A^s + A^w split by the strength flags and the
+    F/C blocks of the splitting,
+        W = -[(D_FF + D_gamma)^-1 (A^s_FF + D_beta)] [D_beta^-1 A^s_FC],
+        D_beta = diag(A^s_FC 1_C),  D_gamma = diag(A^w_FF 1_F + A^w_FC 1_C),
+    and P = [W; I] in the original ordering. An F-point with beta = 0 (no strong C-neighbour)
+    contributes no distance-two path (its row of D_beta^-1 A^s_FC is taken as zero)."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    rows = _rows(A)
+    cols = A.indices
+    off = rows != cols
+    strong = s.astype(bool) & off
+    weak = off & ~strong
+    Fp = np.flatnonzero(cf < 0)
+    fidx = np.full(n, -1)
+    fidx[Fp] = np.arange(Fp.size)
+    As = sp.csr_matrix((np.where(strong, A.data, 0.0), cols.copy(), A.indptr.copy()), shape=A.shape)
+    Aw = sp.csr_matrix((np.where(weak, A.data, 0.0), cols.copy(), A.indptr.copy()), shape=A.shape)
+    Cmask = cf >= 0
+    As_FF = As[Fp][:, Fp]
+    As_FC = As[Fp][:, np.flatnonzero(Cmask)]
+    Aw_F = Aw[Fp]
+    d_FF = A.diagonal()[Fp]
+    beta = np.asarray(As_FC.sum(axis=1)).ravel()
+    gamma = np.asarray(Aw_F.sum(axis=1)).ravel()  # A^w_FF 1_F + A^w_FC 1_C
+    inv_beta = np.where(beta != 0.0, 1.0 / np.where(beta != 0.0, beta, 1.0), 0.0)
+    M1 = sp.diags(1.0 / (d_FF + gamma)) @ (As_FF + sp.diags(beta))
+    M2 = sp.diags(inv_beta) @ As_FC
+    W = -sp.csr_matrix(M1 @ M2)
+    W.sum_duplicates()
+    P = sp.lil_matrix((n, nc))
+    Wc = W.tocoo()
+    P[Fp[Wc.row], Wc.col] = Wc.data
+    P[np.flatnonzero(Cmask), cf[Cmask]] = 1.0
+    P = sp.csr_matrix(P)
+    P.sort_indices()
+    return P
+
+
 def galerkin(A: sp.csr_matrix, P: sp.csr_matrix):
     """R = P^T and the Galerkin coarse operator A_c = R (A P)."""
     R = sp.csr_matrix(P.T)
@@ -190,7 +231,8 @@ def ilu0_factors(A: sp.csr_matrix, sweeps: int):
 
 
 def setup(A: sp.csr_matrix, theta: float = 0.25, strength_mode: str = "abs", max_levels: int = 25,
-          coarse_max: int = 512, direct_max: int = 512, seed: int = 0, ilu_levels=(0,), ilu_sweeps: int = 3):
+          coarse_max: int = 512, direct_max: int = 512, seed: int = 0, ilu_levels=(0,), ilu_sweeps: int = 3,
+          interp: str = "bamg"):
     """The whole hierarchy: a list of per-level dicts (A, s, cf, P, R, and ILU factors on the
     requested non-coarsest levels) and the dense coarse inverse (None above direct_max)."""
     levels = [{"A": sp.csr_matrix(A)}]
@@ -201,7 +243,7 @@ def setup(A: sp.csr_matrix, theta: float = 0.25, strength_mode: str = "abs", max
         cf, nc = pmis(Al, s, seed + 7919 * len(levels))
         if nc == 0 or nc >= 0.9 * Al.shape[0]:
             break
-        P = bamg_direct(Al, s, cf, nc)
+        P = bamg_direct(Al, s, cf, nc) if interp == "bamg" else mm_ext(Al, s, cf, nc)
         R, Ac = galerkin(Al, P)
         lev.update(s=s, cf=cf, P=P, R=R)
         levels.append({"A": Ac})

@@ -223,6 +223,55 @@ def test_bamg_direct_pins():
     _check_bamg(OS)
 
 
+# ---- MM-ext interpolation (Sec. 5.1) --------------------------------------------------------
+
+def _check_mmext(mod):
+    for A in (zero_rowsum(300, 5), zero_rowsum(250, 11, density=0.05)):
+        s = mod.strength(A, 0.25)
+        cf, nc = mod.pmis(A, s, 3)
+        P = mod.mm_ext(A, s, cf, nc).toarray()
+        # constants interpolated exactly on zero-row-sum operators
+        assert np.allclose(P.sum(axis=1), 1.0, rtol=0, atol=1e-13)
+        assert np.array_equal(P[cf >= 0], np.eye(nc)[cf[cf >= 0]])
+        # element form of the extended weights, derived by hand from the matrix product:
+        # w_ij = -(a^s_ij + sum_{k in F^s_i} a_ik a^s_kj / beta_k) / (a_ii + gamma_i), j in C
+        n = A.shape[0]
+        beta, gamma, strongC, strongF = np.zeros(n), np.zeros(n), {}, {}
+        for i in range(n):
+            sc, sf = {}, {}
+            for p in range(A.indptr[i], A.indptr[i + 1]):
+                j, a = A.indices[p], A.data[p]
+                if j == i:
+                    continue
+                if not s[p]:
+                    gamma[i] += a
+                elif cf[j] >= 0:
+                    sc[j] = a
+                    beta[i] += a
+                else:
+                    sf[j] = a
+            strongC[i], strongF[i] = sc, sf
+        Ad = A.diagonal()
+        for i in np.flatnonzero(cf < 0)[:60]:
+            w = np.zeros(nc)
+            for j, a in strongC[i].items():
+                w[cf[j]] += a
+            for k, aik in strongF[i].items():
+                if beta[k] != 0.0:
+                    for j, akj in strongC[k].items():
+                        w[cf[j]] += aik * akj / beta[k]
+            w = -w / (Ad[i] + gamma[i])
+            assert np.allclose(P[i], w, rtol=1e-12, atol=1e-15), i
+        # rows without strong F-neighbours reduce to direct interpolation
+        P0 = mod.bamg_direct(A, s, cf, nc).toarray()
+        rows = [i for i in np.flatnonzero(cf < 0) if not strongF[i]]
+        assert np.allclose(P[rows], P0[rows], rtol=1e-12, atol=1e-15)
+
+
+def test_mm_ext_pins():
+    _check_mmext(OS)
+
+
 # ---- Galerkin product and the coarse inverse (Sec. 5, eq. A_k) ------------------------------
 
 def _check_galerkin(mod):
@@ -306,6 +355,9 @@ SETUP_MUTANTS = [
     ("beta / len(strong_c)) / den", "beta) / den", _check_bamg),                      # beta not spread
     ("den = aii + weak", "den = aii", _check_bamg),                                    # weak not lumped
     ("elif not s[p]:\n                weak += a", "elif not s[p]:\n                weak -= a", _check_bamg),
+    ("M1 = sp.diags(1.0 / (d_FF + gamma)) @ (As_FF + sp.diags(beta))", "M1 = sp.diags(1.0 / (d_FF + gamma)) @ As_FF",
+     _check_mmext),                                                                    # D_beta dropped
+    ("M1 = sp.diags(1.0 / (d_FF + gamma)) @", "M1 = sp.diags(1.0 / d_FF) @", _check_mmext),  # D_gamma dropped
     ("Ac = sp.csr_matrix(R @ sp.csr_matrix(A @ P))", "Ac = sp.csr_matrix(P.T @ sp.csr_matrix(A.T @ P))", _check_galerkin),
     ("z = ((z ^ (z >> 27)) * 0x94D049BB133111EB)", "z = ((z ^ (z >> 26)) * 0x94D049BB133111EB)", _check_splitmix),
 ]
