@@ -263,6 +263,9 @@ int nsamg_ilu0_fixed_point(const nsamg_csr* A, int sweeps, double* lu_out, void*
  *   BAMG-direct interpolation, closed form of eq. (bamgdir) with f = 1:
  *             w_ij = -(a_ij + beta_i / n_{C_i^s}) / (a_ii + sum_{k weak} a_ik), beta_i the sum of
  *             the strong F-couplings; C rows are unit rows;
+ *   MM-ext    (interp = 1, Sec. 5.1) W = -[(D_FF + D_gamma)^-1 (A^s_FF + D_beta)] [D_beta^-1 A^s_FC],
+ *             D_beta = diag(A^s_FC 1), D_gamma = diag(A^w_FF 1 + A^w_FC 1) (weak couplings), P = [W; I]
+ *             in the original ordering; an F-point with beta = 0 adds no distance-two path;
  *   Galerkin  R = P^T, A_c = R (A P) (Sec. 5, eq. A_k); each entry of a product is summed in the
  *             order of the left operand's row, with products and sums rounded separately;
  *   ILU(0)    `ilu_sweeps` fixed-point sweeps (as nsamg_ilu0_fixed_point) on every level l < L-1
@@ -281,7 +284,7 @@ typedef struct {
   uint64_t seed;         /* PMIS seed (default 0)                                               */
   uint64_t ilu_levels;   /* bit l: ILU(0) factors on level l (default 1: the finest level)      */
   int32_t ilu_sweeps;    /* fixed-point sweeps, >= 0 (default 3)                                */
-  int32_t pad;
+  int32_t interp;        /* 0: BAMG-direct (default), 1: MM-ext                                 */
 } nsamg_amg_options;
 
 typedef struct nsamg_amg nsamg_amg;

@@ -8,6 +8,7 @@
 //                 points that strongly depend on a new C-point become F; F-points left without a
 //                 strong C-neighbour are promoted to C (all at once: see k_promote_cand)
 //   BAMG-direct   w_ij = -(a_ij + beta_i / n_{C_i^s}) / (a_ii + sum_{k weak} a_ik)  (eq. bamgdir)
+//   MM-ext        W = -[(D_FF + D_gamma)^-1 (A^s_FF + D_beta)] [D_beta^-1 A^s_FC], one SpGEMM
 //   Galerkin      R = P^T, A_c = R (A P) by a row-wise k-way merge SpGEMM whose sums run in the
 //                 order of the left operand's row (the order of a sequential row-by-row product)
 //   ILU(0)        fixed-point sweeps on the pattern of A, then the row-scaled LDU form
@@ -388,6 +389,97 @@ __global__ void k_interp_fill(int n, const int* __restrict__ rp, const int* __re
     pci[o] = cf[j];
     pv[o] = -(v[p] + beta / (double)nc) / den;
     ++o;
+  }
+}
+
+// ---- MM-ext interpolation ------------------------------------------------------------------
+// W = -[(D_FF + D_gamma)^-1 (A^s_FF + D_beta)] [D_beta^-1 A^s_FC] = -M1 M2, rows numbered over the
+// F-points (fidx). M1 row: the strong F-couplings and the diagonal beta_i, scaled by
+// 1 / (a_ii + gamma_i); M2 row: the strong C-couplings scaled by 1 / beta_i (0 when beta_i = 0).
+__global__ void k_flag_f(int n, const int* __restrict__ cf, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = cf[i] < 0 ? 1 : 0;
+}
+
+__global__ void k_mmext_count(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const unsigned char* __restrict__ s, const int* __restrict__ cf, const int* __restrict__ fidx,
+                              int* __restrict__ c1, int* __restrict__ c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] >= 0) return;
+  int nf = 1, nc = 0;  // M1 keeps the diagonal entry beta_i
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    if (j == i || !s[p]) continue;
+    if (cf[j] >= 0) ++nc;
+    else ++nf;
+  }
+  c1[fidx[i]] = nf;
+  c2[fidx[i]] = nc;
+}
+
+__global__ void k_mmext_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                             const unsigned char* __restrict__ s, const int* __restrict__ cf, const int* __restrict__ fidx,
+                             const int* __restrict__ m1rp, int* __restrict__ m1ci, double* __restrict__ m1v,
+                             const int* __restrict__ m2rp, int* __restrict__ m2ci, double* __restrict__ m2v,
+                             int* __restrict__ bad_row) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] >= 0) return;
+  double aii = 0.0, gamma = 0.0, beta = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    if (j == i) aii += v[p];
+    else if (!s[p]) gamma += v[p];
+    else if (cf[j] >= 0) beta += v[p];
+  }
+  const double den = aii + gamma;
+  if (den == 0.0) {
+    atomicMin(bad_row, i);
+    return;
+  }
+  const double sc = 1.0 / den;
+  const double ib = beta != 0.0 ? 1.0 / beta : 0.0;
+  const int fi = fidx[i];
+  int o1 = m1rp[fi], o2 = m2rp[fi];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    if (j == i) {
+      m1ci[o1] = fi;
+      m1v[o1++] = __dmul_rn(sc, beta);
+      continue;
+    }
+    if (!s[p]) continue;
+    if (cf[j] >= 0) {
+      m2ci[o2] = cf[j];
+      m2v[o2++] = __dmul_rn(ib, v[p]);
+    } else {
+      m1ci[o1] = fidx[j];
+      m1v[o1++] = __dmul_rn(sc, v[p]);
+    }
+  }
+}
+
+__global__ void k_mmext_pcount(int n, const int* __restrict__ cf, const int* __restrict__ fidx, const int* __restrict__ wrp,
+                               int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cnt[i] = cf[i] >= 0 ? 1 : wrp[fidx[i] + 1] - wrp[fidx[i]];
+}
+
+__global__ void k_mmext_pfill(int n, const int* __restrict__ cf, const int* __restrict__ fidx, const int* __restrict__ wrp,
+                              const int* __restrict__ wci, const double* __restrict__ wv, const int* __restrict__ prp,
+                              int* __restrict__ pci, double* __restrict__ pv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = prp[i];
+  if (cf[i] >= 0) {
+    pci[o] = cf[i];
+    pv[o] = 1.0;
+    return;
+  }
+  const int fi = fidx[i];
+  for (int q = wrp[fi]; q < wrp[fi + 1]; ++q, ++o) {
+    pci[o] = wci[q];
+    pv[o] = -wv[q];
   }
 }
 
@@ -816,6 +908,55 @@ int spgemm(DMem& mem, const GCsr& A, const GCsr& B, GCsr& C, cudaStream_t s) {
   return NSAMG_OK;
 }
 
+// MM-ext prolongation of level L (needs L.s, L.cf, L.nc).
+int interpolate_mmext(DMem& mem, GLevel& L, cudaStream_t s) {
+  const GCsr& A = L.A;
+  const int n = A.n;
+  DMem tmp;
+  int *flag = nullptr, *fidx = nullptr, *c1 = nullptr, *c2 = nullptr, *bad = nullptr, *cnt = nullptr;
+  SK(tmp.alloc(&flag, n));
+  SK(tmp.alloc(&fidx, n + 1));
+  SK(tmp.alloc(&bad, 1));
+  SK(tmp.alloc(&cnt, n));
+  k_flag_f<<<nblocks(n), kSetupThreads, 0, s>>>(n, L.cf, flag);
+  SK(scan_excl<int>(flag, fidx, n, s));
+  int nF = 0;
+  SK(read_scalar(fidx + n, &nF, s));
+  GCsr M1, M2, W;
+  M1.n = M1.m = nF;
+  M2.n = nF;
+  M2.m = L.nc;
+  SK(tmp.alloc(&c1, nF));
+  SK(tmp.alloc(&c2, nF));
+  k_mmext_count<<<nblocks(n), kSetupThreads, 0, s>>>(n, A.rp, A.ci, L.s, L.cf, fidx, c1, c2);
+  SK(rowptr_from_counts(tmp, c1, nF, &M1.rp, &M1.nnz, s));
+  SK(rowptr_from_counts(tmp, c2, nF, &M2.rp, &M2.nnz, s));
+  SK(tmp.alloc(&M1.ci, M1.nnz));
+  SK(tmp.alloc(&M1.v, M1.nnz));
+  SK(tmp.alloc(&M2.ci, M2.nnz));
+  SK(tmp.alloc(&M2.v, M2.nnz));
+  const int big = INT32_MAX;
+  CK(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+  k_mmext_fill<<<nblocks(n), kSetupThreads, 0, s>>>(n, A.rp, A.ci, A.v, L.s, L.cf, fidx, M1.rp, M1.ci, M1.v, M2.rp, M2.ci,
+                                                     M2.v, bad);
+  int hbad = 0;
+  SK(read_scalar(bad, &hbad, s));
+  if (hbad != INT32_MAX)
+    return fail(NSAMG_ERR_BAD_MATRIX, "setup: MM-ext interpolation undefined in row " + std::to_string(hbad) +
+                                          " (a_ii + gamma_i = 0)");
+  SK(spgemm(tmp, M1, M2, W, s));
+  k_mmext_pcount<<<nblocks(n), kSetupThreads, 0, s>>>(n, L.cf, fidx, W.rp, cnt);
+  L.P.n = n;
+  L.P.m = L.nc;
+  SK(rowptr_from_counts(mem, cnt, n, &L.P.rp, &L.P.nnz, s));
+  SK(mem.alloc(&L.P.ci, L.P.nnz));
+  SK(mem.alloc(&L.P.v, L.P.nnz));
+  k_mmext_pfill<<<nblocks(n), kSetupThreads, 0, s>>>(n, L.cf, fidx, W.rp, W.ci, W.v, L.P.rp, L.P.ci, L.P.v);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return NSAMG_OK;
+}
+
 // Strength flags, PMIS splitting (cf, nc) of level A.
 int coarsen(DMem& mem, GLevel& L, double theta, int neg_mode, uint64_t seed, cudaStream_t s, int* rounds_out) {
   const GCsr& A = L.A;
@@ -1048,7 +1189,7 @@ int build(const nsamg_csr& A0, const nsamg_amg_options& o, nsamg_amg* g, cudaStr
     SK(coarsen(g->mem, L, o.theta, o.strength_mode, o.seed + 7919ull * (uint64_t)(l + 1), s, &rounds));
     g->pmis_rounds.push_back(rounds);
     if (L.nc == 0 || (double)L.nc >= 0.9 * L.A.n) break;
-    SK(interpolate(g->mem, L, s));
+    SK(o.interp == 1 ? interpolate_mmext(g->mem, L, s) : interpolate(g->mem, L, s));
     SK(transpose(g->mem, L.P, nullptr, true, L.R, s));
     DMem tmp;
     GCsr AP, Ac;
@@ -1080,14 +1221,15 @@ void nsamg_amg_default_options(nsamg_amg_options* o) {
   o->seed = 0;
   o->ilu_levels = 1;
   o->ilu_sweeps = 3;
-  o->pad = 0;
+  o->interp = 0;
 }
 
 int nsamg_amg_build(const nsamg_csr* A, const nsamg_amg_options* opt, void* cuda_stream, nsamg_amg** out) {
   if (out) *out = nullptr;
   if (!A || !opt || !out) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_amg_build: null argument");
   if (!(opt->theta >= 0.0 && opt->theta <= 1.0) || opt->max_levels < 1 || opt->coarse_max < 1 || opt->direct_max < 0 ||
-      opt->direct_max > 8192 || opt->ilu_sweeps < 0 || (opt->strength_mode != 0 && opt->strength_mode != 1))
+      opt->direct_max > 8192 || opt->ilu_sweeps < 0 || (opt->strength_mode != 0 && opt->strength_mode != 1) ||
+      (opt->interp != 0 && opt->interp != 1))
     return fail(NSAMG_ERR_INVALID_ARG, "nsamg_amg_build: option out of range");
   int rc = validate(*A, true, true, "amg A");
   if (rc) return rc;

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
 class AmgOptions(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("strength_mode", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("coarse_max", ctypes.c_int32), ("direct_max", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("ilu_levels", ctypes.c_uint64), ("ilu_sweeps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("ilu_levels", ctypes.c_uint64), ("ilu_sweeps", ctypes.c_int32), ("interp", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -384,7 +384,7 @@ def amg_default_options(**overrides) -> AmgOptions:
     o = AmgOptions()
     load().nsamg_amg_default_options(ctypes.byref(o))
     for k, v in overrides.items():
-        if not hasattr(o, k) or k == "pad":
+        if not hasattr(o, k):
             raise KeyError(k)
         setattr(o, k, float(v) if k == "theta" else int(v))
     return o

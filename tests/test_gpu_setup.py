@@ -160,3 +160,51 @@ def test_no_coarsening_when_small():
         H = g.export()
         assert H.nlevels == 1 and H.levels[0].P is None
         assert np.allclose(H.coarse_inv @ A.toarray(), np.eye(A.shape[0]), atol=1e-10)
+
+
+@pytest.mark.parametrize("name", ["p21", "z3000"])
+def test_mm_ext_levels_match_the_oracle(name):
+    """MM-ext interpolation (Sec. 5.1) on every level against the oracle's matrix formula; the
+    Galerkin products of the MM-ext hierarchy as before."""
+    A, kw, mode, _, _ = built(name)
+    opt = nsamg.amg_default_options(ilu_levels=0, direct_max=512, interp=1, **kw)
+    with nsamg.amg_build(A, opt) as g:
+        H = g.export()
+        splits = [g.splitting(l) for l in range(H.nlevels - 1)]
+    assert H.nlevels >= 3
+    for l, lev in enumerate(H.levels[:-1]):
+        cf, strong = splits[l]
+        s_or = OS.strength(lev.A, 0.25, mode)
+        assert np.array_equal(strong, s_or)
+        cf_or, nc = OS.pmis(lev.A, s_or, kw["seed"] + 7919 * (l + 1))
+        assert np.array_equal(cf, cf_or)
+        P_or = OS.mm_ext(lev.A, s_or, cf_or, nc)
+        # each weight is a sum of up to k = (row length of A) products of mixed sign, summed in
+        # another order by the oracle: |difference| <= 2 k eps max|P| (rounding of both sides)
+        k = int(np.diff(lev.A.indptr).max())
+        assert abs(lev.P - P_or).max() <= 2 * k * np.finfo(float).eps * abs(P_or).max(), l
+        assert lev.P.nnz >= P_or.nnz
+        _, Ac_or = OS.galerkin(lev.A, lev.P)
+        # componentwise: |difference| <= 2 k eps (|R| |A| |P|), k the longest chain of products
+        R = sp.csr_matrix(lev.P.T)
+        bound = (abs(R) @ abs(lev.A) @ abs(lev.P)).toarray()
+        kk = int(np.diff(R.indptr).max() + np.diff(lev.A.indptr).max() + np.diff(lev.P.indptr).max())
+        D = abs(H.levels[l + 1].A - Ac_or).toarray()
+        assert np.all(D <= 2 * kk * np.finfo(float).eps * bound), l
+
+
+def test_solve_on_mm_ext_hierarchy():
+    A = pressure3d_7pt(32, seed=2)
+    b = rhs_uniform(A.shape[0], 3)
+    p = nsamg.default_params(smoother=nsamg.HYBRID_ILU0)
+    its = {}
+    for interp in (0, 1):
+        with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=512, interp=interp)) as g:
+            with g.setup_solver(p) as h:
+                x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+                st = nsamg.solve(h, torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=300)
+                torch.cuda.synchronize()
+                assert st["converged"]
+                assert np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b) <= 1e-8
+                its[interp] = st["iters"]
+    assert its[1] <= its[0] + 2
