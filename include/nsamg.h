@@ -88,6 +88,13 @@ typedef struct {
   int32_t spmv_group;    /* 0: autotune at setup (CSR with 1..32 threads per row, or SELL-32-sigma
                             for matrices with >= 16384 rows); 1..32: CSR with that many threads per
                             row; -1: SELL-32-sigma wherever available                              */
+  int32_t fuse_tail;     /* 1: the V-cycle below the first level with at most 8192 rows (every
+                            smoother pass with all its Neumann terms, residual, transfers and the
+                            coarse solve) runs as one thread-block-cluster kernel that stages each
+                            pass's source vector in shared memory; bitwise the same result as the
+                            separate launches. 0 (default): one launch per pass, which measured
+                            faster on B300 (16 SMs of a cluster are latency bound where 148 SMs
+                            finish a pass in one wave). Batches ignore it.                        */
 } nsamg_params;
 
 typedef struct {

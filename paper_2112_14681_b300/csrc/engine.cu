@@ -386,6 +386,7 @@ inline VC<T> cref(const T* p) {
 template <typename TM, typename TX, typename TY>
 void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
   op.n = M.n;
+  op.src_n = M.m;
   op.rp = M.rp;
   op.ci = M.ci;
   op.v = M.v;
@@ -460,6 +461,11 @@ struct nsamg_handle {
   struct BatchData* batch = nullptr;  // set for handles made by nsamg_batch_setup
   bool shared_mats = false;           // a solver context: matrices belong to another handle
   double anorm_inf = 0.0;             // ||A_0||_inf (for the backward error)
+  // fused V-cycle tail (levels >= tail_l0 run by one cluster kernel); tail_l0 = 0: off
+  int tail_l0 = 0;
+  int tail_np = 0;
+  int tail_ncl = 0;
+  void* tail_passes = nullptr;  // TailPass<double> or TailPass<float> array (device)
   size_t ctx_bytes = 0;               // device bytes of the per-solve workspace (server accounting)
 };
 
@@ -500,9 +506,27 @@ struct Ctx {
   const int* skip;
 };
 
+// While a fused tail is being recorded, passes are appended here instead of launched.
+template <typename T>
+std::vector<TailPass<T>>*& tail_recorder() {
+  thread_local std::vector<TailPass<T>>* r = nullptr;
+  return r;
+}
+
 template <typename T>
 void run(RowOp<T, T, T> op, int G, const Ctx& c) {
   op.skip = c.skip;
+  if (std::vector<TailPass<T>>* rec = tail_recorder<T>()) {
+    if (op.n <= 0) return;
+    TailPass<T> P;
+    P.op = op;
+    P.op.skip = nullptr;
+    P.G = op.v ? G : 1;
+    P.epi = epi_code(op);
+    if (op.v && op.sell.nchunks > 0) P.epi = -100;  // SELL layout: not fusable (flags the recording)
+    rec->push_back(P);
+    return;
+  }
   launch_row(op, G, c.s);
 }
 
@@ -706,6 +730,17 @@ void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c
     launch_k(k_bdense_gemv<T, T>, nb, kThreads, c.s, B->ncrows, B->d_row_sys, B->d_coff, B->d_cblk,
                                                   bcoarse_ptr(B, (T*)nullptr), b, x, c.skip);
   } else if (C) {
+    if (std::vector<TailPass<T>>* rec = tail_recorder<T>()) {
+      TailPass<T> P;
+      P.dense = 1;
+      P.C = C;
+      P.op.n = L.n;
+      P.op.src_n = L.n;
+      P.op.src = b;
+      P.op.out = x;
+      rec->push_back(P);
+      return;
+    }
     ++g_launches;
     const int nb = (L.n * 32 + kThreads - 1) / kThreads;
     launch_k(k_dense_gemv<T, T>, nb, kThreads, c.s, L.n, C, b, x, c.skip);
@@ -717,8 +752,32 @@ void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c
 // One V-cycle with zero initial guess on level l (Sec. 5): pre-smooth, residual, restrict,
 // recurse, prolongate and correct, post-smooth.
 template <typename T>
+void launch_tail(nsamg_handle* h, const Ctx& c) {
+  ++g_launches;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(h->tail_ncl);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = sizeof(T) * kTailStage;
+  cfg.stream = c.s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = h->tail_ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, k_tail<T>, (const TailPass<T>*)h->tail_passes, h->tail_np, c.skip);
+}
+
+template <typename T>
 void vcycle(nsamg_handle* h, std::vector<Level<T>>& lv, int l, VC<T> b, VRef<T> x, const Ctx& c) {
   Level<T>& L = lv[l];
+  if (l > 0 && l == h->tail_l0 && h->tail_passes && !tail_recorder<T>()) {
+    launch_tail<T>(h, c);  // every pass of levels >= l in one cluster kernel
+    return;
+  }
   if (l == (int)lv.size() - 1) {
     coarse_solve(h, L, b, x, c);
     return;
@@ -1094,6 +1153,7 @@ int check_params(const nsamg_params& p) {
   if (p.vcycle_fp32 != 0 && p.vcycle_fp32 != 1) return fail(NSAMG_ERR_INVALID_ARG, "vcycle_fp32 must be 0 or 1");
   if (p.spmv_group < -1 || p.spmv_group > 32 || (p.spmv_group > 0 && (p.spmv_group & (p.spmv_group - 1))))
     return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be -1, 0 or a power of two <= 32");
+  if (p.fuse_tail != 0 && p.fuse_tail != 1) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0 or 1");
   return NSAMG_OK;
 }
 
@@ -1261,6 +1321,69 @@ int alloc_workspace(nsamg_handle* h) {
   return NSAMG_OK;
 }
 
+// Record the passes of the V-cycle below the first level with at most kTailStage rows and keep
+// them on the device for k_tail; picks the largest cluster (16, else 8 CTAs) the device can host.
+// Leaves the tail off (separate launches) when nothing would be fused.
+template <typename T>
+int build_tail(nsamg_handle* h, std::vector<Level<T>>& lv) {
+  if (h->tail_passes) {
+    cudaFree(h->tail_passes);
+    h->tail_passes = nullptr;
+  }
+  h->tail_l0 = h->tail_np = h->tail_ncl = 0;
+  if (!h->p.fuse_tail || h->batch) return NSAMG_OK;
+  const int nl = (int)lv.size();
+  int l0 = 0;
+  for (int l = 1; l < nl; ++l)
+    if (lv[l].n <= kTailStage) {
+      l0 = l;
+      break;
+    }
+  if (l0 == 0 || l0 >= nl - 1) return NSAMG_OK;  // at least one smoothed level below the cut
+  std::vector<TailPass<T>> rec;
+  tail_recorder<T>() = &rec;
+  vcycle(h, lv, l0, cref((const T*)lv[l0].b), vref(lv[l0].x), Ctx{h->stream, nullptr});
+  tail_recorder<T>() = nullptr;
+  for (const auto& P : rec)
+    if (P.epi == -100 || P.op.src_n > kTailStage) return NSAMG_OK;
+  CK(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * kTailStage)));
+  CK(cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  int want = 16;
+  if (const char* e = std::getenv("NSAMG_TAIL_CLUSTER")) want = std::atoi(e);
+  int ncl = 0;
+  for (int cand : {16, 8, 4}) {
+    if (cand > want) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cand);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = sizeof(T) * kTailStage;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cand;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, k_tail<T>, &cfg) == cudaSuccess && num > 0) {
+      ncl = cand;
+      break;
+    }
+  }
+  cudaGetLastError();
+  if (!ncl) return NSAMG_OK;
+  CK(cudaMalloc(&h->tail_passes, sizeof(TailPass<T>) * rec.size()));
+  CK(cudaMemcpy(h->tail_passes, rec.data(), sizeof(TailPass<T>) * rec.size(), cudaMemcpyHostToDevice));
+  h->tail_l0 = l0;
+  h->tail_np = (int)rec.size();
+  h->tail_ncl = ncl;
+  return NSAMG_OK;
+}
+
+int build_tail_any(nsamg_handle* h) {
+  return h->fp32 ? build_tail(h, h->lv32) : build_tail(h, h->lv);
+}
+
 int finish_graph(nsamg_handle* h) {
   if (!h->p.use_graph) {  // count the launches of one step without running it
     cudaGraph_t tmp;
@@ -1372,6 +1495,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
       cudaStreamDestroy(cs);
     }
   } else {
+    if ((rc = build_tail_any(h))) return rc;
     if ((rc = finish_graph(h))) return rc;
   }
   CK(cudaGetLastError());
@@ -1425,6 +1549,7 @@ int clone_context(nsamg_handle* parent, nsamg_handle** out) {
   for (auto& L : h->lv) vec_bytes += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
   for (auto& L : h->lv32) vec_bytes += 6 * sizeof(float) * (size_t)L.n;
   h->ctx_bytes += vec_bytes;
+  if ((rc = build_tail_any(h))) return bail(rc);
   if ((rc = finish_graph(h))) return bail(rc);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail(NSAMG_ERR_CUDA, "sync"));
   *out = h;
@@ -1623,6 +1748,7 @@ void destroy_impl(nsamg_handle* h) {
   destroy_batch(h->batch);
   h->batch = nullptr;
   if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->tail_passes) cudaFree(h->tail_passes);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->shared_mats) {
     release_level_vectors(h->lv);
@@ -1867,6 +1993,7 @@ void nsamg_default_params(nsamg_params* p) {
   p->t_exact = 0;
   p->use_graph = 1;
   p->spmv_group = 0;
+  p->fuse_tail = 0;
 }
 
 int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, void* cuda_stream, nsamg_handle** out) {

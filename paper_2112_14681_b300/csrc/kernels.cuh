@@ -7,6 +7,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 
 namespace nsamg {
 
@@ -73,6 +74,7 @@ struct RowOp {
   VRef<TY> out;
   int neg = 0;
   const int* skip = nullptr;  // if set and *skip != 0 the launch does nothing (stopped solve)
+  int src_n = 0;              // length of the source vector (columns of the matrix)
 };
 
 template <typename TM, typename TX, typename TY>
@@ -205,6 +207,101 @@ __global__ void k_dense_gemv(int n, const TC* __restrict__ C, VRef<const T> bref
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) zref.get()[warp] = acc;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused V-cycle tail: every pass of the V-cycle below a level whose vectors fit in shared memory
+// (pre-smoothing with all its Neumann terms, residual, restriction, the coarse solve,
+// prolongation, post-smoothing) run by ONE thread-block cluster. A cluster barrier separates
+// dependent passes; each CTA stages the pass's source vector in its shared memory and gathers
+// from there. Rows of a pass are split over the cluster's CTAs, G lanes per row, with the
+// accumulation order, shuffle reduction and compile-time epilogue of k_row and k_dense_gemv, so
+// the result equals the unfused launches bit for bit.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct TailPass {
+  RowOp<T, T, T> op;
+  int G = 1;       // threads per row (the standalone launch's choice)
+  int epi = 0;     // epilogue code
+  int dense = 0;   // 1: out = C src, C dense src_n x src_n row-major (coarse solve)
+  const T* C = nullptr;
+};
+
+constexpr int kTailThreads = 1024;
+constexpr int kTailStage = 8192;  // longest staged source vector (elements)
+
+template <int EPI, typename T>
+__device__ __forceinline__ void tail_row_pass(const RowOp<T, T, T>& op, int G, const T* __restrict__ xs, int r0, int r1) {
+  const int64_t t_end = (int64_t)r1 * G;
+  for (int64_t t = (int64_t)r0 * G + threadIdx.x; t < t_end; t += blockDim.x) {
+    const int row = (int)(t / G);
+    T acc = T(0);
+    if (op.v) {
+      const int lane = (int)(t & (G - 1));
+      const int b = __ldg(op.rp + row), e = __ldg(op.rp + row + 1);
+#pragma unroll 4
+      for (int p = b + lane; p < e; p += G) {
+        const int c = __ldg(op.ci + p);
+        acc = fma((T)__ldg(op.v + p), xs[c], acc);
+      }
+      if (G > 1) {
+        const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(seg, acc, o, G);
+      }
+      if (lane != 0) continue;
+    }
+    row_epilogue<EPI>(op, row, acc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const TailPass<T>* __restrict__ passes, int np, const int* skip) {
+  pdl_enter();
+  if (skip && *skip) return;  // same value in every CTA: the whole cluster leaves
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  T* sx = reinterpret_cast<T*>(tail_smem);
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const int rank = (int)cl.block_rank(), ncl = (int)cl.num_blocks();
+  for (int q = 0; q < np; ++q) {
+    const TailPass<T>& P = passes[q];
+    const RowOp<T, T, T>& op = P.op;
+    const T* src = op.src.p;
+    const T* xs = src;
+    if (src && op.src_n > 0 && op.src_n <= kTailStage) {
+      for (int k = threadIdx.x; k < op.src_n; k += blockDim.x) sx[k] = src[k];
+      __syncthreads();
+      xs = sx;
+    }
+    if (P.dense) {
+      const int n = op.n;
+      const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+      for (int row = rank * wpb + (threadIdx.x >> 5); row < n; row += ncl * wpb) {
+        T acc = T(0);
+        for (int j = lane; j < n; j += 32) acc = fma(P.C[(int64_t)row * n + j], xs[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) op.out.p[row] = acc;
+      }
+    } else {
+      const int chunk = (op.n + ncl - 1) / ncl;
+      const int r0 = min(op.n, rank * chunk), r1 = min(op.n, r0 + chunk);
+      const int G = op.v ? P.G : 1;
+      switch (P.epi) {
+        case 0: tail_row_pass<0>(op, G, xs, r0, r1); break;
+        case 2: tail_row_pass<2>(op, G, xs, r0, r1); break;
+        case 3: tail_row_pass<3>(op, G, xs, r0, r1); break;
+        case 6: tail_row_pass<6>(op, G, xs, r0, r1); break;
+        case 7: tail_row_pass<7>(op, G, xs, r0, r1); break;
+        case 11: tail_row_pass<11>(op, G, xs, r0, r1); break;
+        case 16: tail_row_pass<16>(op, G, xs, r0, r1); break;
+        case 18: tail_row_pass<18>(op, G, xs, r0, r1); break;
+        case 19: tail_row_pass<19>(op, G, xs, r0, r1); break;
+        case 27: tail_row_pass<27>(op, G, xs, r0, r1); break;
+        default: tail_row_pass<E_RUNTIME>(op, G, xs, r0, r1); break;
+      }
+    }
+    cl.sync();  // outputs visible to the whole cluster; shared staging free for the next pass
+  }
 }
 
 // ------------------------------------------------------------------------------------------

@@ -511,3 +511,39 @@ def test_solve_with_gpu_computed_ilu0_factors():
         s1 = nsamg.solve(h1, dev(b), x1, rtol=1e-8)
         s2 = nsamg.solve(h2, dev(b), x2, rtol=1e-8)
     assert s2["converged"] and abs(s1["iters"] - s2["iters"]) <= 1
+
+
+@pytest.mark.parametrize("name", ["c1", "p23", "p20s", "p30"])
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.JACOBI_L1, K.ILU0, K.HYBRID_ILU0])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_fused_tail_equals_separate_launches(name, smoother, fp32):
+    """The V-cycle below the first level with <= 8192 rows run as one cluster kernel gives bitwise
+    the same z = M^-1 r as one launch per pass, with fewer launches per Arnoldi step. The layouts
+    are fixed (spmv_group = -1) so that the timed autotuner cannot pick different kernels for the
+    two handles."""
+    A, H = case(name)
+    r = np.random.default_rng(7).uniform(-1, 1, A.shape[0])
+    outs, launches = [], []
+    for fuse in (0, 1):
+        p = nsamg.default_params(**params_for(smoother, vcycle_fp32=fp32, fuse_tail=fuse, spmv_group=-1))
+        with nsamg.setup_hierarchy(H, p) as h:
+            z = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            nsamg.apply_vcycle(h, dev(r), z)
+            outs.append(host(z))
+            launches.append(nsamg.launches_per_step(h))
+    assert np.array_equal(outs[0], outs[1])
+    assert launches[1] < launches[0]
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_fused_tail_solve_is_bitwise_unchanged(fp32):
+    A, H = case("p23")
+    b = rhs_uniform(A.shape[0], 4)
+    res = []
+    for fuse in (0, 1):
+        p = nsamg.default_params(smoother=nsamg.HYBRID_ILU0, vcycle_fp32=fp32, fuse_tail=fuse, spmv_group=-1)
+        with nsamg.setup_hierarchy(H, p) as h:
+            x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=300)
+            res.append((st["iters"], host(x)))
+    assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
