@@ -265,7 +265,11 @@ def time_kernels(nsamg, torch, h, A, H, stream, reps=20):
         return e0.elapsed_time(e1) / reps * 1e-3
 
     t = timed(lambda: nsamg.level_spmv(h, 0, x, y))
-    out["spmv_l0"] = {"s": t, "bytes": spmv_bytes(A), "GBps": spmv_bytes(A) / t / 1e9}
+    g0 = nsamg.level_group(h, 0)  # layout the autotuner chose: 0 = SELL-32-sigma, else CSR threads per row
+    out["spmv_l0"] = {"s": t, "bytes": spmv_bytes(A), "GBps": spmv_bytes(A) / t / 1e9,
+                      "layout": "sell" if g0 == 0 else f"csr{g0}",
+                      "kernel": "k_sell<0, K, double, double, double> (SELL-32-sigma)" if g0 == 0
+                      else f"k_row<{g0}, 0, double, double, double> (CSR, {g0} threads per row)"}
     # ILU pass on the finest level: y_{j+1} = r - L_s y_j (strict lower factor)
     Ls = H.levels[0].ilu_L
     if Ls is not None:
@@ -403,9 +407,9 @@ def run_gpu(args):
                        "max_relres_true": main_r["max_relres_true"], "all_converged": main_r["all_converged"],
                        "smoothers": {k: {kk: v[kk] for kk in ("s_per_solve", "solves_per_s", "iters", "max_relres_true",
                                                              "all_converged")} for k, v in results.items()}},
-            "roofline": {"kernel": "k_row<1,double,double,double> level-0 SpMV y = A x", "bound": "hbm",
+            "roofline": {"kernel": sp["kernel"] + ", level-0 SpMV y = A x (autotuned layout)", "bound": "hbm",
                          "achieved": sp["GBps"], "peak": peak, "unit": "GB/s", "frac": sp["GBps"] / peak,
-                         "peak_kind": peak_kind, "traffic": measured_traffic("spmv_l0"),
+                         "peak_kind": peak_kind, "traffic": measured_traffic("spmv_l0_" + sp["layout"]),
                          "algorithmic_bytes": sp["bytes"], "launch_s": sp["s"]},
             "kernels": {k: {kk: (round(vv, 9) if isinstance(vv, float) else vv) for kk, vv in v.items()} for k, v in kern.items()},
             "clocks": main_r["clocks"],
@@ -666,8 +670,9 @@ def run_profile(args):
 
 
 def run_profile_kernel(args):
-    """Launch one hot kernel 3 times on the full-size finest level (no autotuning, no graph, no
-    other launches before it), for a detailed ncu capture."""
+    """Launch one hot kernel 3 times on the full-size finest level (no graph, no other launches
+    before it), for a detailed ncu capture. The finest-level layout is autotuned as in the bench
+    ("spmv"), or forced: CSR with one thread per row ("spmvcsr") or SELL-32-sigma ("spmvsell")."""
     import torch
     from paper_2112_14681_b300 import nsamg
     nsamg.load()
@@ -675,14 +680,15 @@ def run_profile_kernel(args):
     n = A.shape[0]
     fp32 = args.profile_kernel.endswith("32")
     kind = args.profile_kernel[:-2] if fp32 else args.profile_kernel
-    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=0, vcycle_fp32=int(fp32),
+    group = {"spmvcsr": 1, "spmvsell": -1}.get(kind, 0)
+    p = nsamg.default_params(restart=RESTART, use_graph=0, spmv_group=group, vcycle_fp32=int(fp32),
                              **{k: v for k, v in SMOOTHERS["hybrid_ilu0"].items() if k != "vcycle_fp32"})
     h = nsamg.setup_hierarchy(H, p)
     x = torch.from_numpy(rhs[0]).cuda()
     y = torch.empty_like(x)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("profile_kernel")
-    if kind == "spmv":
+    if kind.startswith("spmv"):
         for _ in range(3):
             nsamg.level_spmv(h, 0, x, y)
     elif kind == "l1spmv":
@@ -776,7 +782,8 @@ def main():
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
     ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
     ap.add_argument("--c3-edge", type=int, default=C3_EDGE)
-    ap.add_argument("--profile-kernel", choices=["spmv", "l1spmv", "ilu", "gram", "update", "spmv32", "ilu32"],
+    ap.add_argument("--profile-kernel", choices=["spmv", "spmvcsr", "spmvsell", "l1spmv", "ilu", "gram", "update",
+                                                 "spmv32", "ilu32"],
                     help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":
