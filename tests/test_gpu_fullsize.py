@@ -181,3 +181,37 @@ def test_fullsize_c3_graded_27pt_fp32_vcycle():
         rel = np.linalg.norm(K.residual(A, b, xs[fp32])) / np.linalg.norm(b)
         assert st["converged"] == 1 and rel <= RTOL
     assert np.linalg.norm(xs[1] - xs[0]) / np.linalg.norm(xs[0]) <= 1e-6
+
+
+def test_fullsize_c4_batched_256_systems():
+    """The benchmark's batched workload as it times it: 256 seeded 7-point systems with edges drawn
+    from 16..64, 4-level hierarchies, one nsamg_batch_solve, GMRES(30), FP32 and FP64 V-cycles.
+    Every system's true residual is recomputed with the oracle's SpMV; three systems (smallest,
+    largest, one in between) are solved by the oracle's one-reduce GMRES and compared (x within
+    1e-6, iteration counts within 1 for the FP64 batch)."""
+    import bench
+    systems, _ = bench.build_pools(bench.BATCH_COUNT, 0)
+    assert len(systems) == 256
+    b = np.concatenate([bb for _, _, bb in systems])
+    sizes = np.array([A.shape[0] for A, _, _ in systems])
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.argsort(sizes)[128])]
+    xs, stats = {}, {}
+    for fp32 in (1, 0):
+        p = nsamg.default_params(restart=bench.BATCH_RESTART, vcycle_fp32=fp32)
+        with nsamg.batch_setup([H for _, H, _ in systems], p) as h:
+            off = h.offsets
+            x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+            stats[fp32] = nsamg.batch_solve(h, dev(b), x, RTOL, bench.MAXIT)
+            xs[fp32] = host(x)
+        for k, (A, H, bb) in enumerate(systems):
+            xk = xs[fp32][off[k]:off[k + 1]]
+            assert stats[fp32][k]["converged"] == 1
+            assert np.linalg.norm(K.residual(A, bb, xk)) / np.linalg.norm(bb) <= RTOL, k
+    op = K.SmootherParams()  # the batch's default solve parameters: poly-GS, 2 terms, 1 + 1 sweeps
+    for k in pick:
+        A, H, bb = systems[k]
+        ref = gmres_onereduce(A, bb, lambda v: ovcycle(H, v, op), m=bench.BATCH_RESTART, rtol=RTOL)
+        for fp32 in (1, 0):
+            xk = xs[fp32][off[k]:off[k + 1]]
+            assert np.linalg.norm(xk - ref.x) / np.linalg.norm(ref.x) <= 1e-6, (k, fp32)
+        assert abs(stats[0][k]["iters"] - ref.iters) <= 1
