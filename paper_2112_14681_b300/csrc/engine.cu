@@ -103,6 +103,7 @@ struct DCSR {
 };
 
 constexpr int kSellMinRows = 16384;
+constexpr double kPlainPad = 1.03;  // natural-order chunk padding accepted for the plain layout
 constexpr int kSellSigma = 4096;  // rows sorted by length inside windows of this many rows
 
 struct HostCSR {  // host copy used while building derived matrices
@@ -162,7 +163,51 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
       CK(cudaMemcpy(d.v, tmp.data(), sizeof(T) * nnz, cudaMemcpyHostToDevice));
     }
   }
+  // Near-uniform rows (natural-order chunks padded by at most kPlainPad): the plain layout, rows
+  // in their own order, each padded to its chunk's width with zero values (column = the row's last
+  // column, or the row itself when empty), so no permutation or row lengths are stored or read.
+  bool plain = false;
   if (n >= kSellMinRows && nnz > 0) {
+    int64_t slots = 0;
+    for (int c = 0; c * 32 < n; ++c) {
+      int w = 0;
+      for (int i = c * 32; i < std::min(n, c * 32 + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
+      slots += 32 * (int64_t)w;
+    }
+    plain = (double)slots <= kPlainPad * (double)nnz;
+  }
+  if (plain) {
+    const int nch = (n + 31) / 32;
+    std::vector<int64_t> cptr(nch + 1, 0);
+    for (int c = 0; c < nch; ++c) {
+      int w = 0;
+      for (int i = c * 32; i < std::min(n, c * 32 + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
+      cptr[c + 1] = cptr[c] + 32 * (int64_t)w;
+    }
+    std::vector<int> scol(std::max<int64_t>(cptr[nch], 1), 0);
+    std::vector<T> sval(std::max<int64_t>(cptr[nch], 1), T(0));
+    for (int c = 0; c < nch; ++c) {
+      const int w = (int)((cptr[c + 1] - cptr[c]) / 32);
+      for (int l = 0; l < 32; ++l) {
+        const int row = c * 32 + l;
+        const int len = row < n ? rp[row + 1] - rp[row] : 0;
+        const int pad_col = len > 0 ? ci[rp[row] + len - 1] : std::min(row, m - 1);
+        for (int j = 0; j < w; ++j) {
+          const int64_t q = cptr[c] + (int64_t)j * 32 + l;
+          scol[q] = j < len ? ci[rp[row] + j] : pad_col;
+          sval[q] = j < len ? (T)v[rp[row] + j] : T(0);
+        }
+      }
+    }
+    d.nchunks = nch;
+    d.sell_k = 1;
+    CK(cudaMalloc(&d.s_cptr, sizeof(int64_t) * cptr.size()));
+    CK(cudaMemcpy(d.s_cptr, cptr.data(), sizeof(int64_t) * cptr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_col, sizeof(int) * scol.size()));
+    CK(cudaMemcpy(d.s_col, scol.data(), sizeof(int) * scol.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d.s_val, sizeof(T) * sval.size()));
+    CK(cudaMemcpy(d.s_val, sval.data(), sizeof(T) * sval.size(), cudaMemcpyHostToDevice));
+  } else if (n >= kSellMinRows && nnz > 0) {
     // SELL-32-sigma: sort rows by length (descending, stable) inside windows of sigma rows, cut
     // into chunks of 32 positions, store each chunk column-major.
     const int nch = (n + 31) / 32;
@@ -311,7 +356,10 @@ void launch_csr(const RowOp<TM, TX, TY>& op, int nb, cudaStream_t s) {
 template <int EPI, int K, typename TM, typename TX, typename TY>
 void launch_sell_one(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   const int nb = blocks_for((int64_t)((op.sell.nchunks + K - 1) / K) * 32);
-  launch_k(k_sell<EPI, K, TM, TX, TY>, nb, kThreads, s, op);
+  if (op.sell.perm)
+    launch_k(k_sell<EPI, K, false, TM, TX, TY>, nb, kThreads, s, op);
+  else
+    launch_k(k_sell<EPI, K, true, TM, TX, TY>, nb, kThreads, s, op);
 }
 
 template <int K, typename TM, typename TX, typename TY>

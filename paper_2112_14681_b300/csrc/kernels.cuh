@@ -51,8 +51,11 @@ enum : int { E_NEG = 1, E_BASE = 2, E_BSCALE = 4, E_SCALE = 8, E_ADD = 16, E_RUN
 template <typename TM>
 struct SellView {
   int nchunks = 0;
-  const int* perm = nullptr;      // position -> row (-1 for padding lanes), nchunks * 32
-  const int* rlen = nullptr;      // entries of the row at each position (0 for padding)
+  // Sorted layout: position -> row (-1 for padding lanes) and the row's entries at each
+  // position. Both null for the plain layout of near-uniform matrices: rows in natural order
+  // (chunk c holds rows 32c..32c+31), every row padded to its chunk's width with zero values.
+  const int* perm = nullptr;
+  const int* rlen = nullptr;
   const int64_t* cptr = nullptr;  // chunk offsets, nchunks + 1
   const int* col = nullptr;
   const TM* val = nullptr;
@@ -133,7 +136,9 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
 
 // K chunks per warp: the K chunks' loads are interleaved in one loop so that each thread keeps
 // K independent gather chains in flight (rows of 2-7 entries are otherwise latency bound).
-template <int EPI, int K, typename TM, typename TX, typename TY>
+// PLAIN: natural row order, chunk width from cptr, no permutation or length reads (the padding
+// entries hold zero values, so they add exact zeros).
+template <int EPI, int K, bool PLAIN, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
   pdl_enter();
   if (op.skip && *op.skip) return;
@@ -151,9 +156,16 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
       const int c = c0 + k;
       const bool ok = c < op.sell.nchunks;
       const int pos = c * 32 + lane;
-      row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
-      len[k] = ok ? __ldg(op.sell.rlen + pos) : 0;
-      off[k] = ok ? __ldg(op.sell.cptr + c) + lane : 0;
+      if constexpr (PLAIN) {
+        const int64_t c_b = ok ? __ldg(op.sell.cptr + c) : 0;
+        row[k] = (ok && pos < op.n) ? pos : -1;
+        len[k] = ok ? (int)((__ldg(op.sell.cptr + c + 1) - c_b) >> 5) : 0;
+        off[k] = c_b + lane;
+      } else {
+        row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
+        len[k] = ok ? __ldg(op.sell.rlen + pos) : 0;
+        off[k] = ok ? __ldg(op.sell.cptr + c) + lane : 0;
+      }
       acc[k] = TY(0);
       jmax = max(jmax, len[k]);
     }
