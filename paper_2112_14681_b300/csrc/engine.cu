@@ -860,16 +860,34 @@ void vcycle(nsamg_handle* h, std::vector<Level<T>>& lv, int l, VC<T> b, VRef<T> 
 // ------------------------------------------------------------------------------------------
 // Autotuning of threads-per-row for large CSR matrices (timed SpMV with each group size).
 // ------------------------------------------------------------------------------------------
+// Read sweep over a buffer larger than L2 (no writes: it leaves no dirty lines behind).
+__global__ void k_l2_sweep(const double* __restrict__ buf, int64_t n, double* __restrict__ sink) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += buf[i];
+  if (acc == -1.0) *sink = acc;  // never true for the zero buffer; keeps the loads
+}
+
+struct TuneScratch {
+  double* buf = nullptr;
+  int64_t n = 0;
+  double* sink = nullptr;
+  int blocks = 592;
+};
+
+// One launch timed after L2 has been swept, as in a V-cycle where the other passes have evicted
+// the matrix (a matrix smaller than L2 would otherwise be timed from cache); best of five.
 template <typename T>
-float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                const TuneScratch& fl) {
   auto op = op_mat(M, cref((const T*)x));
   op.out = vref(y);
   launch_row(op, G, s);
-  launch_row(op, G, s);
   float best = 1e30f;
-  for (int round = 0; round < 3; ++round) {
+  for (int round = 0; round < 5; ++round) {
+    if (fl.buf) k_l2_sweep<<<fl.blocks, 256, 0, s>>>(fl.buf, fl.n, fl.sink);
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 4; ++r) launch_row(op, G, s);
+    launch_row(op, G, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -880,9 +898,9 @@ float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, c
 }
 
 // Timed choice among CSR with G = 1, 2, ..., 32 threads per row and SELL-32-sigma with 1, 2 or
-// 4 chunks per warp (best of three rounds of four launches each, after two untimed launches).
+// 4 chunks per warp (best of five single launches, each after an L2 sweep).
 template <typename T>
-int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
+int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s, const TuneScratch& fl) {
   if (M.n < 20000 || M.nnz == 0) return NSAMG_OK;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -894,7 +912,7 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
   M.use_sell = false;
   for (int G : cands) {
     if (G > 2 * avg + 2) break;
-    const float ms = time_spmv(M, x, y, G, s, e0, e1);
+    const float ms = time_spmv(M, x, y, G, s, e0, e1, fl);
     if (ms < best) {
       best = ms;
       bestG = G;
@@ -904,7 +922,7 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s) {
     for (int K : {1, 2, 4}) {
       M.use_sell = true;
       M.sell_k = K;
-      const float ms = time_spmv(M, x, y, 1, s, e0, e1);
+      const float ms = time_spmv(M, x, y, 1, s, e0, e1, fl);
       if (ms < best) {
         best = ms;
         bestK = K;
@@ -1294,7 +1312,28 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
 template <typename T>
 int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaStream_t s) {
   int rc;
-  if (group == 0 && !lvs.empty() && lvs[0].A.n >= 20000) tune_warmup(lvs[0].A, big_x, big_y, s);
+  const bool timed = group == 0 && !lvs.empty() && lvs[0].A.n >= 20000;
+  if (timed) tune_warmup(lvs[0].A, big_x, big_y, s);
+  // L2 sweep buffer (twice the L2 size) for the timed candidates; freed on return
+  TuneScratch fl;
+  struct FreeScratch {
+    TuneScratch& f;
+    ~FreeScratch() {
+      cudaFree(f.buf);
+      cudaFree(f.sink);
+    }
+  } free_scratch{fl};
+  if (timed) {
+    int dev = 0, l2 = 0, sms = 148;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    fl.n = std::max<int64_t>(2 * (int64_t)l2 / (int64_t)sizeof(double), 1 << 20);
+    fl.blocks = 4 * sms;
+    CK(cudaMalloc(&fl.buf, sizeof(double) * fl.n));
+    CK(cudaMemsetAsync(fl.buf, 0, sizeof(double) * fl.n, s));
+    CK(cudaMalloc(&fl.sink, sizeof(double)));
+  }
   for (auto& L : lvs) {
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
     for (DCSR<T>* M : mats) {
@@ -1311,7 +1350,7 @@ int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaS
       T* y = (M->n <= L.n && L.t2) ? L.t2 : big_y;
       if (M == &L.R) { x = L.t1; y = big_y; }
       if (M == &L.P) { x = big_x; y = L.t2; }
-      if ((rc = tune(*M, x, y, s))) return rc;
+      if ((rc = tune(*M, x, y, s, fl))) return rc;
     }
   }
   return NSAMG_OK;
