@@ -135,7 +135,8 @@ int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, 
  * Blocks until the solve finishes. Returns OK, NOT_CONVERGED, or an error. st may be NULL. */
 int nsamg_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* st);
 
-/* Same as nsamg_solve with HOST arrays: copies b and x0 to the device, solves, copies x back. */
+/* Same as nsamg_solve with HOST arrays: copies b and x0 to the device, solves, copies x back
+ * (in stream order after the solve; on an error return h_x holds the last iterate). */
 int nsamg_solve_host(nsamg_handle* h, const double* h_b, double* h_x, double rtol, int maxit, nsamg_stats* st);
 
 /* z = M^-1 r: one V-cycle with zero initial guess (Sec. 5). d_r, d_z: device float64, n entries.

@@ -1930,7 +1930,10 @@ int noalloc_scratch(Scratch* out, int* blocks) {
   return NSAMG_OK;
 }
 
-int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats) {
+// h_out (optional): host buffer that receives x, copied in stream order right after the solve,
+// before the state read-back, so the host waits once.
+int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int maxit, nsamg_stats* stats,
+               double* h_out = nullptr) {
   if (!h || !d_b || !d_x) return fail(NSAMG_ERR_INVALID_ARG, "null argument");
   if (h->batch) return fail(NSAMG_ERR_INVALID_ARG, "batch handle: use nsamg_batch_solve");
   if (!(rtol > 0.0) || maxit < 0) return fail(NSAMG_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
@@ -1963,6 +1966,7 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
     }
     enqueue_sknorm(h, s);
   }
+  if (h_out) CK(cudaMemcpyAsync(h_out, d_x, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(hs, h->st, sizeof(GState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -2111,10 +2115,8 @@ int nsamg_solve_host(nsamg_handle* h, const double* h_b, double* h_x, double rto
   CK(cudaMallocAsync(&dx, bytes, h->stream));
   CK(cudaMemcpyAsync(db, h_b, bytes, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(dx, h_x, bytes, cudaMemcpyHostToDevice, h->stream));
-  int rc = solve_impl(h, db, dx, rtol, maxit, st);
-  if (rc >= 0) {
-    CK(cudaMemcpyAsync(h_x, dx, bytes, cudaMemcpyDeviceToHost, h->stream));
-  }
+  // x comes back in the same stream pass as the solve state (one host wait)
+  int rc = solve_impl(h, db, dx, rtol, maxit, st, h_x);
   cudaFreeAsync(db, h->stream);
   cudaFreeAsync(dx, h->stream);
   CK(cudaStreamSynchronize(h->stream));
