@@ -545,3 +545,21 @@ def test_planted_mistake_is_caught(modname, old, new, pin):
             x = ns["ilu0_sweep"](Ls, Us, dinv, tridiag(3), np.ones(3), np.zeros(3), int(tl), int(tu))
             bad += not np.allclose(x, np.array(vals, float), atol=1e-15)
         assert bad > 0
+
+
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0])
+def test_truncated_smoothers_converge_like_exact_triangular_solves(smoother):
+    """Sec. 5.2-5.3 and the conclusions: replacing the triangular solves by a few Neumann terms
+    (2-term polynomial GS; 3 + 3 Jacobi terms for ILU(0)) leaves the GMRES iteration count within
+    one of the smoother with exact forward/backward substitution ("direct" mode)."""
+    for A, kw in ((poisson2d_5pt(32), dict(max_levels=3, coarse_max=64)),
+                  (pressure3d_7pt(20, seed=2), dict(coarse_max=200))):
+        H = build_hierarchy(A, ilu_levels=(0,), **kw)
+        b = rhs_uniform(A.shape[0], 0)
+        its = {}
+        for mode in ("definition", "direct"):
+            p = K.SmootherParams(smoother=smoother, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3, mode=mode)
+            r = gmres_mgs(A, b, lambda v, p=p: vcycle(H, v, p), m=30, rtol=1e-8)
+            assert r.converged
+            its[mode] = r.iters
+        assert abs(its["definition"] - its["direct"]) <= 1, its
