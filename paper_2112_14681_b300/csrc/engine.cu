@@ -496,6 +496,7 @@ struct nsamg_handle {
   double* V = nullptr;  // (m+1) columns
   double* Z = nullptr;  // m columns (FP64 V-cycle)
   float* Z32 = nullptr; // m columns (FP32 V-cycle)
+  double* z64 = nullptr;  // FP32 V-cycle: z_i widened to FP64 for the outer product
   double* w = nullptr;
   GState* st = nullptr;
   GState* h_st = nullptr;  // pinned host mirror
@@ -984,7 +985,8 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
     run(op, h->lv[0].A.G, c);
   } else {
     // FP32 V-cycle: vt_i rounded to FP32 (round to nearest), z_i kept in FP32 (flexible GMRES
-    // stores Z), outer product w = A z_i with the FP64 matrix.
+    // stores Z), outer product w = A z_i with the FP64 matrix on z_i widened once to FP64 (exact;
+    // widening inside the SpMV would cost one FP64-pipe conversion per stored entry).
     Level<float>& L0 = h->lv32[0];
     ++g_launches;
     launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), skip);
@@ -993,13 +995,12 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
     z.sel = sel;
     z.ld = h->ld;
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
+    ++g_launches;
+    launch_k(k_cast<float, double>, 8 * 148, kThreads, s, h->n, cref(z), vref(h->z64), skip);
     const auto& A = h->lv[0].A;
-    RowOp<double, float, double> op;
-    set_matrix(op, A);
-    op.src = cref(z);
+    auto op = op_mat(A, cref((const double*)h->z64));
     op.out = vref(h->w);
-    op.skip = skip;
-    launch_row(op, A.G, s);
+    run(op, A.G, c);
   }
   GramArgs ga{};
   ga.n = h->n;
@@ -1177,12 +1178,12 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     z.sel = sel;
     z.ld = h->ld;
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
+    ++g_launches;
+    launch_k(k_cast<float, double>, 8 * 148, kThreads, s, h->n, cref(z), vref(h->z64), (const int*)nullptr);
     const auto& A = h->lv[0].A;
-    RowOp<double, float, double> op;
-    set_matrix(op, A);
-    op.src = cref(z);
+    auto op = op_mat(A, cref((const double*)h->z64));
     op.out = vref(h->w);
-    launch_row(op, A.G, s);
+    run(op, A.G, c);
   }
   g_launches += 2;
   launch_k(k_bgram, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
@@ -1386,6 +1387,7 @@ int alloc_workspace(nsamg_handle* h) {
   if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
   if (h->fp32) {
     if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
+    if ((rc = alloc_vec(&h->z64, h->ld))) return rc;
   } else {
     if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
   }
@@ -1404,7 +1406,7 @@ int alloc_workspace(nsamg_handle* h) {
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
   h->ctx_bytes = sizeof(double) * h->ld * (h->m + 2) + (h->fp32 ? sizeof(float) : sizeof(double)) * h->ld * h->m +
-                 sizeof(GState) + sizeof(double) * h->partial_cap;
+                 (h->fp32 ? sizeof(double) * h->ld : 0) + sizeof(GState) + sizeof(double) * h->partial_cap;
   return NSAMG_OK;
 }
 
@@ -1849,6 +1851,7 @@ void destroy_impl(nsamg_handle* h) {
   cudaFree(h->V);
   cudaFree(h->Z);
   cudaFree(h->Z32);
+  cudaFree(h->z64);
   cudaFree(h->w);
   cudaFree(h->st);
   if (h->h_st) cudaFreeHost(h->h_st);
