@@ -188,14 +188,49 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
 // ------------------------------------------------------------------------------------------
 // Small helpers
 // ------------------------------------------------------------------------------------------
+// Four consecutive elements per load/store when both vectors start 16-byte aligned (library
+// vectors and basis columns are 256-byte aligned); caller arrays that are not take the scalar loop.
+template <typename T>
+struct Quad;
+template <>
+struct Quad<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+template <>
+struct Quad<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  }
+  __device__ __forceinline__ void store(float* p) const { reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]); }
+};
+
 template <typename TA, typename TB>
 __global__ void k_cast(int64_t n, VRef<const TA> a, VRef<TB> b, const int* skip) {
   pdl_enter();
   if (skip && *skip) return;
   const TA* pa = a.get();
   TB* pb = b.get();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    pb[i] = (TB)pa[i];
+  const bool aligned = ((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15u) == 0;
+  const int64_t n4 = aligned ? n / 4 : 0, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+    Quad<TA> x;
+    x.load(pa + 4 * q);
+    Quad<TB> y;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y.v[k] = (TB)x.v[k];
+    y.store(pb + 4 * q);
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) pb[i] = (TB)pa[i];
 }
 
 template <typename T>

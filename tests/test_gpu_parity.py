@@ -547,3 +547,19 @@ def test_fused_tail_solve_is_bitwise_unchanged(fp32):
             st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=300)
             res.append((st["iters"], host(x)))
     assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
+
+
+def test_fp32_vcycle_on_unaligned_caller_arrays():
+    """The FP64 <-> FP32 casts take four elements per access only when both arrays are 16-byte
+    aligned; caller arrays at an odd element offset give the same z through the scalar path."""
+    A, H = case("p23")
+    n = A.shape[0]
+    r = np.random.default_rng(3).uniform(-1, 1, n)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(vcycle_fp32=1, spmv_group=-1)) as h:
+        z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h, dev(r), z)
+        big_r = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+        big_r[1:] = dev(r)
+        big_z = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h, big_r[1:], big_z[1:])
+        assert np.array_equal(host(z), host(big_z)[1:])
