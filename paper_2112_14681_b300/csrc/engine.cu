@@ -1235,6 +1235,27 @@ int alloc_vec(T** p, int64_t n) {
 // pre-scaled triangles of A for polynomial GS, D^-1, the l1 diagonal, P, R and, where the
 // smoother uses it, the ILU(0) factors. `only_A0` uploads just the finest A (the FP64 operator
 // of an FP32-V-cycle handle).
+// Runs independent host preparation + upload jobs in parallel host threads (each on the caller's
+// device); returns the first failure with its message.
+int run_parallel(std::vector<std::function<int()>>& jobs) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::vector<int> rcs(jobs.size(), NSAMG_OK);
+  std::vector<std::string> errs(jobs.size());
+  std::vector<std::thread> th;
+  th.reserve(jobs.size());
+  for (size_t k = 0; k < jobs.size(); ++k)
+    th.emplace_back([&, k] {
+      cudaSetDevice(dev);
+      rcs[k] = jobs[k]();
+      if (rcs[k] != NSAMG_OK) errs[k] = g_err;
+    });
+  for (auto& t : th) t.join();
+  for (size_t k = 0; k < jobs.size(); ++k)
+    if (rcs[k] != NSAMG_OK) return fail(rcs[k], errs[k]);
+  return NSAMG_OK;
+}
+
 template <typename T>
 int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vector<Level<T>>& lvs, bool only_A0) {
   int rc;
@@ -1244,8 +1265,7 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
     const nsamg_level_desc& D = H->levels[l];
     Level<T>& L = lvs[l];
     L.n = D.A.nrows;
-    if ((rc = upload(D.A, L.A))) return rc;
-    if (only_A0) return NSAMG_OK;
+    if (only_A0) return upload(D.A, L.A);
     std::vector<double> dinv(L.n), dl1(L.n);
     for (int i = 0; i < L.n; ++i) {
       double a = 0, s1 = 0;
@@ -1258,19 +1278,27 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
     }
     if ((rc = upload_vec(dinv, &L.dinv))) return rc;
     if ((rc = upload_vec(dl1, &L.dl1inv))) return rc;
-    if ((rc = upload(tri_part(D.A, true, &dinv, &dinv), L.L2))) return rc;
-    if ((rc = upload(tri_part(D.A, false, &dinv, &dinv), L.U2))) return rc;
-    if ((rc = upload(tri_part(D.A, true, &dinv, nullptr), L.L1))) return rc;
-    if ((rc = upload(tri_part(D.A, false, &dinv, nullptr), L.U1))) return rc;
+    // the level's matrices are independent: derived copies (scaled triangles), SELL arrays and
+    // uploads run in parallel host threads
+    std::vector<std::function<int()>> jobs;
+    jobs.push_back([&] { return upload(D.A, L.A); });
+    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, &dinv), L.L2); });
+    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, &dinv), L.U2); });
+    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, nullptr), L.L1); });
+    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, nullptr), L.U1); });
     if (l < nl - 1) {
-      if ((rc = upload(D.P, L.P))) return rc;
-      if ((rc = upload(D.R, L.R))) return rc;
+      jobs.push_back([&] { return upload(D.P, L.P); });
+      jobs.push_back([&] { return upload(D.R, L.R); });
     }
     const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
-    if (want_ilu && D.ilu_L.nrows > 0 && l < nl - 1) {
-      if ((rc = upload(D.ilu_L, L.iL))) return rc;
+    const bool ilu_here = want_ilu && D.ilu_L.nrows > 0 && l < nl - 1;
+    if (ilu_here) {
+      jobs.push_back([&] { return upload(D.ilu_L, L.iL); });
+      if (D.ilu_form == 0) jobs.push_back([&] { return upload(D.ilu_U, L.iU); });
+    }
+    if ((rc = run_parallel(jobs))) return rc;
+    if (ilu_here) {
       if (D.ilu_form == 0) {
-        if ((rc = upload(D.ilu_U, L.iU))) return rc;
         std::vector<double> idv(D.ilu_dinv, D.ilu_dinv + L.n);
         if ((rc = upload_vec(idv, &L.idinv))) return rc;
       } else {
@@ -1519,28 +1547,53 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     h->own_stream = true;
   }
   const int nl = H->nlevels;
+  // NSAMG_SETUP_TIMING=1: phase times on stderr
+  static const bool timing = [] {
+    const char* e = std::getenv("NSAMG_SETUP_TIMING");
+    return e && e[0] == '1';
+  }();
+  auto t_last = std::chrono::steady_clock::now();
+  auto stamp = [&](const char* what) {
+    if (!timing) return;
+    cudaDeviceSynchronize();
+    const auto t = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "nsamg setup %-18s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(t - t_last).count());
+    t_last = t;
+  };
   for (int l = 0; l < nl; ++l) {
     const nsamg_level_desc& D = H->levels[l];
     std::string nm = "level " + std::to_string(l);
-    if ((rc = validate(D.A, true, true, (nm + " A").c_str()))) return rc;
-    if (l < nl - 1) {
-      if ((rc = validate(D.P, false, false, (nm + " P").c_str()))) return rc;
-      if ((rc = validate(D.R, false, false, (nm + " R").c_str()))) return rc;
-      if (D.P.nrows != D.A.nrows || D.R.ncols != D.A.nrows || D.P.ncols != H->levels[l + 1].A.nrows ||
-          D.R.nrows != H->levels[l + 1].A.nrows)
-        return fail(NSAMG_ERR_BAD_MATRIX, nm + ": P/R dimensions do not match the levels");
-    }
+    if (l < nl - 1 && (D.P.nrows != D.A.nrows || D.R.ncols != D.A.nrows || D.P.ncols != H->levels[l + 1].A.nrows ||
+                       D.R.nrows != H->levels[l + 1].A.nrows))
+      return fail(NSAMG_ERR_BAD_MATRIX, nm + ": P/R dimensions do not match the levels");
     if (D.ilu_L.nrows > 0) {
-      if ((rc = validate(D.ilu_L, true, false, (nm + " ilu_L").c_str()))) return rc;
-      if ((rc = validate(D.ilu_U, true, false, (nm + " ilu_U").c_str()))) return rc;
       if (D.ilu_form != 0 && D.ilu_form != 1) return fail(NSAMG_ERR_INVALID_ARG, nm + ": ilu_form must be 0 or 1");
       if ((D.ilu_form == 0 && !D.ilu_dinv) || D.ilu_L.nrows != D.A.nrows || D.ilu_U.nrows != D.A.nrows)
         return fail(NSAMG_ERR_BAD_MATRIX, nm + ": ILU factor dimensions");
     }
   }
+  {  // every matrix validated in parallel host threads (first failure in level order reported)
+    std::vector<std::function<int()>> jobs;
+    for (int l = 0; l < nl; ++l) {
+      const nsamg_level_desc& D = H->levels[l];
+      const std::string nm = "level " + std::to_string(l);
+      jobs.push_back([&D, nm] { return validate(D.A, true, true, (nm + " A").c_str()); });
+      if (l < nl - 1) {
+        jobs.push_back([&D, nm] { return validate(D.P, false, false, (nm + " P").c_str()); });
+        jobs.push_back([&D, nm] { return validate(D.R, false, false, (nm + " R").c_str()); });
+      }
+      if (D.ilu_L.nrows > 0) {
+        jobs.push_back([&D, nm] { return validate(D.ilu_L, true, false, (nm + " ilu_L").c_str()); });
+        jobs.push_back([&D, nm] { return validate(D.ilu_U, true, false, (nm + " ilu_U").c_str()); });
+      }
+    }
+    if ((rc = run_parallel(jobs))) return rc;
+  }
+  stamp("validate");
   h->fp32 = p.vcycle_fp32 == 1;
   if ((rc = build_levels<double>(H, p, h->lv, h->fp32))) return rc;
   if (h->fp32 && (rc = build_levels<float>(H, p, h->lv32, false))) return rc;
+  stamp("levels");
   if (H->coarse_inv) {
     h->nc = H->levels[nl - 1].A.nrows;
     const size_t nc2 = (size_t)h->nc * h->nc;
@@ -1554,6 +1607,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     }
   }
   if ((rc = alloc_workspace(h))) return rc;
+  stamp("workspace");
   h->anorm_inf = norm_inf(H->levels[0].A);
   CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
   if (bi && (rc = setup_batch_data(h, *bi))) return rc;
@@ -1564,6 +1618,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, h->stream))) return rc;
   }
   CK(cudaStreamSynchronize(h->stream));
+  stamp("tune");
   if (h->batch) {
     if (p.use_graph) {
       rc = build_graph_fn(
@@ -1587,6 +1642,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
     if ((rc = build_tail_any(h))) return rc;
     if ((rc = finish_graph(h))) return rc;
   }
+  stamp("graph");
   CK(cudaGetLastError());
   return NSAMG_OK;
 }

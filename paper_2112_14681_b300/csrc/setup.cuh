@@ -1131,6 +1131,36 @@ int coarse_inverse(DMem& mem, const GCsr& A, double** inv, cudaStream_t s) {
 
 }  // namespace gsetup
 
+// Page-locked host array (export mirrors: device-to-host copies at full link speed, and the
+// solver setup uploads from it at the same speed).
+template <typename T>
+struct PinnedArray {
+  T* p = nullptr;
+  size_t n = 0;
+  PinnedArray() = default;
+  PinnedArray(const PinnedArray&) = delete;
+  PinnedArray& operator=(const PinnedArray&) = delete;
+  PinnedArray(PinnedArray&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr, o.n = 0; }
+  PinnedArray& operator=(PinnedArray&& o) noexcept {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    return *this;
+  }
+  ~PinnedArray() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t resize(size_t k) {
+    if (k <= n && p) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMallocHost((void**)&p, sizeof(T) * std::max<size_t>(k, 1));
+    if (e == cudaSuccess) n = k;
+    return e;
+  }
+  T* data() const { return p; }
+};
+
 // The hierarchy built on the device, with host mirrors filled on export.
 struct nsamg_amg {
   gsetup::DMem mem;
@@ -1139,16 +1169,16 @@ struct nsamg_amg {
   std::vector<int> pmis_rounds;
   // host mirrors (export)
   struct HostCsr {
-    std::vector<int> rp, ci;
-    std::vector<double> v;
+    PinnedArray<int> rp, ci;
+    PinnedArray<double> v;
     int n = 0, m = 0;
   };
   struct HostLevel {
     HostCsr A, P, R, L, U;
-    std::vector<double> dinv;
+    PinnedArray<double> dinv;
   };
   std::vector<HostLevel> host;
-  std::vector<double> host_cinv;
+  PinnedArray<double> host_cinv;
   std::vector<nsamg_level_desc> descs;
 };
 
@@ -1157,9 +1187,9 @@ namespace gsetup {
 int download_csr(const GCsr& d, nsamg_amg::HostCsr& h, cudaStream_t s) {
   h.n = d.n;
   h.m = d.m;
-  h.rp.assign(d.n + 1, 0);
-  h.ci.resize(std::max<int64_t>(d.nnz, 1));
-  h.v.resize(std::max<int64_t>(d.nnz, 1));
+  CK(h.rp.resize(d.n + 1));
+  CK(h.ci.resize(std::max<int64_t>(d.nnz, 1)));
+  CK(h.v.resize(std::max<int64_t>(d.nnz, 1)));
   if (d.rp) CK(cudaMemcpyAsync(h.rp.data(), d.rp, sizeof(int) * (d.n + 1), cudaMemcpyDeviceToHost, s));
   if (d.nnz) {
     CK(cudaMemcpyAsync(h.ci.data(), d.ci, sizeof(int) * d.nnz, cudaMemcpyDeviceToHost, s));
@@ -1273,7 +1303,8 @@ int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out) {
   if (!g || !out) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_amg_export: null argument");
   cudaStream_t s = 0;
   const int nl = (int)g->levels.size();
-  g->host.assign(nl, {});
+  g->host.clear();
+  g->host.resize(nl);
   g->descs.assign(nl, {});
   for (int l = 0; l < nl; ++l) {
     const auto& L = g->levels[l];
@@ -1285,8 +1316,9 @@ int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out) {
       rc = gsetup::download_csr(L.L, H.L, s);
       if (!rc) rc = gsetup::download_csr(L.U, H.U, s);
       if (!rc) {
-        H.dinv.resize(L.A.n);
-        cudaError_t e = cudaMemcpyAsync(H.dinv.data(), L.dinv, sizeof(double) * L.A.n, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = H.dinv.resize(L.A.n);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(H.dinv.data(), L.dinv, sizeof(double) * L.A.n, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) rc = cuda_fail(e, "nsamg_amg_export");
       }
     }
@@ -1294,7 +1326,7 @@ int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out) {
   }
   if (g->coarse_inv) {
     const int64_t nc = g->levels.back().A.n;
-    g->host_cinv.resize(nc * nc);
+    CK(g->host_cinv.resize(nc * nc));
     CK(cudaMemcpyAsync(g->host_cinv.data(), g->coarse_inv, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost, s));
   }
   CK(cudaStreamSynchronize(s));
