@@ -268,7 +268,7 @@ def time_kernels(nsamg, torch, h, A, H, stream, reps=20):
     g0 = nsamg.level_group(h, 0)  # layout the autotuner chose: 0 = SELL-32-sigma, else CSR threads per row
     out["spmv_l0"] = {"s": t, "bytes": spmv_bytes(A), "GBps": spmv_bytes(A) / t / 1e9,
                       "layout": "sell" if g0 == 0 else f"csr{g0}",
-                      "kernel": "k_sell<0, K, double, double, double> (SELL-32-sigma)" if g0 == 0
+                      "kernel": "k_sell<0, K, P, double, double, double> (SELL-32; P = 1, plain layout, for near-uniform rows)" if g0 == 0
                       else f"k_row<{g0}, 0, double, double, double> (CSR, {g0} threads per row)"}
     # ILU pass on the finest level: y_{j+1} = r - L_s y_j (strict lower factor)
     Ls = H.levels[0].ilu_L
@@ -690,6 +690,27 @@ def run_profile(args):
     h.close()
 
 
+def run_profile_setup(args):
+    """One GPU Ruge-Stuben setup of the 128^3 operator (nsamg_amg_build) inside an NVTX range
+    'setup_build', after one untimed build (for an ncu launch list of the setup kernels)."""
+    import torch
+    from paper_2112_14681_b300 import nsamg
+    from workloads import pressure3d_7pt
+    nsamg.load()
+    A = pressure3d_7pt(EDGE, sigma=1.0, seed=SEED)
+    opt = nsamg.amg_default_options(theta=0.25, coarse_max=512, seed=SEED, ilu_levels=1, ilu_sweeps=3)
+    nsamg.amg_build(A, opt).close()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("setup_build")
+    t0 = time.perf_counter()
+    g = nsamg.amg_build(A, opt)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_setup_s": dt, "levels": [g.level_info(l) for l in range(g.nlevels)]}))
+    g.close()
+
+
 def run_profile_kernel(args):
     """Launch one hot kernel 3 times on the full-size finest level (no graph, no other launches
     before it), for a detailed ncu capture. The finest-level layout is autotuned as in the bench
@@ -799,6 +820,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="skip the 256-system batched comparison")
     ap.add_argument("--skip-serving", action="store_true", help="skip the Poisson-arrival serving comparison")
     ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
+    ap.add_argument("--profile-setup", action="store_true", help="one GPU AMG setup in an NVTX range, for ncu")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
     ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
@@ -813,6 +835,8 @@ def main():
         run_c3(args)
     elif args.profile_kernel:
         run_profile_kernel(args)
+    elif args.profile_setup:
+        run_profile_setup(args)
     elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
