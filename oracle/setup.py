@@ -10,7 +10,7 @@ TEST INFRASTRUCTURE ONLY (see the package header): nothing on the product path i
                   lambda_i = |S^T_i| + u_i, rounds of local maxima over S_i u S^T_i among the
                   undecided points, undecided points that strongly depend on a new C-point
                   become F; then F-points left without a strong C-neighbour are promoted to C in
-                  index order (the reading this build takes where the paper is silent)
+                  index order (a reading: the paper does not say what happens to them)
   bamg_direct     BAMG-direct interpolation with f = 1, closed form of eq. (bamgdir):
                   w_ij = -(a_ij + beta_i / n_{C_i^s}) / (a_ii + sum_{k weak} a_ik),
                   beta_i = sum of the strong F-neighbour couplings
