@@ -215,3 +215,25 @@ def test_fullsize_c4_batched_256_systems():
             xk = xs[fp32][off[k]:off[k + 1]]
             assert np.linalg.norm(xk - ref.x) / np.linalg.norm(ref.x) <= 1e-6, (k, fp32)
         assert abs(stats[0][k]["iters"] - ref.iters) <= 1
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("poly_gs", dict(smoother=nsamg.POLY_GS, neumann_terms=2, pre_sweeps=1, post_sweeps=1)),
+    ("l1_jacobi", dict(smoother=nsamg.JACOBI_L1, pre_sweeps=2, post_sweeps=2)),
+])
+def test_fullsize_other_smoothers_match_oracle(name, kw):
+    """The benchmark's other FP64 smoothers on the 128^3 case: polynomial Gauss-Seidel (2 terms)
+    and l1-Jacobi (2 + 2 sweeps), against the oracle's one-reduce GMRES with the same V-cycle."""
+    s = state()
+    p = nsamg.default_params(restart=RESTART, **kw)
+    op = K.SmootherParams(smoother=p.smoother, neumann_terms=p.neumann_terms, pre_sweeps=p.pre_sweeps,
+                          post_sweeps=p.post_sweeps, coarse_sweeps=p.coarse_sweeps)
+    ref = gmres_onereduce(s["A"], s["b"], lambda v: ovcycle(s["H"], v, op), m=RESTART, rtol=RTOL)
+    with nsamg.setup_hierarchy(s["H"], p) as h:
+        x = torch.zeros(s["A"].shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(s["b"]), x, rtol=RTOL, maxit=500)
+        xs = host(x)
+    true = np.linalg.norm(s["b"] - s["A"] @ xs) / np.linalg.norm(s["b"])
+    assert st["converged"] == 1 and true <= RTOL
+    assert abs(st["iters"] - ref.iters) <= 1, (st["iters"], ref.iters)
+    assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
