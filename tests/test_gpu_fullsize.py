@@ -237,3 +237,25 @@ def test_fullsize_other_smoothers_match_oracle(name, kw):
     assert st["converged"] == 1 and true <= RTOL
     assert abs(st["iters"] - ref.iters) <= 1, (st["iters"], ref.iters)
     assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+
+
+def test_fullsize_hybrid_ilut_matches_oracle():
+    """The benchmark's ILUT(1e-2, 5) line: finest-level ILUT factors with Ruiz-scaled U and 3 + 3
+    Jacobi terms (Algorithm 2), polynomial GS below, against the oracle with the same factors."""
+    import copy
+    from workloads.hierarchy import Hierarchy, ilut
+    s = state()
+    H = s["H"]
+    l0 = copy.copy(H.levels[0])
+    l0.ilu_L, l0.ilu_U, l0.ilu_dr, l0.ilu_dc = ilut(l0.A, 1e-2, 5)
+    l0.ilu_dinv, l0.ilu_form = None, 1
+    Ht = Hierarchy(levels=[l0] + H.levels[1:], coarse_inv=H.coarse_inv, theta=H.theta, seed=H.seed, info=H.info)
+    ref = gmres_onereduce(s["A"], s["b"], lambda v: ovcycle(Ht, v, s["op"]), m=RESTART, rtol=RTOL)
+    with nsamg.setup_hierarchy(Ht, s["p"]) as h:
+        x = torch.zeros(s["A"].shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(s["b"]), x, rtol=RTOL, maxit=500)
+        xs = host(x)
+    true = np.linalg.norm(s["b"] - s["A"] @ xs) / np.linalg.norm(s["b"])
+    assert st["converged"] == 1 and true <= RTOL
+    assert abs(st["iters"] - ref.iters) <= 1, (st["iters"], ref.iters)
+    assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
