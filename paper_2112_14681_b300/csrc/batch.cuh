@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bxupdate(BatchArgs a, const TZ*
   const int64_t r1 = min(a.off[sys + 1], r0 + a.rpb);
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     double acc = x[r];
-    for (int j = 0; j < k; ++j) acc = fma(s_c[j], (double)__ldcs(Z + (int64_t)j * ldz + r), acc);
+    for (int j = 0; j < k; ++j) acc = fma(s_c[j], convert<double>(__ldcs(Z + (int64_t)j * ldz + r)), acc);
     x[r] = acc;
   }
 }

@@ -496,7 +496,6 @@ struct nsamg_handle {
   double* V = nullptr;  // (m+1) columns
   double* Z = nullptr;  // m columns (FP64 V-cycle)
   float* Z32 = nullptr; // m columns (FP32 V-cycle)
-  double* z64 = nullptr;  // FP32 V-cycle: z_i widened to FP64 for the outer product
   double* w = nullptr;
   GState* st = nullptr;
   GState* h_st = nullptr;  // pinned host mirror
@@ -984,23 +983,22 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
     op.out = vref(h->w);
     run(op, h->lv[0].A.G, c);
   } else {
-    // FP32 V-cycle: vt_i rounded to FP32 (round to nearest), z_i kept in FP32 (flexible GMRES
-    // stores Z), outer product w = A z_i with the FP64 matrix on z_i widened once to FP64 (exact;
-    // widening inside the SpMV would cost one FP64-pipe conversion per stored entry).
+    // FP32 V-cycle: vt_i rounded to FP32 (round to nearest; the kernel that produced vt_i wrote
+    // this copy into the level's input), z_i kept in FP32 (flexible GMRES stores Z), outer product
+    // w = A z_i with the FP64 matrix, z widened exactly in registers by integer operations.
     Level<float>& L0 = h->lv32[0];
-    ++g_launches;
-    launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), skip);
     VRef<float> z;
     z.p = h->Z32;
     z.sel = sel;
     z.ld = h->ld;
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
-    ++g_launches;
-    launch_k(k_cast<float, double>, 8 * 148, kThreads, s, h->n, cref(z), vref(h->z64), skip);
     const auto& A = h->lv[0].A;
-    auto op = op_mat(A, cref((const double*)h->z64));
+    RowOp<double, float, double> op;
+    set_matrix(op, A);
+    op.src = cref(z);
     op.out = vref(h->w);
-    run(op, A.G, c);
+    op.skip = skip;
+    launch_row(op, A.G, s);
   }
   GramArgs ga{};
   ga.n = h->n;
@@ -1020,6 +1018,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ua.cond_inner = cond_inner;
   ua.scr = h->scr;
   ua.scr.ticket = h->scr.ticket + 1;
+  ua.v32 = h->fp32 ? h->lv32[0].b : nullptr;
   launch_k(k_update, h->update_blocks, kRedThreads, s, ua);
 }
 
@@ -1037,6 +1036,7 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   ra.ci = A.ci;
   ra.v = A.v;
   ra.r = h->V;
+  ra.r32 = h->fp32 ? h->lv32[0].b : nullptr;
   ra.st = h->st;
   ra.init = init;
   ra.cond_outer = co;
@@ -1178,12 +1178,12 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     z.sel = sel;
     z.ld = h->ld;
     vcycle(h, h->lv32, 0, cref((const float*)L0.b), z, c);
-    ++g_launches;
-    launch_k(k_cast<float, double>, 8 * 148, kThreads, s, h->n, cref(z), vref(h->z64), (const int*)nullptr);
     const auto& A = h->lv[0].A;
-    auto op = op_mat(A, cref((const double*)h->z64));
+    RowOp<double, float, double> op;  // z widened exactly in registers
+    set_matrix(op, A);
+    op.src = cref(z);
     op.out = vref(h->w);
-    run(op, A.G, c);
+    launch_row(op, A.G, s);
   }
   g_launches += 2;
   launch_k(k_bgram, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
@@ -1415,7 +1415,6 @@ int alloc_workspace(nsamg_handle* h) {
   if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
   if (h->fp32) {
     if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
-    if ((rc = alloc_vec(&h->z64, h->ld))) return rc;
   } else {
     if ((rc = alloc_vec(&h->Z, h->ld * h->m))) return rc;
   }
@@ -1434,7 +1433,7 @@ int alloc_workspace(nsamg_handle* h) {
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
   h->ctx_bytes = sizeof(double) * h->ld * (h->m + 2) + (h->fp32 ? sizeof(float) : sizeof(double)) * h->ld * h->m +
-                 (h->fp32 ? sizeof(double) * h->ld : 0) + sizeof(GState) + sizeof(double) * h->partial_cap;
+                 sizeof(GState) + sizeof(double) * h->partial_cap;
   return NSAMG_OK;
 }
 
@@ -1907,7 +1906,6 @@ void destroy_impl(nsamg_handle* h) {
   cudaFree(h->V);
   cudaFree(h->Z);
   cudaFree(h->Z32);
-  cudaFree(h->z64);
   cudaFree(h->w);
   cudaFree(h->st);
   if (h->h_st) cudaFreeHost(h->h_st);

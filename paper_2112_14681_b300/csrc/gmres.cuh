@@ -249,6 +249,7 @@ struct UpdateArgs {
   const double* h_standalone;
   double* sumsq_out;
   Scratch scr;
+  float* v32;  // if set: FP32 copy of vt_{i+1} (the next V-cycle's input when it runs in FP32)
 };
 
 __global__ void __launch_bounds__(kRedThreads) k_update(UpdateArgs a) {
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(UpdateArgs a) {
 #pragma unroll 8
     for (int j = 0; j < i; ++j) acc = fma(-s_h[j], __ldcs(a.V + (int64_t)j * a.ldv + r), acc);
     vn[r] = acc;
+    if (a.v32) a.v32[r] = narrow_f64(acc);
     ss = fma(acc, acc, ss);
   }
 #pragma unroll
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(int64_t n, const TZ* Z,
   double* x = st->x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     double acc = x[r];
-    for (int j = 0; j < k; ++j) acc = fma(s_c[j], (double)__ldcs(Z + (int64_t)j * ldz + r), acc);
+    for (int j = 0; j < k; ++j) acc = fma(s_c[j], convert<double>(__ldcs(Z + (int64_t)j * ldz + r)), acc);
     x[r] = acc;
   }
 }
@@ -401,6 +403,7 @@ struct ResidArgs {
   const int* ci;
   const double* v;
   double* r;           // V[:, 0]
+  float* r32;          // if set: FP32 copy of r (the first V-cycle input of a cycle in FP32)
   GState* st;
   int init;
   unsigned long long cond_outer, cond_inner;
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(kRedThreads) k_resid(ResidArgs a) {
       const double ri = bi - acc;
       const double xi = x[row];
       a.r[row] = ri;
+      if (a.r32) a.r32[row] = narrow_f64(ri);
       rr = ri * ri;
       bb = bi * bi;
       xx = xi * xi;

@@ -6,6 +6,7 @@
 // all whole-vector reductions into a single deterministic pass with a last-block finalise.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 
@@ -32,6 +33,44 @@ struct VRef {
 
 template <typename T>
 __host__ __device__ inline VRef<T> vref(T* p) { VRef<T> r; r.p = p; return r; }
+
+// IEEE 754 binary32 <-> binary64 conversions with integer operations. On this part the hardware
+// conversion instructions issue on the FP64 pipe at a fraction of the FMA rate, which made the
+// precision casts of the FP32 V-cycle conversion bound; the integer forms run on the integer
+// pipe. Widening is exact for every input; narrowing rounds to nearest, ties to even (IEEE 754
+// default), and inputs outside the binary32 normal range (results that underflow or overflow,
+// infinities, NaN) take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  // branch-free (it runs per gathered entry inside the mixed-precision SpMV): every class of
+  // input is formed with selects; a subnormal m * 2^-149 is renormalised from its leading bit p
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t m = u & 0x7fffffu;
+  const int p = 31 - __clz(m | 1u);  // leading bit of a subnormal's field (m > 0)
+  const bool sub = (e == 0u) & (m != 0u);
+  const uint64_t ed = sub ? (uint64_t)(p + 874) : (e == 0u ? 0ull : (e == 0xffu ? 2047ull : (uint64_t)(e + 896u)));
+  const uint64_t md = sub ? (((uint64_t)m << (52 - p)) & 0xfffffffffffffull) : ((uint64_t)m << 29);
+  return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | (ed << 52) | md));
+}
+
+__device__ __forceinline__ float narrow_f64(double d) {
+  const uint64_t u = (uint64_t)__double_as_longlong(d);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e < 897 || e > 1150) return __double2float_rn(d);  // below the binary32 normal range, or beyond it
+  const uint64_t m = u & 0xfffffffffffffull;              // 52 mantissa bits
+  const uint64_t rem = m & 0x1fffffffull;                 // the 29 bits dropped
+  uint32_t bits = ((uint32_t)(e - 896) << 23) | (uint32_t)(m >> 29);
+  if (rem > 0x10000000ull || (rem == 0x10000000ull && (bits & 1u))) bits += 1u;  // may carry into the exponent (to infinity at the top)
+  return __uint_as_float(((uint32_t)(u >> 63) << 31) | bits);
+}
+
+template <typename TB, typename TA>
+__device__ __forceinline__ TB convert(TA a) {
+  if constexpr (std::is_same<TA, TB>::value) return a;
+  else if constexpr (std::is_same<TA, double>::value && std::is_same<TB, float>::value) return narrow_f64(a);
+  else if constexpr (std::is_same<TA, float>::value && std::is_same<TB, double>::value) return widen_f32(a);
+  else return (TB)a;
+}
 
 // ------------------------------------------------------------------------------------------
 // Generic fused row kernel:
@@ -122,7 +161,7 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
 #pragma unroll 4
     for (int p = b + lane; p < e; p += G) {
       const int c = __ldg(op.ci + p);
-      acc = fma((TY)__ldg(op.v + p), (TY)__ldg(src + c), acc);
+      acc = fma(convert<TY>(__ldg(op.v + p)), convert<TY>(__ldg(src + c)), acc);
     }
     if constexpr (G > 1) {
       const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -175,7 +214,7 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
       for (int k = 0; k < K; ++k) {
         if (j < len[k]) {
           const int64_t q = off[k] + 32 * (int64_t)j;
-          acc[k] = fma((TY)__ldg(op.sell.val + q), (TY)__ldg(src + __ldg(op.sell.col + q)), acc[k]);
+          acc[k] = fma(convert<TY>(__ldg(op.sell.val + q)), convert<TY>(__ldg(src + __ldg(op.sell.col + q))), acc[k]);
         }
       }
     }
@@ -227,10 +266,10 @@ __global__ void k_cast(int64_t n, VRef<const TA> a, VRef<TB> b, const int* skip)
     x.load(pa + 4 * q);
     Quad<TB> y;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) y.v[k] = (TB)x.v[k];
+    for (int k = 0; k < 4; ++k) y.v[k] = convert<TB>(x.v[k]);
     y.store(pb + 4 * q);
   }
-  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) pb[i] = (TB)pa[i];
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) pb[i] = convert<TB>(pa[i]);
 }
 
 template <typename T>

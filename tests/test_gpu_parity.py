@@ -563,3 +563,36 @@ def test_fp32_vcycle_on_unaligned_caller_arrays():
         big_z = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
         nsamg.apply_vcycle(h, big_r[1:], big_z[1:])
         assert np.array_equal(host(z), host(big_z)[1:])
+
+
+def test_fp32_casts_round_to_nearest_even():
+    """The FP64 -> FP32 -> FP64 casts of FP32-V-cycle handles (integer forms) against IEEE 754
+    conversion (numpy): a one-level FP32 handle whose operator is the identity returns
+    double(float(x)). Covers the whole exponent range, exact ties (to even), values beside them,
+    the binary32 overflow boundary (FLT_MAX + half an ulp rounds to infinity), the normal/subnormal
+    boundary, zeros, infinities and NaN."""
+    from workloads.hierarchy import Hierarchy, Level
+    rng = np.random.default_rng(17)
+    f = (rng.uniform(1, 2, 4000) * 2.0 ** rng.integers(-126, 128, 4000)).astype(np.float32)
+    f *= np.where(rng.random(4000) < 0.5, -1, 1).astype(np.float32)
+    ulp = np.spacing(np.abs(f)).astype(np.float64)
+    ties = f.astype(np.float64) + np.sign(f) * ulp / 2
+    vals = np.concatenate([
+        rng.uniform(-1, 1, 4000) * 2.0 ** rng.integers(-160, 160, 4000),
+        ties, np.nextafter(ties, np.inf), np.nextafter(ties, -np.inf),
+        [3.4028234663852886e38, 3.4028234663852886e38 * (1 + 2.0 ** -25), 3.4028235677973366e38,
+         np.nextafter(3.4028235677973366e38, 0), 1.1754943508222875e-38, 1.1754942e-38, 1.4e-45, 7e-46,
+         1e-40, -1e-40, 0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 2.0 ** 24 + 1, 16777217.0],
+    ])
+    n = vals.size
+    I = sp.identity(n, format="csr")
+    I.indices = I.indices.astype(np.int32)
+    I.indptr = I.indptr.astype(np.int32)
+    H = Hierarchy(levels=[Level(A=I)], coarse_inv=None)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(vcycle_fp32=1)) as h:
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        nsamg.level_spmv(h, 0, dev(vals), y)
+        got = host(y)
+    with np.errstate(over="ignore"):
+        want = vals.astype(np.float32).astype(np.float64)
+    np.testing.assert_array_equal(got, want)
