@@ -208,3 +208,30 @@ def test_solve_on_mm_ext_hierarchy():
                 assert np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b) <= 1e-8
                 its[interp] = st["iters"]
     assert its[1] <= its[0] + 2
+
+
+def test_setup_edge_cases():
+    # a 1 x 1 operator: no coarsening, the coarse inverse is 1 / a
+    one = sp.csr_matrix(np.array([[4.0]]))
+    with nsamg.amg_build(one, nsamg.amg_default_options()) as g:
+        H = g.export()
+        assert H.nlevels == 1 and np.allclose(H.coarse_inv, [[0.25]])
+    # max_levels = 1 stops before any coarsening
+    A = pressure3d_7pt(10, seed=1)
+    with nsamg.amg_build(A, nsamg.amg_default_options(max_levels=1, direct_max=0)) as g:
+        assert g.nlevels == 1 and g.export().coarse_inv is None
+    # positive couplings only, sign-aware strength: nothing is strong, every point would stay C,
+    # so coarsening stops (no level is added)
+    B = sp.csr_matrix(sp.diags([np.ones(999), 4 * np.ones(1000), np.ones(999)], [-1, 0, 1]))
+    B.sort_indices()
+    with nsamg.amg_build(B, nsamg.amg_default_options(strength_mode=1, coarse_max=10, direct_max=0)) as g:
+        assert g.nlevels == 1
+    # zero fixed-point sweeps: the factors are the initial guess l = a_ij / a_jj, u = a_ij
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=100, ilu_sweeps=0)) as g:
+        lev = g.export().levels[0]
+        Ls, Us, dinv = OS.ilu0_factors(lev.A, 0)
+        assert rel_close(lev.ilu_L.data, Ls.data, 1e-15) and rel_close(lev.ilu_U.data, Us.data, 1e-15)
+    # an unknown interpolation choice is rejected
+    with pytest.raises(nsamg.NsamgError) as e:
+        nsamg.amg_build(A, nsamg.amg_default_options(interp=2))
+    assert e.value.status == -1
