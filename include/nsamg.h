@@ -317,8 +317,15 @@ int nsamg_amg_level_splitting(const nsamg_amg* g, int l, int32_t* cf, uint8_t* s
 /* Host copy of the whole hierarchy as a nsamg_hierarchy_desc; the arrays are owned by g and stay
  * valid until the next export or nsamg_amg_destroy. */
 int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out);
-/* nsamg_amg_export followed by nsamg_setup_hierarchy: a solver handle for the GPU-built hierarchy
- * (the handle owns its own copies; g may be destroyed afterwards). */
+/* A solver handle for the GPU-built hierarchy, formed on the device without a host round trip:
+ * the solve-phase arrays (D^-1, l1 diagonal, scaled triangles, plain SELL copies of near-uniform
+ * matrices, transfers, ILU(0) factors of the levels the smoother uses, coarse inverse) are derived
+ * from g's device operators by kernels, with the same arithmetic as nsamg_setup_hierarchy on the
+ * exported hierarchy (with fixed threads per row the two handles give bitwise equal solves;
+ * matrices that are not near-uniform get no sorted SELL copy here). The handle owns its own
+ * copies; g may be destroyed afterwards. Blocks until done.
+ * Errors: INVALID_ARG (null pointer, parameter out of range), BAD_MATRIX (a level operator with a
+ * missing or zero diagonal or a non-finite entry), OOM, CUDA. On error *out is NULL. */
 int nsamg_amg_setup_solver(nsamg_amg* g, const nsamg_params* p, void* cuda_stream, nsamg_handle** out);
 void nsamg_amg_destroy(nsamg_amg* g);
 

@@ -144,6 +144,19 @@ int validate(const nsamg_csr& A, bool square, bool need_diag, const char* name) 
   return NSAMG_OK;
 }
 
+// Threads per CSR row before tuning.
+int default_group(int n, int64_t nnz) {
+  const double avg = n ? (double)nnz / n : 0.0;
+  if (n < 16384) {
+    // small levels are latency bound: give each row enough lanes that every lane handles about
+    // one entry (the FP64 issue cost of idle lanes does not matter at this size)
+    int G = 1;
+    while (G < 32 && G < avg) G <<= 1;
+    return G;
+  }
+  return avg <= 12 ? 1 : avg <= 24 ? 2 : avg <= 48 ? 4 : avg <= 96 ? 8 : 16;
+}
+
 template <typename T>
 int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t nnz, DCSR<T>& d) {
   d.n = n;
@@ -256,16 +269,7 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
     CK(cudaMalloc(&d.s_val, sizeof(T) * sval.size()));
     CK(cudaMemcpy(d.s_val, sval.data(), sizeof(T) * sval.size(), cudaMemcpyHostToDevice));
   }
-  const double avg = n ? (double)nnz / n : 0.0;
-  if (n < 16384) {
-    // small levels are latency bound: give each row enough lanes that every lane handles about
-    // one entry (the FP64 issue cost of idle lanes does not matter at this size)
-    int G = 1;
-    while (G < 32 && G < avg) G <<= 1;
-    d.G = G;
-  } else {
-    d.G = avg <= 12 ? 1 : avg <= 24 ? 2 : avg <= 48 ? 4 : avg <= 96 ? 8 : 16;
-  }
+  d.G = default_group(n, nnz);
   return NSAMG_OK;
 }
 

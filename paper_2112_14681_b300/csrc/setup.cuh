@@ -1239,6 +1239,265 @@ int build(const nsamg_csr& A0, const nsamg_amg_options& o, nsamg_amg* g, cudaStr
 
 }  // namespace gsetup
 
+// ==============================================================================================
+// Solver handle straight from the device hierarchy (no host round trip): the per-level arrays the
+// solve phase needs (D^-1, the l1 diagonal, the pre-scaled triangles, the plain SELL copies of
+// near-uniform matrices, ILU(0) factors, transfers, coarse inverse) are formed by kernels from the
+// GPU-built operators, with the same arithmetic as the host path. Matrices that are not near-
+// uniform get no SELL copy here (the host path's sorted SELL-32-sigma layout is not built).
+// ==============================================================================================
+namespace gsetup {
+
+// D^-1, the l1 row sums' inverses and max_i sum_j |a_ij| (flags[0], as the bits of a non-negative
+// double, which order like the values); flags[1] gets bit 0 for a row with a missing or zero
+// diagonal and bit 1 for a non-finite entry.
+__global__ void k_diag_l1(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                          double* __restrict__ dinv, double* __restrict__ dl1, unsigned long long* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0, s1 = 0.0;
+  unsigned long long bad = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    if (ci[p] == i) a = v[p];
+    s1 += fabs(v[p]);
+    if (!isfinite(v[p])) bad |= 2ull;
+  }
+  if (a == 0.0) bad |= 1ull;
+  dinv[i] = 1.0 / a;
+  dl1[i] = 1.0 / s1;
+  if (isfinite(s1)) atomicMax(&flags[0], (unsigned long long)__double_as_longlong(s1));
+  if (bad) atomicOr(&flags[1], bad);
+}
+
+__global__ void k_tri_count(int n, const int* __restrict__ rp, const int* __restrict__ ci, int lower, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) c += lower ? (ci[p] < i) : (ci[p] > i);
+  cnt[i] = c;
+}
+
+// strictly lower (or upper) part, rows scaled by rs and columns by cs (each optional)
+__global__ void k_tri_fill(int n, const int* __restrict__ rp, const int* __restrict__ ci, const double* __restrict__ v,
+                           int lower, const double* __restrict__ rs, const double* __restrict__ cs, const int* __restrict__ trp,
+                           int* __restrict__ tci, double* __restrict__ tv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = trp[i];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int c = ci[p];
+    if (lower ? c < i : c > i) {
+      double x = v[p];
+      if (rs) x *= rs[i];
+      if (cs) x *= cs[c];
+      tci[o] = c;
+      tv[o] = x;
+      ++o;
+    }
+  }
+}
+
+__global__ void k_chunk_slots(int n, int nch, const int* __restrict__ rp, int64_t* __restrict__ slots) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  int w = 0;
+  for (int i = c * 32; i < min(n, c * 32 + 32); ++i) w = max(w, rp[i + 1] - rp[i]);
+  slots[c] = 32 * (int64_t)w;
+}
+
+template <typename T>
+__global__ void k_plain_fill(int n, int m, int nch, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const T* __restrict__ v, const int64_t* __restrict__ cptr, int* __restrict__ scol,
+                             T* __restrict__ sval) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nch * 32) return;
+  const int c = pos >> 5, l = pos & 31, row = pos;
+  const int w = (int)((cptr[c + 1] - cptr[c]) >> 5);
+  const int len = row < n ? rp[row + 1] - rp[row] : 0;
+  const int b = row < n ? rp[row] : 0;
+  const int pad_col = len > 0 ? ci[b + len - 1] : min(row, m - 1);
+  for (int j = 0; j < w; ++j) {
+    const int64_t q = cptr[c] + (int64_t)j * 32 + l;
+    scol[q] = j < len ? ci[b + j] : pad_col;
+    sval[q] = j < len ? v[b + j] : T(0);
+  }
+}
+
+template <typename TB, typename TA>
+__global__ void k_convert(int64_t n, const TA* __restrict__ a, TB* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = nsamg::convert<TB>(a[i]);
+}
+
+// Device CSR (FP64 values) -> DCSR<T> of the solve phase: copy or round the values, plain SELL
+// copy when natural-order chunks pad by <= kPlainPad, default threads per row.
+template <typename T>
+int dev_upload(const GCsr& sc, DCSR<T>& d, cudaStream_t s) {
+  d.n = sc.n;
+  d.m = sc.m;
+  d.nnz = sc.nnz;
+  const int64_t cap = std::max<int64_t>(sc.nnz, 1);
+  CK(cudaMalloc(&d.rp, sizeof(int) * (sc.n + 1)));
+  CK(cudaMalloc(&d.ci, sizeof(int) * cap));
+  CK(cudaMalloc(&d.v, sizeof(T) * cap));
+  CK(cudaMemcpyAsync(d.rp, sc.rp, sizeof(int) * (sc.n + 1), cudaMemcpyDeviceToDevice, s));
+  if (sc.nnz) {
+    CK(cudaMemcpyAsync(d.ci, sc.ci, sizeof(int) * sc.nnz, cudaMemcpyDeviceToDevice, s));
+    if constexpr (sizeof(T) == sizeof(double)) {
+      CK(cudaMemcpyAsync(d.v, sc.v, sizeof(double) * sc.nnz, cudaMemcpyDeviceToDevice, s));
+    } else {
+      k_convert<T, double><<<nblocks(sc.nnz), kSetupThreads, 0, s>>>(sc.nnz, sc.v, d.v);
+    }
+  }
+  d.G = default_group(sc.n, sc.nnz);
+  if (sc.n >= kSellMinRows && sc.nnz > 0) {
+    const int nch = (sc.n + 31) / 32;
+    int64_t *slots = nullptr, *cptr = nullptr;
+    CK(cudaMallocAsync((void**)&slots, sizeof(int64_t) * nch, s));
+    CK(cudaMalloc(&cptr, sizeof(int64_t) * (nch + 1)));
+    k_chunk_slots<<<nblocks(nch), kSetupThreads, 0, s>>>(sc.n, nch, sc.rp, slots);
+    int rc = scan_excl<int64_t>(slots, cptr, nch, s);
+    int64_t total = 0;
+    if (rc == NSAMG_OK) rc = read_scalar(cptr + nch, &total, s);
+    cudaFreeAsync(slots, s);
+    if (rc != NSAMG_OK) {
+      cudaFree(cptr);
+      return rc;
+    }
+    if ((double)total <= kPlainPad * (double)sc.nnz) {
+      d.s_cptr = cptr;
+      CK(cudaMalloc(&d.s_col, sizeof(int) * std::max<int64_t>(total, 1)));
+      CK(cudaMalloc(&d.s_val, sizeof(T) * std::max<int64_t>(total, 1)));
+      k_plain_fill<T><<<nblocks((int64_t)nch * 32), kSetupThreads, 0, s>>>(sc.n, sc.m, nch, d.rp, d.ci, d.v, d.s_cptr,
+                                                                           d.s_col, d.s_val);
+      d.nchunks = nch;
+      d.sell_k = 1;
+    } else {
+      cudaFree(cptr);
+    }
+  }
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+template <typename T>
+int dev_vec(const double* src, int64_t n, T** d, cudaStream_t s) {
+  CK(cudaMalloc(d, sizeof(T) * std::max<int64_t>(n, 1)));
+  if constexpr (sizeof(T) == sizeof(double)) {
+    CK(cudaMemcpyAsync(*d, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    k_convert<T, double><<<nblocks(n), kSetupThreads, 0, s>>>(n, src, *d);
+  }
+  return NSAMG_OK;
+}
+
+// The triangle of A (strict lower / upper), rows scaled by rs, columns by cs, as DCSR<T>.
+template <typename T>
+int dev_tri(const GCsr& A, bool lower, const double* rs, const double* cs, DCSR<T>& d, cudaStream_t s) {
+  DMem tmp;
+  int* cnt = nullptr;
+  SK(tmp.alloc(&cnt, A.n));
+  k_tri_count<<<nblocks(A.n), kSetupThreads, 0, s>>>(A.n, A.rp, A.ci, lower ? 1 : 0, cnt);
+  GCsr T0;
+  T0.n = T0.m = A.n;
+  SK(rowptr_from_counts(tmp, cnt, A.n, &T0.rp, &T0.nnz, s));
+  SK(tmp.alloc(&T0.ci, T0.nnz));
+  SK(tmp.alloc(&T0.v, T0.nnz));
+  k_tri_fill<<<nblocks(A.n), kSetupThreads, 0, s>>>(A.n, A.rp, A.ci, A.v, lower ? 1 : 0, rs, cs, T0.rp, T0.ci, T0.v);
+  SK(dev_upload<T>(T0, d, s));
+  CK(cudaStreamSynchronize(s));
+  return NSAMG_OK;
+}
+
+template <typename T>
+int dev_build_levels(nsamg_amg* g, const nsamg_params& p, std::vector<Level<T>>& lvs, bool only_A0, double* anorm,
+                     cudaStream_t s) {
+  const int nl = only_A0 ? 1 : (int)g->levels.size();
+  lvs.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const GLevel& G = g->levels[l];
+    Level<T>& L = lvs[l];
+    L.n = G.A.n;
+    SK(dev_upload<T>(G.A, L.A, s));
+    if (only_A0) break;
+    DMem tmp;
+    double *dinv = nullptr, *dl1 = nullptr;
+    unsigned long long* flags = nullptr;
+    SK(tmp.alloc(&dinv, L.n));
+    SK(tmp.alloc(&dl1, L.n));
+    SK(tmp.alloc(&flags, 2));
+    CK(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned long long), s));
+    k_diag_l1<<<nblocks(L.n), kSetupThreads, 0, s>>>(L.n, G.A.rp, G.A.ci, G.A.v, dinv, dl1, flags);
+    unsigned long long hf[2] = {0, 0};
+    CK(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hf[1] & 2ull) return fail(NSAMG_ERR_BAD_MATRIX, "level " + std::to_string(l) + " A: non-finite value");
+    if (hf[1] & 1ull) return fail(NSAMG_ERR_BAD_MATRIX, "level " + std::to_string(l) + " A: missing or zero diagonal");
+    if (l == 0 && anorm) std::memcpy(anorm, &hf[0], sizeof(double));
+    SK(dev_vec<T>(dinv, L.n, &L.dinv, s));
+    SK(dev_vec<T>(dl1, L.n, &L.dl1inv, s));
+    SK(dev_tri<T>(G.A, true, dinv, dinv, L.L2, s));
+    SK(dev_tri<T>(G.A, false, dinv, dinv, L.U2, s));
+    SK(dev_tri<T>(G.A, true, dinv, nullptr, L.L1, s));
+    SK(dev_tri<T>(G.A, false, dinv, nullptr, L.U1, s));
+    if (l < (int)g->levels.size() - 1 && G.P.rp) {
+      SK(dev_upload<T>(G.P, L.P, s));
+      SK(dev_upload<T>(G.R, L.R, s));
+    }
+    const bool want_ilu = (p.smoother == NSAMG_SMOOTHER_ILU0) || (p.smoother == NSAMG_SMOOTHER_HYBRID_ILU0 && l == 0);
+    if (want_ilu && G.has_ilu) {
+      SK(dev_upload<T>(G.L, L.iL, s));
+      SK(dev_upload<T>(G.U, L.iU, s));
+      SK(dev_vec<T>(G.dinv, L.n, &L.idinv, s));
+      L.ilu = true;
+    }
+    L.kind = (p.smoother == NSAMG_SMOOTHER_JACOBI_L1) ? 'j' : (L.ilu ? 'i' : 'p');
+    T** vecs[] = {&L.b, &L.x, &L.r, &L.t1, &L.t2, &L.t3};
+    for (T** v : vecs) SK(alloc_vec(v, L.n));
+    CK(cudaStreamSynchronize(s));
+  }
+  return NSAMG_OK;
+}
+
+int dev_setup_impl(nsamg_amg* g, const nsamg_params* pp, void* stream, nsamg_handle* h) {
+  nsamg_params p;
+  nsamg_default_params(&p);
+  if (pp) p = *pp;
+  int rc = check_params(p);
+  if (rc) return rc;
+  h->p = p;
+  CK(cudaGetDevice(&h->device));
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreate(&h->stream));
+    h->own_stream = true;
+  }
+  cudaStream_t s = h->stream;
+  h->fp32 = p.vcycle_fp32 == 1;
+  double anorm = 0.0;
+  SK(dev_build_levels<double>(g, p, h->lv, h->fp32, h->fp32 ? nullptr : &anorm, s));
+  if (h->fp32) SK(dev_build_levels<float>(g, p, h->lv32, false, &anorm, s));
+  if (g->coarse_inv) {
+    h->nc = g->levels.back().A.n;
+    const int64_t nc2 = (int64_t)h->nc * h->nc;
+    if (h->fp32) SK(dev_vec<float>(g->coarse_inv, nc2, &h->coarse_inv32, s));
+    else SK(dev_vec<double>(g->coarse_inv, nc2, &h->coarse_inv, s));
+  }
+  SK(alloc_workspace(h));
+  h->anorm_inf = anorm;
+  CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
+  SK(tune_levels(h->lv, h->V, h->w, p.spmv_group, s));
+  if (h->fp32) SK(tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, s));
+  CK(cudaStreamSynchronize(s));
+  SK(build_tail_any(h));
+  SK(finish_graph(h));
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+}  // namespace gsetup
+
 extern "C" {
 
 void nsamg_amg_default_options(nsamg_amg_options* o) {
@@ -1356,10 +1615,16 @@ int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out) {
 int nsamg_amg_setup_solver(nsamg_amg* g, const nsamg_params* p, void* cuda_stream, nsamg_handle** out) {
   if (out) *out = nullptr;
   if (!g || !p || !out) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_amg_setup_solver: null argument");
-  nsamg_hierarchy_desc H;
-  int rc = nsamg_amg_export(g, &H);
-  if (rc) return rc;
-  return nsamg_setup_hierarchy(&H, p, cuda_stream, out);
+  nsamg_handle* h = new nsamg_handle();
+  const int rc = gsetup::dev_setup_impl(g, p, cuda_stream, h);
+  if (rc != NSAMG_OK) {
+    std::string keep = g_err;
+    destroy_impl(h);
+    g_err = keep;
+    return rc;
+  }
+  *out = h;
+  return NSAMG_OK;
 }
 
 void nsamg_amg_destroy(nsamg_amg* g) {

@@ -235,3 +235,51 @@ def test_setup_edge_cases():
     with pytest.raises(nsamg.NsamgError) as e:
         nsamg.amg_build(A, nsamg.amg_default_options(interp=2))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("smoother", ["hybrid_ilu0", "poly_gs", "jacobi_l1", "ilu0"])
+def test_device_built_handle_equals_the_host_built_handle(smoother):
+    """nsamg_amg_setup_solver forms D^-1, the l1 diagonal, the scaled triangles, the plain SELL
+    copies and the transfers from the device hierarchy with kernels; with the threads per row
+    fixed, the solve is bit for bit the one on the same hierarchy exported and set up on the
+    host (same arrays, same kernels)."""
+    A = pressure3d_7pt(32, seed=2)  # 32768 rows: level 0 gets its plain SELL copies
+    b = torch.from_numpy(rhs_uniform(A.shape[0], 3)).cuda()
+    sm = {"hybrid_ilu0": nsamg.HYBRID_ILU0, "poly_gs": nsamg.POLY_GS, "jacobi_l1": nsamg.JACOBI_L1,
+          "ilu0": nsamg.ILU0}[smoother]
+    p = nsamg.default_params(smoother=sm, spmv_group=1)
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=512, ilu_levels=0b111, ilu_sweeps=3)) as g:
+        H = g.export()
+        xs, sts = [], []
+        for make in (lambda: g.setup_solver(p), lambda: nsamg.setup_hierarchy(H, p)):
+            with make() as h:
+                x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+                sts.append(nsamg.solve(h, b, x, rtol=1e-8, maxit=300))
+                torch.cuda.synchronize()
+                xs.append(x.cpu().numpy())
+    assert sts[0]["converged"] and sts[0]["iters"] == sts[1]["iters"]
+    assert np.array_equal(xs[0], xs[1])
+    assert sts[0]["nrbe"] == sts[1]["nrbe"]  # same ||A||_inf
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_device_built_handle_tuned(fp32):
+    """Default (tuned) thread shapes and the FP32 V-cycle: the device-built handle converges to
+    the tolerance in the host-built handle's iteration count (+-1: the tuner may pick another
+    shape on each handle, which changes rounding only)."""
+    A = pressure3d_7pt(32, seed=5)
+    bn = rhs_uniform(A.shape[0], 1)
+    b = torch.from_numpy(bn).cuda()
+    p = nsamg.default_params(smoother=nsamg.HYBRID_ILU0, vcycle_fp32=fp32)
+    its = []
+    with nsamg.amg_build(A, nsamg.amg_default_options(coarse_max=512)) as g:
+        H = g.export()
+        for make in (lambda: g.setup_solver(p), lambda: nsamg.setup_hierarchy(H, p)):
+            with make() as h:
+                x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+                st = nsamg.solve(h, b, x, rtol=1e-8, maxit=300)
+                torch.cuda.synchronize()
+                assert st["converged"]
+                assert np.linalg.norm(bn - A @ x.cpu().numpy()) / np.linalg.norm(bn) <= 1e-8
+                its.append(st["iters"])
+    assert abs(its[0] - its[1]) <= 1
