@@ -435,10 +435,16 @@ inline VC<T> cref(const T* p) {
 }
 
 // out = [add +] [scale *] (bscale*base -/+ M src)  -- builders for the common forms
+// Matrices of at least this many stored bytes are streamed evict-first through L2 (ld_stream);
+// the smaller coarse-level matrices keep the default priority and can stay in L2 from one
+// V-cycle to the next.
+constexpr int64_t kStreamMatBytes = 32ll << 20;
+
 template <typename TM, typename TX, typename TY>
 void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
   op.n = M.n;
   op.src_n = M.m;
+  op.mat_stream = M.nnz * (int64_t)(sizeof(TM) + sizeof(int)) >= kStreamMatBytes;
   op.rp = M.rp;
   op.ci = M.ci;
   op.v = M.v;

@@ -117,7 +117,34 @@ struct RowOp {
   int neg = 0;
   const int* skip = nullptr;  // if set and *skip != 0 the launch does nothing (stopped solve)
   int src_n = 0;              // length of the source vector (columns of the matrix)
+  int mat_stream = 0;         // large matrix: entries loaded evict-first in L2 (ld_stream)
 };
+
+// Matrix entries of a large FP64 matrix in a row pass: each stored entry is read once per pass,
+// and a matrix streamed with the default L2 priority pushes out the vector that the pass gathers
+// from (each entry of it is gathered by several rows) and the vectors that the next pass reads
+// again. Such matrices are loaded evict-first in L2. (Bypassing L1 as well, or giving the FP32
+// matrices of the mixed-precision V-cycle the same path, measured slower.)
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int ld_stream(const int* p, uint64_t pol) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
 
 template <typename TM, typename TX, typename TY>
 __host__ __device__ inline int epi_code(const RowOp<TM, TX, TY>& op) {
@@ -158,10 +185,21 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
     const TX* __restrict__ src = op.src.get();
     const int lane = (int)(gid & (G - 1));
     const int b = __ldg(op.rp + row), e = __ldg(op.rp + row + 1);
+    bool stream = false;
+    if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+    if (stream) {
+      const uint64_t pol = l2_evict_first();
 #pragma unroll 4
-    for (int p = b + lane; p < e; p += G) {
-      const int c = __ldg(op.ci + p);
-      acc = fma(convert<TY>(__ldg(op.v + p)), convert<TY>(__ldg(src + c)), acc);
+      for (int p = b + lane; p < e; p += G) {
+        const int c = ld_stream(op.ci + p, pol);
+        acc = fma(convert<TY>(ld_stream(op.v + p, pol)), convert<TY>(__ldg(src + c)), acc);
+      }
+    } else {
+#pragma unroll 4
+      for (int p = b + lane; p < e; p += G) {
+        const int c = __ldg(op.ci + p);
+        acc = fma(convert<TY>(__ldg(op.v + p)), convert<TY>(__ldg(src + c)), acc);
+      }
     }
     if constexpr (G > 1) {
       const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -208,13 +246,30 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
       acc[k] = TY(0);
       jmax = max(jmax, len[k]);
     }
+    bool stream = false;
+    if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+    if (stream) {
+      const uint64_t pol = l2_evict_first();
 #pragma unroll 2
-    for (int j = 0; j < jmax; ++j) {
+      for (int j = 0; j < jmax; ++j) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (j < len[k]) {
-          const int64_t q = off[k] + 32 * (int64_t)j;
-          acc[k] = fma(convert<TY>(__ldg(op.sell.val + q)), convert<TY>(__ldg(src + __ldg(op.sell.col + q))), acc[k]);
+        for (int k = 0; k < K; ++k) {
+          if (j < len[k]) {
+            const int64_t q = off[k] + 32 * (int64_t)j;
+            acc[k] = fma(convert<TY>(ld_stream(op.sell.val + q, pol)), convert<TY>(__ldg(src + ld_stream(op.sell.col + q, pol))),
+                         acc[k]);
+          }
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int j = 0; j < jmax; ++j) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (j < len[k]) {
+            const int64_t q = off[k] + 32 * (int64_t)j;
+            acc[k] = fma(convert<TY>(__ldg(op.sell.val + q)), convert<TY>(__ldg(src + __ldg(op.sell.col + q))), acc[k]);
+          }
         }
       }
     }
