@@ -97,6 +97,7 @@ struct DCSR {
   int64_t* s_cptr = nullptr;
   int* s_col = nullptr;
   T* s_val = nullptr;
+  int s_width = 0;  // plain layout with uniform chunk width (0: widths from s_cptr)
   bool use_sell = false;
   int sell_k = 1;  // chunks per warp
   bool present() const { return n > 0; }
@@ -191,12 +192,17 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
   }
   if (plain) {
     const int nch = (n + 31) / 32;
-    std::vector<int64_t> cptr(nch + 1, 0);
+    std::vector<int> cw(nch, 0);
+    int wmax = 0;
     for (int c = 0; c < nch; ++c) {
-      int w = 0;
-      for (int i = c * 32; i < std::min(n, c * 32 + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
-      cptr[c + 1] = cptr[c] + 32 * (int64_t)w;
+      for (int i = c * 32; i < std::min(n, c * 32 + 32); ++i) cw[c] = std::max(cw[c], rp[i + 1] - rp[i]);
+      wmax = std::max(wmax, cw[c]);
     }
+    // every chunk as wide as the widest when that still pads by at most kPlainPad: the kernel then
+    // computes chunk offsets instead of loading them
+    d.s_width = 32.0 * wmax * nch <= kPlainPad * (double)nnz ? wmax : 0;
+    std::vector<int64_t> cptr(nch + 1, 0);
+    for (int c = 0; c < nch; ++c) cptr[c + 1] = cptr[c] + 32 * (int64_t)(d.s_width ? d.s_width : cw[c]);
     std::vector<int> scol(std::max<int64_t>(cptr[nch], 1), 0);
     std::vector<T> sval(std::max<int64_t>(cptr[nch], 1), T(0));
     for (int c = 0; c < nch; ++c) {
@@ -455,6 +461,7 @@ void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
     op.sell.cptr = M.s_cptr;
     op.sell.col = M.s_col;
     op.sell.val = M.s_val;
+    op.sell.width = M.s_width;
     op.sell_k = M.sell_k;
   }
 }

@@ -98,6 +98,7 @@ struct SellView {
   const int64_t* cptr = nullptr;  // chunk offsets, nchunks + 1
   const int* col = nullptr;
   const TM* val = nullptr;
+  int width = 0;  // plain layout with every chunk padded to this width: chunk c starts at 32 width c
 };
 
 template <typename TM, typename TX, typename TY>
@@ -234,10 +235,15 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
       const bool ok = c < op.sell.nchunks;
       const int pos = c * 32 + lane;
       if constexpr (PLAIN) {
-        const int64_t c_b = ok ? __ldg(op.sell.cptr + c) : 0;
         row[k] = (ok && pos < op.n) ? pos : -1;
-        len[k] = ok ? (int)((__ldg(op.sell.cptr + c + 1) - c_b) >> 5) : 0;
-        off[k] = c_b + lane;
+        if (op.sell.width) {  // uniform chunks: no offset load ahead of the entry loads
+          len[k] = ok ? op.sell.width : 0;
+          off[k] = (int64_t)c * 32 * op.sell.width + lane;
+        } else {
+          const int64_t c_b = ok ? __ldg(op.sell.cptr + c) : 0;
+          len[k] = ok ? (int)((__ldg(op.sell.cptr + c + 1) - c_b) >> 5) : 0;
+          off[k] = c_b + lane;
+        }
       } else {
         row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
         len[k] = ok ? __ldg(op.sell.rlen + pos) : 0;

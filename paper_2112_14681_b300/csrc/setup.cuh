@@ -1305,6 +1305,16 @@ __global__ void k_chunk_slots(int n, int nch, const int* __restrict__ rp, int64_
   slots[c] = 32 * (int64_t)w;
 }
 
+__global__ void k_max_slots(int nch, const int64_t* __restrict__ slots, unsigned long long* __restrict__ mx) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nch) atomicMax(mx, (unsigned long long)slots[c]);
+}
+
+__global__ void k_set_slots(int nch, int64_t v, int64_t* __restrict__ slots) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nch) slots[c] = v;
+}
+
 template <typename T>
 __global__ void k_plain_fill(int n, int m, int nch, const int* __restrict__ rp, const int* __restrict__ ci,
                              const T* __restrict__ v, const int64_t* __restrict__ cptr, int* __restrict__ scol,
@@ -1355,8 +1365,19 @@ int dev_upload(const GCsr& sc, DCSR<T>& d, cudaStream_t s) {
     int64_t *slots = nullptr, *cptr = nullptr;
     CK(cudaMallocAsync((void**)&slots, sizeof(int64_t) * nch, s));
     CK(cudaMalloc(&cptr, sizeof(int64_t) * (nch + 1)));
+    unsigned long long* mx = nullptr;
+    CK(cudaMallocAsync((void**)&mx, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
     k_chunk_slots<<<nblocks(nch), kSetupThreads, 0, s>>>(sc.n, nch, sc.rp, slots);
-    int rc = scan_excl<int64_t>(slots, cptr, nch, s);
+    k_max_slots<<<nblocks(nch), kSetupThreads, 0, s>>>(nch, slots, mx);
+    unsigned long long max_slots = 0;
+    int rc = read_scalar(mx, &max_slots, s);
+    cudaFreeAsync(mx, s);
+    // uniform chunk width (the widest chunk's) when that pads by at most kPlainPad, as on the host
+    const int wmax = (int)(max_slots / 32);
+    const bool uniform = 32.0 * wmax * nch <= kPlainPad * (double)sc.nnz;
+    if (rc == NSAMG_OK && uniform) k_set_slots<<<nblocks(nch), kSetupThreads, 0, s>>>(nch, 32 * (int64_t)wmax, slots);
+    if (rc == NSAMG_OK) rc = scan_excl<int64_t>(slots, cptr, nch, s);
     int64_t total = 0;
     if (rc == NSAMG_OK) rc = read_scalar(cptr + nch, &total, s);
     cudaFreeAsync(slots, s);
@@ -1365,6 +1386,7 @@ int dev_upload(const GCsr& sc, DCSR<T>& d, cudaStream_t s) {
       return rc;
     }
     if ((double)total <= kPlainPad * (double)sc.nnz) {
+      d.s_width = uniform ? wmax : 0;
       d.s_cptr = cptr;
       CK(cudaMalloc(&d.s_col, sizeof(int) * std::max<int64_t>(total, 1)));
       CK(cudaMalloc(&d.s_val, sizeof(T) * std::max<int64_t>(total, 1)));
