@@ -274,7 +274,7 @@ def time_kernels(nsamg, torch, h, A, H, stream, reps=24):
     g0 = nsamg.level_group(h, 0)  # layout the autotuner chose: 0 = SELL-32-sigma, else CSR threads per row
     out["spmv_l0"] = {"s": t, "bytes": spmv_bytes(A), "GBps": spmv_bytes(A) / t / 1e9,
                       "layout": "sell" if g0 == 0 else f"csr{g0}",
-                      "kernel": "k_sell<0, K, P, double, double, double> (SELL-32; P = 1, plain layout, for near-uniform rows)" if g0 == 0
+                      "kernel": "k_sell<0, K, U, P, double, double, double> (SELL-32, K chunks per warp, U entries staged; P = 1, plain layout, for near-uniform rows)" if g0 == 0
                       else f"k_row<{g0}, 0, double, double, double> (CSR, {g0} threads per row)"}
     tw = timed(lambda k: nsamg.level_spmv(h, 0, xs[0], ys[0]))
     out["spmv_l0_warm"] = {"s": tw, "GBps_algorithmic": spmv_bytes(A) / tw / 1e9,

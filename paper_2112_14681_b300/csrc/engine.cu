@@ -93,13 +93,13 @@ struct DCSR {
   // SELL-32-sigma copy (matrices with at least kSellMinRows rows); use_sell picks it at launch
   int nchunks = 0;
   int* s_perm = nullptr;
-  int* s_rlen = nullptr;
   int64_t* s_cptr = nullptr;
   int* s_col = nullptr;
   T* s_val = nullptr;
   int s_width = 0;  // plain layout with uniform chunk width (0: widths from s_cptr)
   bool use_sell = false;
   int sell_k = 1;  // chunks per warp
+  int sell_u = 1;  // entries staged per chunk and round
   bool present() const { return n > 0; }
 };
 
@@ -228,7 +228,8 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
     CK(cudaMemcpy(d.s_val, sval.data(), sizeof(T) * sval.size(), cudaMemcpyHostToDevice));
   } else if (n >= kSellMinRows && nnz > 0) {
     // SELL-32-sigma: sort rows by length (descending, stable) inside windows of sigma rows, cut
-    // into chunks of 32 positions, store each chunk column-major.
+    // into chunks of 32 positions, store each chunk column-major; every row is padded to its
+    // chunk's width with zero values in its own last column (the kernel reads no row lengths).
     const int nch = (n + 31) / 32;
     std::vector<int> perm((size_t)nch * 32, -1), rlen((size_t)nch * 32, 0), order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -249,16 +250,20 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
     }
     std::vector<int> scol(std::max<int64_t>(cptr[nch], 1), 0);
     std::vector<T> sval(std::max<int64_t>(cptr[nch], 1), T(0));
-    for (int c = 0; c < nch; ++c)
+    for (int c = 0; c < nch; ++c) {
+      const int w = (int)((cptr[c + 1] - cptr[c]) / 32);
       for (int l = 0; l < 32; ++l) {
         const int row = perm[(size_t)c * 32 + l];
-        if (row < 0) continue;
-        for (int j = 0; j < rlen[(size_t)c * 32 + l]; ++j) {
+        if (row < 0) continue;  // no row at this position: columns 0, values 0
+        const int len = rlen[(size_t)c * 32 + l];
+        const int pad_col = len > 0 ? ci[rp[row] + len - 1] : std::min(row, m - 1);
+        for (int j = 0; j < w; ++j) {
           const int64_t q = cptr[c] + (int64_t)j * 32 + l;
-          scol[q] = ci[rp[row] + j];
-          sval[q] = (T)v[rp[row] + j];
+          scol[q] = j < len ? ci[rp[row] + j] : pad_col;
+          sval[q] = j < len ? (T)v[rp[row] + j] : T(0);
         }
       }
+    }
     d.nchunks = nch;
     const double avg_row = (double)nnz / n;
     // FP64 rows are FP64-issue bound (one chunk per warp keeps registers and occupancy);
@@ -266,8 +271,6 @@ int upload(const int* rp, const int* ci, const double* v, int n, int m, int64_t 
     d.sell_k = sizeof(T) == sizeof(double) ? 1 : (avg_row <= 8 ? 4 : avg_row <= 16 ? 2 : 1);
     CK(cudaMalloc(&d.s_perm, sizeof(int) * perm.size()));
     CK(cudaMemcpy(d.s_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&d.s_rlen, sizeof(int) * rlen.size()));
-    CK(cudaMemcpy(d.s_rlen, rlen.data(), sizeof(int) * rlen.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d.s_cptr, sizeof(int64_t) * cptr.size()));
     CK(cudaMemcpy(d.s_cptr, cptr.data(), sizeof(int64_t) * cptr.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d.s_col, sizeof(int) * scol.size()));
@@ -295,7 +298,6 @@ void release(DCSR<T>& d) {
   cudaFree(d.ci);
   cudaFree(d.v);
   cudaFree(d.s_perm);
-  cudaFree(d.s_rlen);
   cudaFree(d.s_cptr);
   cudaFree(d.s_col);
   cudaFree(d.s_val);
@@ -363,43 +365,43 @@ void launch_csr(const RowOp<TM, TX, TY>& op, int nb, cudaStream_t s) {
   launch_k(k_row<G, E_RUNTIME, TM, TX, TY>, nb, kThreads, s, op);
 }
 
-template <int EPI, int K, typename TM, typename TX, typename TY>
+template <int EPI, int K, int U, typename TM, typename TX, typename TY>
 void launch_sell_one(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   const int nb = blocks_for((int64_t)((op.sell.nchunks + K - 1) / K) * 32);
   if (op.sell.perm)
-    launch_k(k_sell<EPI, K, false, TM, TX, TY>, nb, kThreads, s, op);
+    launch_k(k_sell<EPI, K, U, false, TM, TX, TY>, nb, kThreads, s, op);
   else
-    launch_k(k_sell<EPI, K, true, TM, TX, TY>, nb, kThreads, s, op);
+    launch_k(k_sell<EPI, K, U, true, TM, TX, TY>, nb, kThreads, s, op);
 }
 
-template <int K, typename TM, typename TX, typename TY>
+template <int K, int U, typename TM, typename TX, typename TY>
 void launch_sell_k(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   if constexpr (std::is_same<TX, TY>::value) {
     switch (epi_code(op)) {
-      case 0: launch_sell_one<0, K>(op, s); return;
-      case 3: launch_sell_one<3, K>(op, s); return;
-      case 7: launch_sell_one<7, K>(op, s); return;
-      case 11: launch_sell_one<11, K>(op, s); return;
-      case 16: launch_sell_one<16, K>(op, s); return;
-      case 19: launch_sell_one<19, K>(op, s); return;
-      case 27: launch_sell_one<27, K>(op, s); return;
+      case 0: launch_sell_one<0, K, U>(op, s); return;
+      case 3: launch_sell_one<3, K, U>(op, s); return;
+      case 7: launch_sell_one<7, K, U>(op, s); return;
+      case 11: launch_sell_one<11, K, U>(op, s); return;
+      case 16: launch_sell_one<16, K, U>(op, s); return;
+      case 19: launch_sell_one<19, K, U>(op, s); return;
+      case 27: launch_sell_one<27, K, U>(op, s); return;
       default: break;
     }
   } else {
     if (epi_code(op) == 0) {
-      launch_sell_one<0, K>(op, s);
+      launch_sell_one<0, K, U>(op, s);
       return;
     }
   }
-  launch_sell_one<E_RUNTIME, K>(op, s);
+  launch_sell_one<E_RUNTIME, K, U>(op, s);
 }
 
-// Chunks per warp: 4 for short rows (latency bound), 2 up to 16 entries per row, else 1.
+// SELL shapes (chunks per warp K, entries staged per chunk U): (1,1), (2,1), (4,1), (1,4), (2,2).
 template <typename TM, typename TX, typename TY>
-void launch_sell(const RowOp<TM, TX, TY>& op, int K, cudaStream_t s) {
-  if (K >= 4) launch_sell_k<4>(op, s);
-  else if (K == 2) launch_sell_k<2>(op, s);
-  else launch_sell_k<1>(op, s);
+void launch_sell(const RowOp<TM, TX, TY>& op, int K, int U, cudaStream_t s) {
+  if (K >= 4) launch_sell_k<4, 1>(op, s);
+  else if (K == 2) U > 1 ? launch_sell_k<2, 2>(op, s) : launch_sell_k<2, 1>(op, s);
+  else U > 1 ? launch_sell_k<1, 4>(op, s) : launch_sell_k<1, 1>(op, s);
 }
 
 template <typename TM, typename TX, typename TY>
@@ -407,7 +409,7 @@ void launch_row(const RowOp<TM, TX, TY>& op, int G, cudaStream_t s) {
   if (op.n <= 0) return;
   ++g_launches;
   if (op.v && op.sell.nchunks > 0) {
-    launch_sell(op, op.sell_k, s);
+    launch_sell(op, op.sell_k, op.sell_u, s);
     return;
   }
   if (!op.v) G = 1;
@@ -457,12 +459,12 @@ void set_matrix(RowOp<TM, TX, TY>& op, const DCSR<TM>& M) {
   if (M.use_sell) {
     op.sell.nchunks = M.nchunks;
     op.sell.perm = M.s_perm;
-    op.sell.rlen = M.s_rlen;
     op.sell.cptr = M.s_cptr;
     op.sell.col = M.s_col;
     op.sell.val = M.s_val;
     op.sell.width = M.s_width;
     op.sell_k = M.sell_k;
+    op.sell_u = M.sell_u;
   }
 }
 
@@ -914,8 +916,8 @@ float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, c
   return best;
 }
 
-// Timed choice among CSR with G = 1, 2, ..., 32 threads per row and SELL-32-sigma with 1, 2 or
-// 4 chunks per warp (best of five single launches, each after an L2 sweep).
+// Timed choice among CSR with G = 1, 2, ..., 32 threads per row and the SELL shapes of
+// launch_sell (best of five single launches, each after an L2 sweep).
 template <typename T>
 int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s, const TuneScratch& fl) {
   if (M.n < 20000 || M.nnz == 0) return NSAMG_OK;
@@ -935,20 +937,27 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s, const TuneScratch& fl) {
       bestG = G;
     }
   }
+  int bestU = 1;
   if (M.nchunks > 0) {
-    for (int K : {1, 2, 4}) {
+    const int shapes[][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 4}, {2, 2}};
+    for (const auto& ku : shapes) {
       M.use_sell = true;
-      M.sell_k = K;
+      M.sell_k = ku[0];
+      M.sell_u = ku[1];
       const float ms = time_spmv(M, x, y, 1, s, e0, e1, fl);
       if (ms < best) {
         best = ms;
-        bestK = K;
+        bestK = ku[0];
+        bestU = ku[1];
       }
     }
   }
   M.G = bestG;
   M.use_sell = bestK > 0;
-  if (bestK) M.sell_k = bestK;
+  if (bestK) {
+    M.sell_k = bestK;
+    M.sell_u = bestU;
+  }
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -90,11 +90,10 @@ enum : int { E_NEG = 1, E_BASE = 2, E_BSCALE = 4, E_SCALE = 8, E_ADD = 16, E_RUN
 template <typename TM>
 struct SellView {
   int nchunks = 0;
-  // Sorted layout: position -> row (-1 for padding lanes) and the row's entries at each
-  // position. Both null for the plain layout of near-uniform matrices: rows in natural order
-  // (chunk c holds rows 32c..32c+31), every row padded to its chunk's width with zero values.
+  // Sorted layout: position -> row (-1 for padding lanes). Null for the plain layout of
+  // near-uniform matrices (rows in natural order, chunk c holds rows 32c..32c+31). Either way
+  // every row is padded to its chunk's width with zero values.
   const int* perm = nullptr;
-  const int* rlen = nullptr;
   const int64_t* cptr = nullptr;  // chunk offsets, nchunks + 1
   const int* col = nullptr;
   const TM* val = nullptr;
@@ -109,6 +108,7 @@ struct RowOp {
   const TM* v = nullptr;
   SellView<TM> sell;              // used instead of rp/ci/v when sell.nchunks > 0
   int sell_k = 1;                 // SELL chunks per warp (host-side launch choice)
+  int sell_u = 1;                 // SELL entries staged per chunk and round (host-side launch choice)
   VRef<const TX> src;
   VRef<const TY> base;
   const TY* bscale = nullptr;
@@ -212,77 +212,95 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
   row_epilogue<EPI>(op, row, acc);
 }
 
-// K chunks per warp: the K chunks' loads are interleaved in one loop so that each thread keeps
-// K independent gather chains in flight (rows of 2-7 entries are otherwise latency bound).
-// PLAIN: natural row order, chunk width from cptr, no permutation or length reads (the padding
-// entries hold zero values, so they add exact zeros).
-template <int EPI, int K, bool PLAIN, typename TM, typename TX, typename TY>
+template <bool ST, typename T>
+__device__ __forceinline__ T ld_entry(const T* p, uint64_t pol) {
+  if constexpr (ST) return ld_stream(p, pol);
+  else return __ldg(p);
+}
+
+// Entries j, j+1, ... of K chunks, U at a time per chunk: the column and value loads of all K*U
+// entries are issued before any gather and the gathers before any FMA, so a thread has K*U
+// entries in flight per memory round trip (longer rows are latency bound with one or two; short
+// rows prefer U = 1, which needs fewer registers and keeps more warps resident). Every lane runs
+// to its chunk's width (uniform over the warp); padded entries hold zero values and a column of
+// their own row, so they add exact zeros. Each row's FMAs keep the order j = 0, 1, 2, ...
+template <bool ST, int K, int U, typename TM, typename TX, typename TY>
+__device__ __forceinline__ void sell_accumulate(const SellView<TM>& sv, const TX* __restrict__ src, const int64_t (&off)[K],
+                                                const int (&len)[K], int jmax, TY (&acc)[K], uint64_t pol) {
+#pragma unroll(U == 1 ? 2 : 1)
+  for (int j = 0; j < jmax; j += U) {
+    int cj[K][U];
+    TM vj[K][U];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool in = j + u < len[k];
+        const int64_t q = off[k] + 32 * (int64_t)(j + u);
+        cj[k][u] = in ? ld_entry<ST>(sv.col + q, pol) : 0;
+        vj[k][u] = in ? ld_entry<ST>(sv.val + q, pol) : TM(0);
+      }
+    TX xj[K][U];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int u = 0; u < U; ++u) xj[k][u] = j + u < len[k] ? __ldg(src + cj[k][u]) : TX(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (j + u < len[k]) acc[k] = fma(convert<TY>(vj[k][u]), convert<TY>(xj[k][u]), acc[k]);
+  }
+}
+
+// K chunks of 32 rows per warp, each lane one row of each chunk, U entries of each chunk staged
+// per round (sell_accumulate). PLAIN: natural row order (chunk c holds rows 32c..32c+31);
+// otherwise rows sorted by length within windows, with a permutation. Chunk widths come from
+// cptr, or from sell.width when every chunk has the same width.
+template <int EPI, int K, int U, bool PLAIN, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
   pdl_enter();
   if (op.skip && *op.skip) return;
   const int lane = threadIdx.x & 31;
   const TX* __restrict__ src = op.src.get();
-  {
-    const int c0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * K;
-    if (c0 >= op.sell.nchunks) return;
-    int row[K], len[K];
-    int64_t off[K];
-    TY acc[K];
-    int jmax = 0;
+  const int c0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * K;
+  if (c0 >= op.sell.nchunks) return;
+  int row[K], len[K];
+  int64_t off[K];
+  TY acc[K];
+  int jmax = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int c = c0 + k;
-      const bool ok = c < op.sell.nchunks;
-      const int pos = c * 32 + lane;
-      if constexpr (PLAIN) {
-        row[k] = (ok && pos < op.n) ? pos : -1;
-        if (op.sell.width) {  // uniform chunks: no offset load ahead of the entry loads
-          len[k] = ok ? op.sell.width : 0;
-          off[k] = (int64_t)c * 32 * op.sell.width + lane;
-        } else {
-          const int64_t c_b = ok ? __ldg(op.sell.cptr + c) : 0;
-          len[k] = ok ? (int)((__ldg(op.sell.cptr + c + 1) - c_b) >> 5) : 0;
-          off[k] = c_b + lane;
-        }
-      } else {
-        row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
-        len[k] = ok ? __ldg(op.sell.rlen + pos) : 0;
-        off[k] = ok ? __ldg(op.sell.cptr + c) + lane : 0;
-      }
-      acc[k] = TY(0);
-      jmax = max(jmax, len[k]);
-    }
-    bool stream = false;
-    if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
-    if (stream) {
-      const uint64_t pol = l2_evict_first();
-#pragma unroll 2
-      for (int j = 0; j < jmax; ++j) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (j < len[k]) {
-            const int64_t q = off[k] + 32 * (int64_t)j;
-            acc[k] = fma(convert<TY>(ld_stream(op.sell.val + q, pol)), convert<TY>(__ldg(src + ld_stream(op.sell.col + q, pol))),
-                         acc[k]);
-          }
-        }
-      }
+  for (int k = 0; k < K; ++k) {
+    const int c = c0 + k;
+    const bool ok = c < op.sell.nchunks;
+    const int pos = c * 32 + lane;
+    if constexpr (PLAIN) {
+      row[k] = (ok && pos < op.n) ? pos : -1;
     } else {
-#pragma unroll 2
-      for (int j = 0; j < jmax; ++j) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (j < len[k]) {
-            const int64_t q = off[k] + 32 * (int64_t)j;
-            acc[k] = fma(convert<TY>(__ldg(op.sell.val + q)), convert<TY>(__ldg(src + __ldg(op.sell.col + q))), acc[k]);
-          }
-        }
-      }
+      row[k] = ok ? __ldg(op.sell.perm + pos) : -1;
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (row[k] >= 0) row_epilogue<EPI>(op, row[k], acc[k]);
+    if (op.sell.width) {  // uniform chunks: no offset load ahead of the entry loads
+      len[k] = ok ? op.sell.width : 0;
+      off[k] = (int64_t)c * 32 * op.sell.width + lane;
+    } else {
+      const int64_t c_b = ok ? __ldg(op.sell.cptr + c) : 0;
+      len[k] = ok ? (int)((__ldg(op.sell.cptr + c + 1) - c_b) >> 5) : 0;
+      off[k] = c_b + lane;
+    }
+    acc[k] = TY(0);
+    jmax = max(jmax, len[k]);
   }
+  bool stream = false;
+  if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+  if (stream) {
+    if constexpr (sizeof(TM) == sizeof(double))
+      sell_accumulate<true, K, U>(op.sell, src, off, len, jmax, acc, l2_evict_first());
+  } else {
+    sell_accumulate<false, K, U>(op.sell, src, off, len, jmax, acc, 0ull);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (row[k] >= 0) row_epilogue<EPI>(op, row[k], acc[k]);
 }
 
 // ------------------------------------------------------------------------------------------
