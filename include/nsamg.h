@@ -85,9 +85,9 @@ typedef struct {
   int32_t vcycle_fp32;   /* 0: FP64 V-cycle. 1: FP32 matrices and vectors in the V-cycle         */
   int32_t t_exact;       /* 0: T = I - L (truncated Neumann, Algorithm 1). 1: T = (I + L)^-1    */
   int32_t use_graph;     /* 1: run each solve as one CUDA graph with device-side loop control    */
-  int32_t spmv_group;    /* 0: autotune at setup (CSR with 1..32 threads per row, or SELL-32-sigma
-                            for matrices with >= 16384 rows); 1..32: CSR with that many threads per
-                            row; -1: SELL-32-sigma wherever available                              */
+  int32_t spmv_group;    /* 0: autotune at setup (CSR with 1..32 threads per row, or a SELL-32
+                            shape for matrices with >= 16384 rows); 1..32: CSR with that many
+                            threads per row; -1: SELL-32 wherever available (shape sell_shape)     */
   int32_t fuse_tail;     /* 1: the V-cycle below the first level with at most 8192 rows (every
                             smoother pass with all its Neumann terms, residual, transfers and the
                             coarse solve) runs as one thread-block-cluster kernel that stages each
@@ -95,6 +95,11 @@ typedef struct {
                             separate launches. 0 (default): one launch per pass, which measured
                             faster on B300 (16 SMs of a cluster are latency bound where 148 SMs
                             finish a pass in one wave). Batches ignore it.                        */
+  int32_t sell_shape;    /* with spmv_group = -1: the SELL launch shape 10 K + U, K chunks of 32
+                            rows per warp and U entries of each chunk staged per round: 11, 21,
+                            41, 14 or 22 (0 = 11). Every shape sums each row in the same order, so
+                            the results do not depend on it. Ignored otherwise (the autotuner
+                            picks the shape).                                                     */
 } nsamg_params;
 
 typedef struct {

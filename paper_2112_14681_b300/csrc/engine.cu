@@ -1246,6 +1246,9 @@ int check_params(const nsamg_params& p) {
   if (p.vcycle_fp32 != 0 && p.vcycle_fp32 != 1) return fail(NSAMG_ERR_INVALID_ARG, "vcycle_fp32 must be 0 or 1");
   if (p.spmv_group < -1 || p.spmv_group > 32 || (p.spmv_group > 0 && (p.spmv_group & (p.spmv_group - 1))))
     return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be -1, 0 or a power of two <= 32");
+  if (p.sell_shape != 0 && p.sell_shape != 11 && p.sell_shape != 21 && p.sell_shape != 41 && p.sell_shape != 14 &&
+      p.sell_shape != 22)
+    return fail(NSAMG_ERR_INVALID_ARG, "sell_shape must be 0, 11, 21, 41, 14 or 22");
   if (p.fuse_tail != 0 && p.fuse_tail != 1) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0 or 1");
   return NSAMG_OK;
 }
@@ -1365,7 +1368,7 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
 }
 
 template <typename T>
-int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaStream_t s) {
+int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, int shape, cudaStream_t s) {
   int rc;
   const bool timed = group == 0 && !lvs.empty() && lvs[0].A.n >= 20000;
   if (timed) tune_warmup(lvs[0].A, big_x, big_y, s);
@@ -1393,8 +1396,10 @@ int tune_levels(std::vector<Level<T>>& lvs, T* big_x, T* big_y, int group, cudaS
     DCSR<T>* mats[] = {&L.A, &L.L2, &L.U2, &L.L1, &L.U1, &L.P, &L.R, &L.iL, &L.iU};
     for (DCSR<T>* M : mats) {
       if (!M->present()) continue;
-      if (group == -1) {  // SELL-32-sigma wherever the matrix has it, default CSR shape elsewhere
+      if (group == -1) {  // SELL wherever the matrix has it (the given shape), default CSR shape elsewhere
         M->use_sell = M->nchunks > 0;
+        M->sell_k = shape ? shape / 10 : 1;
+        M->sell_u = shape ? shape % 10 : 1;
         continue;
       }
       if (group) {
@@ -1637,10 +1642,10 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
   if (bi && (rc = setup_batch_data(h, *bi))) return rc;
   // Threads per row: fixed by the caller or tuned on the device.
-  if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, h->stream))) return rc;
+  if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, p.sell_shape, h->stream))) return rc;
   if (h->fp32) {
     // FP32 scratch for tuning: the finest level's work vectors are the largest
-    if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, h->stream))) return rc;
+    if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, p.sell_shape, h->stream))) return rc;
   }
   CK(cudaStreamSynchronize(h->stream));
   stamp("tune");
@@ -2167,6 +2172,7 @@ void nsamg_default_params(nsamg_params* p) {
   p->t_exact = 0;
   p->use_graph = 1;
   p->spmv_group = 0;
+  p->sell_shape = 0;
   p->fuse_tail = 0;
 }
 

@@ -47,3 +47,18 @@ def test_status_strings_and_defaults():
     assert nsamg.status_str(-6) == "non-finite value"
     p = nsamg.default_params()
     assert (p.smoother, p.neumann_terms, p.restart, p.use_graph) == (nsamg.POLY_GS, 2, 30, 1)
+
+
+def _struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "nsamg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    return re.findall(r"\b(?:int32_t|int64_t|uint64_t|double|float)\s+(\w+)\s*;", body)
+
+
+@pytest.mark.parametrize("cname,pyname", [("nsamg_params", "Params"), ("nsamg_stats", "Stats")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes mirrors list the header's fields in the header's order (a field added to one
+    side only would shift every later field across the ABI)."""
+    from paper_2112_14681_b300 import nsamg
+    assert [f[0] for f in getattr(nsamg, pyname)._fields_] == _struct_fields(cname)
