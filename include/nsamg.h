@@ -144,6 +144,16 @@ int nsamg_solve(nsamg_handle* h, const double* d_b, double* d_x, double rtol, in
  * (in stream order after the solve; on an error return h_x holds the last iterate). */
 int nsamg_solve_host(nsamg_handle* h, const double* h_b, double* h_x, double rtol, int maxit, nsamg_stats* st);
 
+/* A second solver context on the hierarchy of `parent` (a handle from nsamg_setup_hierarchy or
+ * nsamg_amg_setup_solver): it shares the parent's read-only matrices, coarse inverse and tuned
+ * kernel shapes and owns its own level vectors, Krylov workspace, CUDA graph and a new
+ * non-blocking stream, so solves on different contexts can run at the same time from different
+ * host threads (for instance one context's host copies beside another's kernels). A solve on
+ * a context gives bitwise the parent's result. The parent must outlive its contexts; destroy a
+ * context with nsamg_destroy. Errors: INVALID_ARG (null pointer, a batch handle, or a context as
+ * parent), OOM, CUDA. On error *out is NULL. */
+int nsamg_context_create(nsamg_handle* parent, nsamg_handle** out);
+
 /* z = M^-1 r: one V-cycle with zero initial guess (Sec. 5). d_r, d_z: device float64, n entries.
  * Asynchronous on the handle's stream. */
 int nsamg_apply_vcycle(nsamg_handle* h, const double* d_r, double* d_z);

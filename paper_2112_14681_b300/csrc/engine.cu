@@ -2481,6 +2481,16 @@ int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream) 
   return NSAMG_OK;
 }
 
+int nsamg_context_create(nsamg_handle* parent, nsamg_handle** out) {
+  if (out) *out = nullptr;
+  if (!parent || !out) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_context_create: null argument");
+  if (parent->batch) return fail(NSAMG_ERR_INVALID_ARG, "nsamg_context_create: batch handle");
+  if (parent->shared_mats)
+    return fail(NSAMG_ERR_INVALID_ARG, "nsamg_context_create: pass the handle that owns the matrices");
+  CK(cudaSetDevice(parent->device));
+  return clone_context(parent, out);
+}
+
 void nsamg_destroy(nsamg_handle* h) { destroy_impl(h); }
 
 const char* nsamg_status_str(int s) {

@@ -65,7 +65,8 @@ EXPORTS = [
     "nsamg_default_params", "nsamg_setup_hierarchy", "nsamg_solve", "nsamg_solve_host", "nsamg_apply_vcycle",
     "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
-    "nsamg_update", "nsamg_destroy", "nsamg_status_str", "nsamg_last_error", "nsamg_launches_per_step",
+    "nsamg_update", "nsamg_destroy", "nsamg_context_create", "nsamg_status_str", "nsamg_last_error",
+    "nsamg_launches_per_step",
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
     "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
@@ -126,6 +127,7 @@ def load(path: str = LIB_PATH):
         "nsamg_amg_setup_solver": (i32, [vp, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
         "nsamg_amg_destroy": (None, [vp]),
         "nsamg_destroy": (None, [vp]),
+        "nsamg_context_create": (i32, [vp, ctypes.POINTER(vp)]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
         "nsamg_last_error": (ctypes.c_char_p, []),
@@ -238,6 +240,18 @@ class Handle:
         _check(lib.nsamg_setup_hierarchy(ctypes.byref(desc), ctypes.byref(self.params), sptr, ctypes.byref(h)))
         self._h = h
         self.n = levels[0].A.shape[0]
+
+    def context(self) -> "Handle":
+        """A second solver context on this hierarchy (nsamg_context_create); keeps this handle
+        alive while it exists."""
+        c = Handle.__new__(Handle)
+        c.params = self.params
+        hp = ctypes.c_void_p()
+        _check(load().nsamg_context_create(self._h, ctypes.byref(hp)))
+        c._h = hp
+        c.n = self.n
+        c._parent = self
+        return c
 
     def close(self):
         if getattr(self, "_h", None):
