@@ -174,6 +174,37 @@ __device__ __forceinline__ void row_epilogue(const RowOp<TM, TX, TY>& op, int ro
   op.out.get()[row] = t;
 }
 
+template <bool ST, typename T>
+__device__ __forceinline__ T ld_entry(const T* p, uint64_t pol) {
+  if constexpr (ST) return ld_stream(p, pol);
+  else return __ldg(p);
+}
+
+// Entries b + lane, b + lane + G, ... of one CSR row, UR per round: the UR column and value loads
+// are issued before the gathers and the gathers before the FMAs, which keep the order of p (so
+// the lane's sum is the one of the plain loop).
+template <bool ST, int G, int UR, typename TM, typename TX, typename TY>
+__device__ __forceinline__ TY csr_accumulate(const int* __restrict__ ci, const TM* __restrict__ v, const TX* __restrict__ src,
+                                             int b, int e, int lane, TY acc, uint64_t pol) {
+  for (int p0 = b + lane; p0 < e; p0 += UR * G) {
+    int cj[UR];
+    TM vj[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) {
+      const int p = p0 + u * G;
+      cj[u] = p < e ? ld_entry<ST>(ci + p, pol) : 0;
+      vj[u] = p < e ? ld_entry<ST>(v + p, pol) : TM(0);
+    }
+    TX xj[UR];
+#pragma unroll
+    for (int u = 0; u < UR; ++u) xj[u] = p0 + u * G < e ? __ldg(src + cj[u]) : TX(0);
+#pragma unroll
+    for (int u = 0; u < UR; ++u)
+      if (p0 + u * G < e) acc = fma(convert<TY>(vj[u]), convert<TY>(xj[u]), acc);
+  }
+  return acc;
+}
+
 template <int G, int EPI, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
   pdl_enter();
@@ -188,19 +219,12 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
     const int b = __ldg(op.rp + row), e = __ldg(op.rp + row + 1);
     bool stream = false;
     if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+    constexpr int UR = 4;
     if (stream) {
-      const uint64_t pol = l2_evict_first();
-#pragma unroll 4
-      for (int p = b + lane; p < e; p += G) {
-        const int c = ld_stream(op.ci + p, pol);
-        acc = fma(convert<TY>(ld_stream(op.v + p, pol)), convert<TY>(__ldg(src + c)), acc);
-      }
+      if constexpr (sizeof(TM) == sizeof(double))
+        acc = csr_accumulate<true, G, UR>(op.ci, op.v, src, b, e, lane, acc, l2_evict_first());
     } else {
-#pragma unroll 4
-      for (int p = b + lane; p < e; p += G) {
-        const int c = __ldg(op.ci + p);
-        acc = fma(convert<TY>(__ldg(op.v + p)), convert<TY>(__ldg(src + c)), acc);
-      }
+      acc = csr_accumulate<false, G, UR>(op.ci, op.v, src, b, e, lane, acc, 0ull);
     }
     if constexpr (G > 1) {
       const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -210,12 +234,6 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
     if (lane != 0) return;
   }
   row_epilogue<EPI>(op, row, acc);
-}
-
-template <bool ST, typename T>
-__device__ __forceinline__ T ld_entry(const T* p, uint64_t pol) {
-  if constexpr (ST) return ld_stream(p, pol);
-  else return __ldg(p);
 }
 
 // Entries j, j+1, ... of K chunks, U at a time per chunk: the column and value loads of all K*U
