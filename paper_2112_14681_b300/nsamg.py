@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -242,8 +243,9 @@ class Handle:
         self.n = levels[0].A.shape[0]
 
     def context(self) -> "Handle":
-        """A second solver context on this hierarchy (nsamg_context_create); keeps this handle
-        alive while it exists."""
+        """A second solver context on this hierarchy (nsamg_context_create). It keeps this handle
+        alive while it exists, and closing this handle closes its contexts first (they use its
+        matrices)."""
         c = Handle.__new__(Handle)
         c.params = self.params
         hp = ctypes.c_void_p()
@@ -251,9 +253,14 @@ class Handle:
         c._h = hp
         c.n = self.n
         c._parent = self
+        if not hasattr(self, "_contexts"):
+            self._contexts = weakref.WeakSet()
+        self._contexts.add(c)
         return c
 
     def close(self):
+        for c in list(getattr(self, "_contexts", ())):
+            c.close()
         if getattr(self, "_h", None):
             load().nsamg_destroy(self._h)
             self._h = None

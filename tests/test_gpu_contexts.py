@@ -66,6 +66,8 @@ def test_context_solves_equal_the_parent_also_concurrently(fp32):
         x = np.zeros(n)
         nsamg.solve_host(h, rhs[1], x, 1e-8, 300)
         assert np.array_equal(x, ref[1])
+        c3 = h.context()
+    assert c3._h is None  # closing the parent closed its live context first
 
 
 def test_context_of_a_batch_handle_is_rejected():
