@@ -344,9 +344,10 @@ int nsamg_amg_export(nsamg_amg* g, nsamg_hierarchy_desc* out);
 int nsamg_amg_setup_solver(nsamg_amg* g, const nsamg_params* p, void* cuda_stream, nsamg_handle** out);
 void nsamg_amg_destroy(nsamg_amg* g);
 
-/* Matrix layout chosen for a level's operator (diagnostic): 0 = SELL-32-sigma (one thread per
- * row, rows sorted by length inside windows of 4096 rows, chunks of 32 stored column-major),
- * else the number of threads per row of the CSR kernel. */
+/* Matrix layout chosen for a level's operator (diagnostic): 0 = the SELL-32 copy (chunks of 32
+ * rows stored column-major, one thread per row; natural row order when that pads by <= 3%, else
+ * rows sorted by length inside windows of 4096 rows), else the number of threads per row of the
+ * CSR kernel. For an FP32 V-cycle handle, the FP32 copy of the level's operator. */
 int nsamg_level_group(nsamg_handle* h, int level);
 
 /* Kernel launches in one Arnoldi step (V-cycle, SpMV, Gram, update). A solve launches
