@@ -1244,6 +1244,8 @@ int check_params(const nsamg_params& p) {
   if (p.pre_sweeps < 0 || p.post_sweeps < 0 || p.coarse_sweeps < 1) return fail(NSAMG_ERR_INVALID_ARG, "bad sweep counts");
   if (p.restart < 1 || p.restart > NSAMG_MAX_RESTART) return fail(NSAMG_ERR_INVALID_ARG, "restart out of range 1..64");
   if (p.vcycle_fp32 != 0 && p.vcycle_fp32 != 1) return fail(NSAMG_ERR_INVALID_ARG, "vcycle_fp32 must be 0 or 1");
+  if (p.t_exact != 0 && p.t_exact != 1) return fail(NSAMG_ERR_INVALID_ARG, "t_exact must be 0 or 1");
+  if (p.use_graph != 0 && p.use_graph != 1) return fail(NSAMG_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   if (p.spmv_group < -1 || p.spmv_group > 32 || (p.spmv_group > 0 && (p.spmv_group & (p.spmv_group - 1))))
     return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be -1, 0 or a power of two <= 32");
   if (p.sell_shape != 0 && p.sell_shape != 11 && p.sell_shape != 21 && p.sell_shape != 41 && p.sell_shape != 14 &&

@@ -62,3 +62,21 @@ def test_binding_structs_match_the_header(cname, pyname):
     side only would shift every later field across the ABI)."""
     from paper_2112_14681_b300 import nsamg
     assert [f[0] for f in getattr(nsamg, pyname)._fields_] == _struct_fields(cname)
+
+
+@pytest.mark.parametrize("bad", [dict(smoother=9), dict(neumann_terms=0), dict(ilu_terms_L=0), dict(ilu_terms_U=0),
+                                 dict(pre_sweeps=-1), dict(post_sweeps=-1), dict(coarse_sweeps=0), dict(restart=0),
+                                 dict(restart=65), dict(vcycle_fp32=2), dict(t_exact=2), dict(use_graph=2),
+                                 dict(spmv_group=3), dict(spmv_group=64), dict(spmv_group=-2), dict(sell_shape=12),
+                                 dict(fuse_tail=2)])
+def test_params_are_rejected_before_any_device_work(bad):
+    """nsamg_setup_hierarchy validates every parameter first: INVALID_ARG with a message, no device
+    needed (this runs on CPU)."""
+    from paper_2112_14681_b300 import nsamg
+    from workloads import pressure3d_7pt
+    from workloads.hierarchy import Hierarchy, Level
+    H = Hierarchy(levels=[Level(A=pressure3d_7pt(4))])
+    with pytest.raises(nsamg.NsamgError) as e:
+        nsamg.setup_hierarchy(H, nsamg.default_params(**bad))
+    assert e.value.status == -1
+    assert nsamg.load().nsamg_last_error()
