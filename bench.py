@@ -805,10 +805,9 @@ C3_EDGE = 192
 def run_c3(args):
     """27-point Q1 FE Laplacian on 192^3 interior nodes (7,077,888 rows, 189,119,224 nnz), wall-
     normal grading to h_x/h_z,min = 100, seeded symmetric permutation then RCM. FP32 V-cycle
-    inside FP64 flexible GMRES(30) against the FP64 V-cycle; true residuals checked with the
-    oracle's FP64 SpMV, and the FP32-V solution compared with the FP64 one."""
+    inside FP64 flexible GMRES(30) against the FP64 V-cycle; true residuals recomputed on the host
+    with scipy's FP64 product, and the FP32-V solution compared with the FP64 one."""
     import torch
-    import oracle.kernels as OK
     from paper_2112_14681_b300 import nsamg
     from workloads import build_hierarchy, rhs_uniform
     from workloads.matrices import q1_27pt_graded
@@ -838,10 +837,10 @@ def run_c3(args):
                 st = nsamg.solve(h, db, x, RTOL, 2000)
                 ts.append(time.perf_counter() - t1)
             xh = x.cpu().numpy()
-        rel = float(np.linalg.norm(OK.residual(A, b, xh)) / np.linalg.norm(b))
+        rel = float(np.linalg.norm(b - A @ xh) / np.linalg.norm(b))
         xs[name] = xh
         res[name] = {"s_per_solve": min(ts), "iters": st["iters"], "restarts": st["restarts"],
-                     "relres_true_oracle_spmv": rel, "relres_reported": st["relres_true"], "converged": st["converged"]}
+                     "relres_true_host_spmv": rel, "relres_reported": st["relres_true"], "converged": st["converged"]}
     res["x_fp32v_vs_fp64_rel"] = float(np.linalg.norm(xs["fp32v"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
     res["speedup_fp32v"] = res["fp64"]["s_per_solve"] / res["fp32v"]["s_per_solve"]
     print(json.dumps({"c3": res}))
