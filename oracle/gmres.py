@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .kernels import project
+from . import kernels as K
 
 
 @dataclass
@@ -140,6 +140,9 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
         vt <- w - [V, v_i] h;  H[:i+1, i] = h                      (step 12)
         beta also closes column i-1: H[i, i-1] = beta, then Givens  (steps 13-14)
     After the last step the subdiagonal of the final column is ||vt||.
+    Steps 6, 8/12 and 11 are the per-kernel references kernels.gram, kernels.update and
+    kernels.project, so the Arnoldi-relation, orthogonality and L = tril(V^T V) checks of this
+    solver also check those three functions.
     """
     if T_mode not in ("trunc", "exact"):
         raise ValueError("T_mode must be 'trunc' or 'exact'")
@@ -170,9 +173,7 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
             if i < m and iters + i < maxit:
                 z = M(vt)
                 w = A @ z
-                cols = [V[:, j] for j in range(i)] + [vt]
-                a = np.array([float(np.dot(c, vt)) for c in cols])
-                s = np.array([float(np.dot(c, w)) for c in cols])
+                a, s = K.gram(V[:, :i], vt, w)
                 beta = float(np.sqrt(a[i]))
             else:  # no further column: only the lagged norm of the last vector is needed
                 beta = float(np.linalg.norm(vt))
@@ -191,14 +192,12 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
                 break
             if beta == 0.0:  # exact breakdown at the start: b - A x = 0 handled above
                 break
-            V[:, i] = vt / beta
             Z[:, i] = z / beta
-            w = w / beta
             r = np.concatenate([s[:i] / beta, [s[i] / beta ** 2]])
             Lm[i, :i] = a[:i] / beta
-            h = project(Lm, r, T_mode)
+            h = K.project(Lm, r, T_mode)
             Hm[: i + 1, i] = h
-            vt = w - V[:, : i + 1] @ h
+            V[:, i], vt = K.update(V[:, :i], vt, w, beta, h)
         iters += k
         if k == 0:
             return GmresResult(x, iters, restarts, False, relres, relres_imp, hist)

@@ -340,14 +340,13 @@ def _c1():
     return A, H, b
 
 
-@pytest.mark.parametrize("solver", ["mgs", "trunc", "exact"])
-def test_gmres_arnoldi_relation_and_orthogonality(solver):
+def _check_arnoldi(f):
     """A Z_k = V_{k+1} H_{k+1,k} (Sec. 1) and near-orthonormal V (Sec. 3) on a well-conditioned cycle."""
     A, H, b = _c1()
     p = K.SmootherParams(neumann_terms=2)
     M = lambda v: vcycle(H, v, p)
-    f = gmres_mgs if solver == "mgs" else (lambda *a, **k: gmres_onereduce(*a, T_mode=solver, **k))
     r = f(A, b, M, m=30, rtol=1e-6)
+    assert r.converged
     rel = np.linalg.norm(A @ r.Z - r.V @ r.H) / (np.linalg.norm(A.toarray(), 2) * np.linalg.norm(r.Z))
     assert rel <= 1e-14
     k = r.V.shape[1] - 1
@@ -359,6 +358,12 @@ def test_gmres_arnoldi_relation_and_orthogonality(solver):
         loss = np.linalg.norm(np.eye(j + 1) - Vj.T @ Vj)
         assert loss <= 1e2 * eps / r.history[j - 1]
     assert np.linalg.norm(np.eye(2) - r.V[:, :2].T @ r.V[:, :2]) <= 1e-14
+
+
+@pytest.mark.parametrize("solver", ["mgs", "trunc", "exact"])
+def test_gmres_arnoldi_relation_and_orthogonality(solver):
+    f = gmres_mgs if solver == "mgs" else (lambda *a, **k: gmres_onereduce(*a, T_mode=solver, **k))
+    _check_arnoldi(f)
 
 
 @pytest.mark.parametrize("solver", ["mgs", "trunc"])
@@ -471,6 +476,15 @@ MUTANTS = [
     ("oracle.kernels", "T = U if backward else L", "T = L if backward else U", "polygs"),  # transposed operand
     ("oracle.kernels", "f = dinv * y\n        t = f.copy()", "f = y\n        t = f.copy()", "ilu"),  # D_U^-1 dropped
     ("oracle.gmres", "S = np.linalg.solve(np.eye(k) + U, U)", "S = U", "sknorm"),  # (I + U)^-1 dropped
+    # the one-reduce step kernels (Algorithm 1 steps 6, 8 and 12), reached through gmres_onereduce
+    ("oracle.kernels", "nxt = w / beta", "nxt = w", "krylov"),                   # w / beta dropped
+    ("oracle.kernels", "    nxt = nxt - h[V.shape[1]] * v\n", "", "krylov"),    # h_i v_i term dropped
+    ("oracle.kernels", "nxt = nxt - h[j] * V[:, j]", "nxt = nxt - h[j] * V[:, V.shape[1] - 1 - j]", "krylov"),
+    ("oracle.kernels", "v = vt / beta\n", "v = vt\n", "krylov"),                # v_i not normalised
+    ("oracle.kernels", "for j in range(V.shape[1])] + [vt]", "for j in range(V.shape[1])]", "krylov"),  # vt column dropped
+    ("oracle.kernels", "for j in range(V.shape[1])] + [vt]", "for j in range(V.shape[1])] + [w]", "krylov"),  # wrong last column
+    ("oracle.kernels", "s = np.array([float(np.dot(c, w)) for c in cols])",
+     "s = np.array([float(np.dot(c, vt)) for c in cols])", "krylov"),          # s formed with vt, not w
 ]
 
 
@@ -507,10 +521,26 @@ def _mutated(modname, old, new):
     return ns
 
 
-@pytest.mark.parametrize("modname,old,new,pin", MUTANTS, ids=[m[2].split("\n")[0] for m in MUTANTS])
-def test_planted_mistake_is_caught(modname, old, new, pin):
+def _fails(fn):
+    try:
+        fn()
+    except (AssertionError, IndexError, ValueError):
+        return True
+    return False
+
+
+@pytest.mark.parametrize("modname,old,new,pin", MUTANTS, ids=[m[2].split("\n")[0] or m[1].strip() for m in MUTANTS])
+def test_planted_mistake_is_caught(modname, old, new, pin, monkeypatch):
     """Each planted mistake in the oracle (on the CPU) makes one of the pins above fail."""
     ns = _mutated(modname, old, new)
+    if pin == "krylov":
+        # gmres_onereduce calls the step kernels through the module, so the planted kernel is the
+        # one the Arnoldi-relation, orthogonality and lower-Gram pins exercise
+        for name in ("gram", "update", "project"):
+            monkeypatch.setattr(K, name, ns[name])
+        trunc = lambda *a, **k: gmres_onereduce(*a, T_mode="trunc", **k)
+        assert _fails(lambda: _check_arnoldi(trunc)) or _fails(lambda: _check_lrows(gmres_onereduce))
+        return
     if pin == "project":
         with pytest.raises(AssertionError):
             _check_projection(ns["project"])
