@@ -18,6 +18,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.sparse as sp
 
 from . import kernels as K
 
@@ -124,8 +125,15 @@ def gmres_mgs(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxit: int
         V, Z, Hm = V[:, : k + 1], Z[:, :k], Hm[: k + 1, :k]
 
 
+def inf_norm(A) -> float:
+    """||A||_inf: the largest row sum of |a_ij|."""
+    if sp.issparse(A):
+        return float(abs(sp.csr_matrix(A)).sum(axis=1).max())
+    return float(np.abs(np.asarray(A)).sum(axis=1).max())
+
+
 def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxit: int = 1000,
-                    T_mode: str = "trunc") -> GmresResult:
+                    T_mode: str = "trunc", stop: str = "relres") -> GmresResult:
     """Algorithm 1 restated with right preconditioning (z = M^-1 vt) and the scalings the
     printed algorithm leaves implicit:
 
@@ -143,9 +151,16 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
     Steps 6, 8/12 and 11 are the per-kernel references kernels.gram, kernels.update and
     kernels.project, so the Arnoldi-relation, orthogonality and L = tril(V^T V) checks of this
     solver also check those three functions.
+    stop = "relres": ||b - A x|| / ||b|| <= rtol (eq. relres). stop = "nrbe": the norm-wise
+    relative backward error beta(x) = ||b - A x|| / (||b|| + ||A||_inf ||x||) <= rtol (Sec. 3);
+    inside a cycle the implicit residual is tested against rtol (||b|| + ||A||_inf ||x_0||) with
+    x_0 the cycle's start, and the true residual at the cycle's end decides with beta(x).
     """
     if T_mode not in ("trunc", "exact"):
         raise ValueError("T_mode must be 'trunc' or 'exact'")
+    if stop not in ("relres", "nrbe"):
+        raise ValueError("stop must be 'relres' or 'nrbe'")
+    anorm = inf_norm(A) if stop == "nrbe" else 0.0
     M = M or (lambda v: v.copy())
     n = b.size
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
@@ -157,9 +172,12 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
     Vout = Zout = Hout = Lout = None
     while True:
         vt = b - A @ x
-        relres = float(np.linalg.norm(vt)) / bnorm
-        if relres <= rtol or iters >= maxit:
-            return GmresResult(x, iters, max(restarts, 0), relres <= rtol, relres, min(relres_imp, relres), hist,
+        rnorm = float(np.linalg.norm(vt))
+        relres = rnorm / bnorm
+        den = bnorm + anorm * float(np.linalg.norm(x))  # the cycle's tolerance scale (= ||b|| for relres)
+        crit = rnorm / den
+        if crit <= rtol or iters >= maxit:
+            return GmresResult(x, iters, max(restarts, 0), crit <= rtol, relres, min(relres_imp, relres), hist,
                                Vout, Zout, Hout, Lout)
         restarts += 1
         V = np.zeros((n, m + 1))
@@ -186,7 +204,7 @@ def gmres_onereduce(A, b, M=None, x0=None, m: int = 30, rtol: float = 1e-8, maxi
                 k = i
                 relres_imp = res / bnorm
                 hist.append(relres_imp)
-                if beta == 0.0 or res <= rtol * bnorm or iters + i >= maxit:
+                if beta == 0.0 or res <= rtol * den or iters + i >= maxit:
                     done = True
             if done or z is None:
                 break

@@ -199,6 +199,65 @@ def test_ilut_complete_factorisation_and_ruiz():
     assert np.all(np.abs(Ut.max(axis=1).toarray() - 1) < 0.1) and np.all(np.abs(Ut.max(axis=0).toarray() - 1) < 0.1)
 
 
+def test_dep_bound_reproduces_the_printed_values():
+    """eq. depU against Table tab:depU (n = 14186, nu from Table tab:2normUs) and the worked
+    example after the theorem (n = 1e9, ||U_s|| = 0.8: at most 225)."""
+    from workloads.hierarchy import dep_bound
+    for n, nu, printed in _read_golden("dep_bound_tab_depU.txt"):
+        got = dep_bound(int(n), float(nu))
+        assert abs(got - float(printed)) <= (0.6 if float(printed) >= 225 else 0.01), (n, nu, got)
+
+
+def _ruiz_case(e=7, seed=3, lfil=4):
+    from workloads.hierarchy import ilut
+    A = pressure3d_7pt(e, seed=seed)
+    Ls, U, _, _ = ilut(A, droptol=1e-3, lfil=lfil, ruiz=False)
+    # a row/column imbalance that Ruiz has to remove (dep of the unscaled factor is large)
+    n = U.shape[0]
+    sr = np.exp(np.random.default_rng(seed).uniform(-6, 6, n))
+    return sp.csr_matrix(sp.diags(sr) @ U)
+
+
+def test_ruiz_dep_is_henrici_departure_of_the_scaled_factor():
+    """Sec. 5.3: dep(A) = sqrt(||A||_F^2 - ||D||_F^2) with D the eigenvalues; for the scaled
+    triangular factor the reported dep equals that definition evaluated with LAPACK's eigenvalues,
+    nu is ||U_s||_F of its unit-diagonal form, and the reported bound is eq. depU for that nu."""
+    from workloads.hierarchy import dep_bound, ruiz_dep
+    U = _ruiz_case()
+    dr, dc, info = ruiz_dep(U, dep_factor=1.0)
+    Ut = (sp.diags(dr) @ U @ sp.diags(dc)).toarray()
+    lam = np.linalg.eigvals(Ut)
+    dep = np.sqrt(max(np.linalg.norm(Ut) ** 2 - np.sum(np.abs(lam) ** 2), 0.0))
+    assert info["dep"] == pytest.approx(dep, rel=1e-8)
+    Us = np.diag(1.0 / np.diag(Ut)) @ Ut - np.eye(Ut.shape[0])
+    assert info["nu"] == pytest.approx(np.linalg.norm(Us), rel=1e-12)
+    assert info["bound"] == pytest.approx(dep_bound(Ut.shape[0], info["nu"]), rel=1e-12)
+    assert info["dep"] < 1e-2 * info["dep_unscaled"]  # scaling removed the imbalance
+
+
+def test_ruiz_dep_early_termination():
+    """The dep-based stop ends Ruiz after fewer sweeps than the max-norm criterion, either with dep
+    below the eq. depU bound or at the sweep where dep stopped decreasing (then with the smallest
+    dep of the sweeps run); the ILUT smoother with that scaling still equals the exact
+    triangular solves when enough terms are taken (the scaling does not change the limit)."""
+    from workloads.hierarchy import _csr, _load, ruiz_dep
+    U = _csr(_ruiz_case())
+    n = U.shape[0]
+    pdr, pdc = np.ones(n), np.ones(n)
+    plain_sweeps = _load().nsw_ruiz(n, U.indptr, U.indices, U.data, 1e-3, 50, pdr, pdc)  # max-norm Ruiz
+    dr, dc, info = ruiz_dep(U, dep_factor=1.0)
+    assert info["sweeps"] < plain_sweeps
+    assert info["reason"] in ("dep_below_bound", "dep_increased")
+    if info["reason"] == "dep_below_bound":
+        assert info["dep"] <= info["bound"]
+    # the scaled iteration is exact with n terms for any positive scaling
+    Ls = sp.csr_matrix((n, n))
+    A = sp.csr_matrix(U)
+    r = np.random.default_rng(1).standard_normal(n)
+    x = K.ilut_sweep(Ls, U, dr, dc, A, r, np.zeros(n), 1, n)
+    np.testing.assert_allclose(x, np.linalg.solve(U.toarray(), r), rtol=1e-9, atol=1e-12 * np.abs(x).max())
+
+
 def test_ilu0_fixed_point_has_the_ilu0_factors_as_fixed_point_and_converges():
     """The exact ILU(0) factors satisfy the fixed-point equations on the pattern (one sweep returns
     them), and the Jacobi-style sweeps reach them in finitely many steps."""
@@ -420,6 +479,30 @@ def test_truncation_does_not_change_convergence(smoother):
     assert np.linalg.norm(r2.x - r1.x) / nx <= 1e-10
 
 
+def _check_nrbe_stop(solver):
+    """Sec. 3: beta(x) = ||b - A x|| / (||b|| + ||A||_inf ||x||) never exceeds the relative residual,
+    so stopping on the backward error takes at most as many steps as stopping on eq. relres; on
+    the 2D Poisson matrix ||A||_inf ||x|| is 30 times ||b||, so a restarted solve (whose later
+    cycles know ||x_0||) stops earlier, with beta(x) <= tol while the relative residual is still
+    above tol."""
+    A, H, b = _c1()
+    p = K.SmootherParams(neumann_terms=2)
+    M = lambda v: vcycle(H, v, p)
+    r0 = solver(A, b, M, m=6, rtol=1e-8, stop="relres")
+    r1 = solver(A, b, M, m=6, rtol=1e-8, stop="nrbe")
+    Ad = A.toarray()
+    x = r1.x
+    beta = np.linalg.norm(b - Ad @ x) / (np.linalg.norm(b) + np.abs(Ad).sum(axis=1).max() * np.linalg.norm(x))
+    assert np.abs(Ad).sum(axis=1).max() * np.linalg.norm(x) >= 10 * np.linalg.norm(b)
+    assert r1.converged and beta <= 1e-8
+    assert r1.relres_true > 1e-8
+    assert r1.iters < r0.iters and r0.relres_true <= 1e-8
+
+
+def test_nrbe_stop():
+    _check_nrbe_stop(gmres_onereduce)
+
+
 def test_gmres_restart_path():
     """GMRES(m) with m smaller than the iteration count restarts from the true residual."""
     A, H, b = _c1()
@@ -476,6 +559,8 @@ MUTANTS = [
     ("oracle.kernels", "T = U if backward else L", "T = L if backward else U", "polygs"),  # transposed operand
     ("oracle.kernels", "f = dinv * y\n        t = f.copy()", "f = y\n        t = f.copy()", "ilu"),  # D_U^-1 dropped
     ("oracle.gmres", "S = np.linalg.solve(np.eye(k) + U, U)", "S = U", "sknorm"),  # (I + U)^-1 dropped
+    ("oracle.gmres", "den = bnorm + anorm * float(np.linalg.norm(x))", "den = bnorm", "nrbe"),  # ||A|| ||x|| dropped
+    ("oracle.gmres", "crit = rnorm / den", "crit = rnorm / bnorm", "nrbe"),    # outer test on eq. relres
     # the one-reduce step kernels (Algorithm 1 steps 6, 8 and 12), reached through gmres_onereduce
     ("oracle.kernels", "nxt = w / beta", "nxt = w", "krylov"),                   # w / beta dropped
     ("oracle.kernels", "    nxt = nxt - h[V.shape[1]] * v\n", "", "krylov"),    # h_i v_i term dropped
@@ -548,6 +633,10 @@ def test_planted_mistake_is_caught(modname, old, new, pin, monkeypatch):
     if pin == "sknorm":
         with pytest.raises(AssertionError):
             _check_sknorm(ns["sk_norm"])
+        return
+    if pin == "nrbe":
+        with pytest.raises(AssertionError):
+            _check_nrbe_stop(ns["gmres_onereduce"])
         return
     if pin == "lrows":
         with pytest.raises(AssertionError):

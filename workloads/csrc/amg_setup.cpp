@@ -399,4 +399,199 @@ int nsw_ruiz(int n, const int* rp, const int* ci, const double* v, double tol, i
   return it;
 }
 
+// Henrici's departure from normality of D_r U D_c for an upper triangular U (Sec. 5.3:
+// dep(A)^2 = ||A||_F^2 - ||D||_F^2 with D the eigenvalues, here the diagonal): the Frobenius
+// norm of the scaled strictly upper part. Also nu = ||diag(U~)^-1 U~ - I||_F, the ||U_s||_F of the
+// unit-diagonal form U~ = diag(U~)(I + U_s) that the theorem's bound is stated for.
+static void ruiz_dep(int n, const int* rp, const int* ci, const double* v, const double* dr, const double* dc,
+                     double* dep, double* nu) {
+  double d2 = 0.0, n2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) diag = dr[i] * v[p] * dc[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] != i) {
+        const double a = dr[i] * v[p] * dc[ci[p]];
+        d2 += a * a;
+        if (diag != 0.0) n2 += (a / diag) * (a / diag);
+      }
+  }
+  *dep = std::sqrt(d2);
+  *nu = std::sqrt(n2);
+}
+
+// Ruiz scaling of an upper triangular U with the early termination the paper proposes after the
+// dep(U) bound (Sec. 5.3, eq. depU): before each sweep k the departure from normality dep_k of
+// the current scaled factor is compared with dep_factor * sqrt((2 sqrt(n) + nu_k) nu_k); the
+// iteration stops when it is below, when dep_k no longer decreases (then the previous sweep's
+// scaling is kept: the paper observes dep(U) reaching its minimum after one or two sweeps), when
+// the row and column maxima are within `tol` of one, or after maxit sweeps.
+// info (7 doubles): dep and nu of the returned scaling, its bound, dep of the unscaled U,
+// the stop reason (0 tol, 1 dep below bound, 2 dep increased, 3 maxit), sweeps, 0.
+int nsw_ruiz_dep(int n, const int* rp, const int* ci, const double* v, double tol, int maxit, double dep_factor,
+                 double* dr, double* dc, double* info) {
+  std::vector<double> rmax(n), cmax(n), pr(n), pc(n);
+  for (int i = 0; i < n; ++i) dr[i] = dc[i] = 1.0;
+  double dep = 0.0, nu = 0.0;
+  ruiz_dep(n, rp, ci, v, dr, dc, &dep, &nu);
+  info[3] = dep;
+  double prev = INFINITY, prev_nu = 0.0;
+  int reason = 3, it = 0;
+  for (; it < maxit; ++it) {
+    const double bound = std::sqrt((2.0 * std::sqrt((double)n) + nu) * nu);
+    if (it > 0 && dep >= prev) {  // no longer decreasing: back to the previous sweep's scaling
+      for (int i = 0; i < n; ++i) {
+        dr[i] = pr[i];
+        dc[i] = pc[i];
+      }
+      dep = prev;
+      nu = prev_nu;
+      --it;
+      reason = 2;
+      break;
+    }
+    if (dep <= dep_factor * bound) {
+      reason = 1;
+      break;
+    }
+    std::fill(rmax.begin(), rmax.end(), 0.0);
+    std::fill(cmax.begin(), cmax.end(), 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        const double a = std::fabs(dr[i] * v[p] * dc[ci[p]]);
+        rmax[i] = std::max(rmax[i], a);
+        cmax[ci[p]] = std::max(cmax[ci[p]], a);
+      }
+    double dev = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (rmax[i] > 0) dev = std::max(dev, std::fabs(1.0 - rmax[i]));
+      if (cmax[i] > 0) dev = std::max(dev, std::fabs(1.0 - cmax[i]));
+    }
+    if (dev <= tol) {
+      reason = 0;
+      break;
+    }
+    for (int i = 0; i < n; ++i) {
+      pr[i] = dr[i];
+      pc[i] = dc[i];
+      if (rmax[i] > 0) dr[i] /= std::sqrt(rmax[i]);
+      if (cmax[i] > 0) dc[i] /= std::sqrt(cmax[i]);
+    }
+    prev = dep;
+    prev_nu = nu;
+    ruiz_dep(n, rp, ci, v, dr, dc, &dep, &nu);
+  }
+  info[0] = dep;
+  info[1] = nu;
+  info[2] = std::sqrt((2.0 * std::sqrt((double)n) + nu) * nu);
+  info[4] = reason;
+  info[5] = it;
+  info[6] = 0.0;
+  return it;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Input generation for the graded 27-point case: Q1 assembly and symmetric permutation. Both
+// reproduce the Python generator's scipy operations bit for bit (same products, sums and order)
+// and only make them parallel.
+// ------------------------------------------------------------------------------------------
+namespace {
+inline double tri(const double* d, const double* o, int a, int b) {
+  return a == b ? d[a] : o[a < b ? a : b];  // symmetric tridiagonal entry, |a - b| <= 1
+}
+}  // namespace
+
+extern "C" {
+
+// A = Mz (x) My (x) Kx + Mz (x) Ky (x) Mx + Kz (x) My (x) Mx on e^3 interior nodes (x fastest),
+// from the diagonals (d) and off-diagonals (o) of the assembled 1D stiffness K and mass M
+// matrices (x and y share Kx, Mx). Each entry is ((mz * my) * kx + (mz * ky) * mx) + (kz * my) * mx
+// (the order of scipy's kron products and CSR sums); exact zeros are dropped as scipy's sum does.
+// rp: n + 1 entries, ci / v: (3e - 2)^3 entries. Returns nnz.
+int64_t nsw_q1_assemble(int e, const double* kxd, const double* kxo, const double* mxd, const double* mxo,
+                        const double* kzd, const double* kzo, const double* mzd, const double* mzo, int64_t* rp,
+                        int* ci, double* v) {
+  const int64_t n = (int64_t)e * e * e;
+  rp[0] = 0;
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n; ++r) {
+    const int ix = (int)(r % e), iy = (int)((r / e) % e), iz = (int)(r / ((int64_t)e * e));
+    const int cx = (ix > 0) + 1 + (ix < e - 1), cy = (iy > 0) + 1 + (iy < e - 1), cz = (iz > 0) + 1 + (iz < e - 1);
+    rp[r + 1] = (int64_t)cx * cy * cz;
+  }
+  for (int64_t r = 0; r < n; ++r) rp[r + 1] += rp[r];
+  int64_t zeros = 0;
+#pragma omp parallel for schedule(static) reduction(+ : zeros)
+  for (int64_t r = 0; r < n; ++r) {
+    const int ix = (int)(r % e), iy = (int)((r / e) % e), iz = (int)(r / ((int64_t)e * e));
+    int64_t p = rp[r];
+    for (int jz = iz - 1; jz <= iz + 1; ++jz) {
+      if (jz < 0 || jz >= e) continue;
+      const double mz = tri(mzd, mzo, iz, jz), kz = tri(kzd, kzo, iz, jz);
+      for (int jy = iy - 1; jy <= iy + 1; ++jy) {
+        if (jy < 0 || jy >= e) continue;
+        const double my = tri(mxd, mxo, iy, jy), ky = tri(kxd, kxo, iy, jy);
+        const double t1 = mz * my, t2 = mz * ky, t3 = kz * my;
+        for (int jx = ix - 1; jx <= ix + 1; ++jx) {
+          if (jx < 0 || jx >= e) continue;
+          const double kx = tri(kxd, kxo, ix, jx), mx = tri(mxd, mxo, ix, jx);
+          const double val = (t1 * kx + t2 * mx) + t3 * mx;  // built with -ffp-contract=off: no FMAs
+          ci[p] = (int)(jx + (int64_t)e * (jy + (int64_t)e * jz));
+          v[p] = val;
+          zeros += (val == 0.0);
+          ++p;
+        }
+      }
+    }
+  }
+  if (zeros) {  // never expected for these operators; compact serially to match scipy
+    int64_t q = 0;
+    for (int64_t r = 0; r < n; ++r) {
+      const int64_t b = rp[r], end = rp[r + 1];
+      rp[r] = q;
+      for (int64_t p = b; p < end; ++p)
+        if (v[p] != 0.0) {
+          ci[q] = ci[p];
+          v[q] = v[p];
+          ++q;
+        }
+    }
+    rp[n] = q;
+  }
+  return rp[n];
+}
+
+// B = P A P^T for the ordering perm (new row k is old row perm[k]; new column of old column c is
+// inv[c] with inv[perm[k]] = k), columns sorted ascending in each row, values copied unchanged:
+// scipy's A[perm, :][:, perm] followed by sort_indices.
+void nsw_sym_permute(int n, const int* rp, const int* ci, const double* v, const int* perm, int* brp, int* bci,
+                     double* bv) {
+  std::vector<int> inv(n);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < n; ++k) inv[perm[k]] = k;
+  brp[0] = 0;
+  for (int k = 0; k < n; ++k) brp[k + 1] = brp[k] + (rp[perm[k] + 1] - rp[perm[k]]);
+#pragma omp parallel for schedule(dynamic, 4096)
+  for (int k = 0; k < n; ++k) {
+    const int o = perm[k];
+    int q = brp[k];
+    for (int p = rp[o]; p < rp[o + 1]; ++p, ++q) {
+      // insertion into the sorted prefix [brp[k], q)
+      const int c = inv[ci[p]];
+      const double x = v[p];
+      int t = q;
+      while (t > brp[k] && bci[t - 1] > c) {
+        bci[t] = bci[t - 1];
+        bv[t] = bv[t - 1];
+        --t;
+      }
+      bci[t] = c;
+      bv[t] = x;
+    }
+  }
+}
+
 }  // extern "C"

@@ -125,8 +125,39 @@ def _fe1d(h: np.ndarray):
 
 
 def _sym_permute(A: sp.csr_matrix, perm: np.ndarray) -> sp.csr_matrix:
-    """P A P^T for the ordering `perm` (new row k is old row perm[k])."""
-    return _finish(A[perm, :][:, perm])
+    """P A P^T for the ordering `perm` (new row k is old row perm[k]): the host setup library's
+    parallel form of scipy's A[perm, :][:, perm] with sorted columns (bitwise the same)."""
+    from .hierarchy import _load
+    n = A.shape[0]
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+    v = np.ascontiguousarray(A.data, dtype=np.float64)
+    brp = np.empty(n + 1, np.int32)
+    bci = np.empty(A.nnz, np.int32)
+    bv = np.empty(A.nnz, np.float64)
+    _load().nsw_sym_permute(n, rp, ci, v, perm, brp, bci, bv)
+    B = sp.csr_matrix((bv, bci, brp), shape=A.shape)
+    B.has_sorted_indices = True
+    return B
+
+
+def _q1_assemble(Kx, Mx, Kz, Mz) -> sp.csr_matrix:
+    """Mz(x)My(x)Kx + Mz(x)Ky(x)Mx + Kz(x)My(x)Mx by the host setup library (the products and
+    sums of scipy's kron / + in the same order, so bitwise the same matrix)."""
+    from .hierarchy import _load
+    e = Kx.shape[0]
+    d = lambda M: np.ascontiguousarray(M.diagonal(), dtype=np.float64)
+    o = lambda M: np.ascontiguousarray(M.diagonal(1) if e > 1 else np.zeros(1), dtype=np.float64)
+    n = e ** 3
+    nnz = (3 * e - 2) ** 3
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(nnz, np.int32)
+    v = np.empty(nnz, np.float64)
+    got = _load().nsw_q1_assemble(e, d(Kx), o(Kx), d(Mx), o(Mx), d(Kz), o(Kz), d(Mz), o(Mz), rp, ci, v)
+    A = sp.csr_matrix((v[:got], ci[:got], rp.astype(np.int32)), shape=(n, n))
+    A.has_sorted_indices = True
+    return A
 
 
 def q1_27pt_graded(e: int, aspect: float = 100.0, seed: int = 0, permute: bool = True,
@@ -146,10 +177,7 @@ def q1_27pt_graded(e: int, aspect: float = 100.0, seed: int = 0, permute: bool =
     hz = np.diff(_graded_coords(e, aspect, growth))
     Kx, Mx = _fe1d(hx)
     Kz, Mz = _fe1d(hz)
-    A = sp.kron(sp.kron(Mz, Mx), Kx, format="csr")
-    A = A + sp.kron(sp.kron(Mz, Kx), Mx, format="csr")
-    A = A + sp.kron(sp.kron(Kz, Mx), Mx, format="csr")
-    A = _finish(A)
+    A = _q1_assemble(Kx, Mx, Kz, Mz)
     if permute:
         A = _sym_permute(A, _rng(seed, _TAG_PERM).permutation(A.shape[0]))
         rcm = reverse_cuthill_mckee(A, symmetric_mode=True)
