@@ -125,6 +125,8 @@ SERVE_EDGES = (32, 160)
 SERVE_RATE = 200.0
 SERVE_WARM = 200
 SERVE_REQS = 2000
+SERVE_REQS_SUSTAINED = 1000  # the second run, at 0.7 of the FIFO FP64 arm's capacity
+SERVE_WARM_SUSTAINED = 100
 
 
 def _batch_system(args):
@@ -249,7 +251,7 @@ def spmv_bytes(A) -> int:
 N_ROT = 8  # vector pairs rotated through by the cold timings: 8 x 2 x 16.8 MB > 2 x L2
 
 
-def time_kernels(nsamg, torch, h, A, H, stream, reps=24):
+def time_kernels(nsamg, torch, h, A, H, stream, fma64: float, reps=24):
     """CUDA-event timing (on the library's stream) of single kernels of the level-0 operator.
     Each launch reads and writes vectors that no recent launch touched (N_ROT pairs larger than
     L2 together), so vector and matrix bytes both come from HBM; spmv_l0_warm repeats one x, y
@@ -290,22 +292,123 @@ def time_kernels(nsamg, torch, h, A, H, stream, reps=24):
                                   "note": "4 triangular passes (2 L_s, 2 U_s) from a zero guess"}
         out["ilu_sweep_x0_l0"]["GBps"] = out["ilu_sweep_x0_l0"]["bytes"] / tl / 1e9
         del b_ilu
-    # one-reduce Gram at step i = 10 and basis update over n rows
-    i = 10
-    ld = (n + 63) // 64 * 64
-    V = torch.rand((i + 2) * ld, dtype=torch.float64, device="cuda")
-    w = torch.rand(n, dtype=torch.float64, device="cuda")
-    o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
-    hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
-    ss = torch.empty(1, dtype=torch.float64, device="cuda")
+    # one-reduce Gram and basis update over n rows at step i = 10 and i = 40, in double-FP32 (the
+    # solve's default) and FP64; columns normalised like the solver's basis
+    hbm, _ = peaks()
     sp = stream.cuda_stream
-    tg = timed(lambda k: nsamg.gram(n, i, V, ld, w, o, sp))
-    out["gram_i10"] = {"s": tg, "bytes": 8 * (i + 2) * n, "GBps": 8 * (i + 2) * n / tg / 1e9,
-                       "dfma": 2 * (i + 1) * n}
-    tu = timed(lambda k: nsamg.update(n, i, V, ld, w, 1.0, hc, ss, sp))
-    out["update_i10"] = {"s": tu, "bytes": 8 * (i + 4) * n, "GBps": 8 * (i + 4) * n / tu / 1e9,
-                         "dfma": (i + 2) * n}
+    ld = (n + 63) // 64 * 64
+    for i in (10, 40):
+        V = torch.rand((i + 2) * ld, dtype=torch.float64, device="cuda")
+        Vv = V.view(i + 2, ld)
+        Vv[:, n:] = 0.0
+        Vv /= torch.linalg.norm(Vv, dim=1, keepdim=True)
+        w = torch.rand(n, dtype=torch.float64, device="cuda")
+        o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
+        hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
+        ss = torch.empty(1, dtype=torch.float64, device="cuda")
+        for tag, g, u, fg, fu in (("", nsamg.gram, nsamg.update, 2 * n, 3 * n),
+                                  ("_fp64", nsamg.gram_fp64, nsamg.update_fp64, 2 * (i + 1) * n, (i + 4) * n)):
+            tg = timed(lambda k: g(n, i, V, ld, w, o, sp))
+            tu = timed(lambda k: u(n, i, V, ld, w, 1.0, hc, ss, sp))
+            for name, t, b, f in ((f"gram{tag}_i{i}", tg, 8 * (i + 2) * n, fg), (f"update{tag}_i{i}", tu, 8 * (i + 4) * n, fu)):
+                out[name] = kernel_roofline(t, b, f, hbm, fma64)
     return out
+
+
+def kernel_roofline(t: float, nbytes: int, fp64_ops: int, hbm_gbs: float, fp64_fma_per_s: float) -> dict:
+    """A kernel's time against its two floors: algorithmic bytes at the measured HBM bandwidth and
+    FP64 operations at the measured FP64 FMA rate (B300 issues FP64 at ~1/80 of FP32)."""
+    t_hbm = nbytes / (hbm_gbs * 1e9)
+    t_fp64 = fp64_ops / fp64_fma_per_s
+    bound = "hbm" if t_hbm >= t_fp64 else "fp64"
+    return {"s": t, "bytes": nbytes, "GBps": nbytes / t / 1e9, "frac_hbm": t_hbm / t, "fp64_ops": fp64_ops,
+            "t_hbm_floor_s": t_hbm, "t_fp64_floor_s": t_fp64, "bound": bound, "frac_of_bound": max(t_hbm, t_fp64) / t}
+
+
+def main_config(A, H, world: int = 1) -> dict:
+    """The workload's static description, identical in both arms (measured values go elsewhere)."""
+    return {"workload": WORKLOAD, "n": int(A.shape[0]), "nnz": int(A.nnz), "levels": H.info["n"],
+            "operator_complexity": round(H.info["operator_complexity"], 3), "smoother": "hybrid_ilu0",
+            "restart": RESTART, "rtol": RTOL, "l2_flush": "none: working set > L2 (126 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
+# --- FP64 oracle on the host cores: whole solves in a spawn process pool (one thread each) ------
+_ORACLE = {}
+
+
+def _oracle_init(path):
+    import pickle
+    with open(path, "rb") as f:
+        _ORACLE.update(pickle.load(f))
+    import oracle.kernels as K
+    from oracle.vcycle import vcycle
+    p = K.SmootherParams(smoother=K.HYBRID_ILU0, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3)
+    vcycle(_ORACLE["H"], _ORACLE["rhs"][0], p)  # caches the level splits (untimed)
+
+
+def _oracle_solve(k):
+    """One full FP64 oracle solve (one-reduce GMRES(50), hybrid ILU(0) V-cycle) of rhs k."""
+    import oracle.kernels as K
+    from oracle.gmres import gmres_onereduce
+    from oracle.vcycle import vcycle
+    A, H, rhs = _ORACLE["A"], _ORACLE["H"], _ORACLE["rhs"]
+    p = K.SmootherParams(smoother=K.HYBRID_ILU0, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3)
+    t0 = time.perf_counter()
+    r = gmres_onereduce(A, rhs[k % len(rhs)], lambda v: vcycle(H, v, p), m=RESTART, rtol=RTOL, maxit=MAXIT)
+    return time.perf_counter() - t0, r.iters, r.relres_true
+
+
+def host_info() -> dict:
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        import psutil
+        avail = psutil.virtual_memory().available
+    except Exception:
+        avail = None
+    return {"nproc": os.cpu_count(), "cpu_model": model, "mem_available_gb": None if avail is None else round(avail / 2**30, 1)}
+
+
+def oracle_workers(want: int) -> int:
+    """Concurrent single-threaded oracle solves: at most one per core and ~3 GB of host memory
+    each (hierarchy, Krylov basis and directions of the 128^3 system)."""
+    info = host_info()
+    p = max(1, min(want, (info["nproc"] or 1)))
+    if info["mem_available_gb"]:
+        p = max(1, min(p, int(info["mem_available_gb"] // 3)))
+    return p
+
+
+class OraclePool:
+    """Spawn pool of single-threaded oracle workers that share the pickled inputs."""
+
+    def __init__(self, A, H, rhs, workers: int):
+        import multiprocessing as mp
+        import pickle
+        import tempfile
+        self.dir = tempfile.mkdtemp(prefix="nsamg_oracle_")
+        self.path = os.path.join(self.dir, "inputs.pkl")
+        with open(self.path, "wb") as f:
+            pickle.dump({"A": A, "H": H, "rhs": rhs}, f, protocol=pickle.HIGHEST_PROTOCOL)
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(self.path,))
+
+    def solves(self, ks):
+        return self.pool.map(_oracle_solve, list(ks), chunksize=1)
+
+    def close(self):
+        import shutil
+        self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
 
 
 def run_gpu(args):
@@ -416,12 +519,21 @@ def run_gpu(args):
     for c in ctxs:
         c.close()
     del hxs
-    kern = time_kernels(nsamg, torch, h, A, H, stream) if rank == 0 else {}
+    fma = {"fp64_fma_per_s": nsamg.fma_rate(True), "fp32_fma_per_s": nsamg.fma_rate(False),
+           "how": "nsamg_fma_probe: 8 blocks per SM x 256 threads, 8 independent FMA chains per thread, best of 5 "
+                  "launches timed with CUDA events"} if rank == 0 else {}
+    kern = time_kernels(nsamg, torch, h, A, H, stream, fma["fp64_fma_per_s"]) if rank == 0 else {}
     setup_t = time_gpu_setup(nsamg, torch, A, H) if rank == 0 and extras else None
     for hh in handles.values():
         hh.close()
     batched = run_batched(nsamg, torch, batch_sys) if batch_sys else None
     served = run_serving(nsamg, torch, serve_pool) if serve_pool else None
+    if served:
+        # the same stream at 0.7 of the FIFO FP64 arm's measured capacity, a rate both arms sustain
+        rate2 = round(0.7 * served["one_at_a_time_fp64"]["solves_per_s"], 1)
+        served["sustainable"] = run_serving(nsamg, torch, serve_pool, rate=rate2, nreq_meas=SERVE_REQS_SUSTAINED,
+                                            warm=SERVE_WARM_SUSTAINED)
+    c3 = run_c3_gpu_setup(nsamg, torch, C3_EDGE) if rank == 0 and extras and not args.skip_c3 else None
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -441,18 +553,17 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic (seeded lognormal-density 7-point FV pressure Poisson, b ~ U[-1,1])",
-            "config": {"workload": WORKLOAD, "n": n, "nnz": int(A.nnz), "levels": H.info["n"],
-                       "operator_complexity": round(H.info["operator_complexity"], 3), "smoother": main,
-                       "restart": RESTART, "rtol": RTOL, "l2_flush": "none: working set > L2 (126 MB)",
-                       "parallelism": f"replicas x{world}", "iters": main_r["iters"],
-                       "max_relres_true": main_r["max_relres_true"], "all_converged": main_r["all_converged"],
-                       "smoothers": {k: {kk: v[kk] for kk in ("s_per_solve", "solves_per_s", "iters", "max_relres_true",
-                                                             "all_converged")} for k, v in results.items()}},
+            "config": main_config(A, H, world),
+            "results": {"iters": main_r["iters"], "max_relres_true": main_r["max_relres_true"],
+                        "all_converged": main_r["all_converged"],
+                        "smoothers": {k: {kk: v[kk] for kk in ("s_per_solve", "solves_per_s", "iters", "max_relres_true",
+                                                              "all_converged")} for k, v in results.items()}},
             "roofline": {"kernel": sp["kernel"] + ", level-0 SpMV y = A x (autotuned layout)", "bound": "hbm",
                          "achieved": sp["GBps"], "peak": peak, "unit": "GB/s", "frac": sp["GBps"] / peak,
                          "peak_kind": peak_kind, "traffic": measured_traffic("spmv_l0_" + sp["layout"]),
                          "algorithmic_bytes": sp["bytes"], "launch_s": sp["s"]},
             "kernels": {k: {kk: (round(vv, 9) if isinstance(vv, float) else vv) for kk, vv in v.items()} for k, v in kern.items()},
+            "alu_peaks": fma,
             "clocks": main_r["clocks"],
             # value: one stream of solves, like the device-timed value; two_contexts: the same host-
             # buffer solves from two solver contexts and host threads (throughput, not latency)
@@ -468,8 +579,11 @@ def run_gpu(args):
             line["batched"] = batched
         if served:
             line["served"] = served
+        if c3:
+            line["c3"] = c3
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(A, H, rhs[0], x_first)
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(A, H, rhs)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -541,12 +655,22 @@ def _arrivals(n: int, rate: float, npool: int, seed: int = 3):
     return t, which
 
 
-def run_serving(nsamg, torch, pool, budget_gb: float = 80.0, slots: int = 8):
+def _queue_summary(q):
+    """Requests waiting or running, sampled at every arrival: percentiles and the mean over each
+    quarter of the run (a queue that keeps growing shows rising quarter means)."""
+    q = np.asarray(q, dtype=float)
+    quarters = [float(np.mean(c)) for c in np.array_split(q, 4)] if q.size >= 4 else []
+    return {"max": float(q.max()) if q.size else 0.0, "p50": float(np.percentile(q, 50)) if q.size else 0.0,
+            "mean_by_quarter": quarters}
+
+
+def run_serving(nsamg, torch, pool, rate: float = SERVE_RATE, nreq_meas: int = SERVE_REQS, warm: int = SERVE_WARM,
+                budget_gb: float = 80.0, slots: int = 8):
     """Poisson-arrival request stream on resident hierarchies: server (FP32 V-cycle, continuous
     batching) against plain FP64 one-at-a-time FIFO on the same arrival trace."""
-    nreq = SERVE_WARM + SERVE_REQS
-    t_arr, which = _arrivals(nreq, SERVE_RATE, len(pool))
-    out = {"pool": len(pool), "rate_per_s": SERVE_RATE, "requests": SERVE_REQS, "warmup": SERVE_WARM,
+    nreq = warm + nreq_meas
+    t_arr, which = _arrivals(nreq, rate, len(pool))
+    out = {"pool": len(pool), "rate_per_s": rate, "requests": nreq_meas, "warmup": warm,
            "pool_rows": int(sum(A.shape[0] for A, _ in pool))}
     gen = torch.Generator(device="cuda")
 
@@ -558,7 +682,7 @@ def run_serving(nsamg, torch, pool, budget_gb: float = 80.0, slots: int = 8):
     p32 = nsamg.default_params(restart=30, vcycle_fp32=1)
     hs = [nsamg.setup_hierarchy(H, p32) for _, H in pool]
     torch.cuda.synchronize()
-    lat, conv, done_t = [], True, []
+    lat, conv, done_t, qlen = [], True, [], []
     with nsamg.Server(int(budget_gb * (1 << 30)), slots) as srv:
         live = {}
         t0 = time.perf_counter()
@@ -568,7 +692,7 @@ def run_serving(nsamg, torch, pool, budget_gb: float = 80.0, slots: int = 8):
                     r = srv.poll(q)
                     if r is not None:
                         kk = live.pop(q)[0]
-                        if kk >= SERVE_WARM:
+                        if kk >= warm:
                             lat.append(r["t_done"] - r["t_submit"])
                             done_t.append(r["t_done"])
                             conv = conv and r["converged"] == 1
@@ -578,49 +702,55 @@ def run_serving(nsamg, torch, pool, budget_gb: float = 80.0, slots: int = 8):
             x = torch.zeros(n, dtype=torch.float64, device="cuda")
             tq = srv.submit(hs[which[k]], b, x)
             live[tq] = (k, b, x)
+            if k >= warm:
+                qlen.append(len(live))
         for q in list(live):
             r = srv.wait(q)
             kk = live.pop(q)[0]
-            if kk >= SERVE_WARM:
+            if kk >= warm:
                 lat.append(r["t_done"] - r["t_submit"])
                 done_t.append(r["t_done"])
                 conv = conv and r["converged"] == 1
         info = srv.info()
     for h in hs:
         h.close()
-    span = t_arr[-1] - t_arr[SERVE_WARM]
+    span = t_arr[-1] - t_arr[warm]
     lat = np.array(lat)
     out["server_fp32v"] = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                           "solves_per_s": SERVE_REQS / max(span, max(done_t) - min(done_t)),
+                           "solves_per_s": nreq_meas / max(span, max(done_t) - min(done_t)),
                            "all_converged": conv, "slots": slots, "budget_gb": budget_gb,
-                           "contexts_at_end": info["contexts"]}
+                           "contexts_at_end": info["contexts"], "queue": _queue_summary(qlen)}
     # --- one-at-a-time FP64 FIFO
     p64 = nsamg.default_params(restart=30)
     hs = [nsamg.setup_hierarchy(H, p64) for _, H in pool]
     torch.cuda.synchronize()
-    lat2, conv2 = [], True
+    lat2, conv2, qlen2 = [], True, []
     t0 = time.perf_counter()
     tdone = []
     for k in range(nreq):
         now = time.perf_counter() - t0
         if now < t_arr[k]:
             time.sleep(t_arr[k] - now)
+        elif k >= warm:  # requests already arrived and waiting behind this one, plus this one
+            qlen2.append(int(np.searchsorted(t_arr, now, side="right")) - k)
         n = pool[which[k]][0].shape[0]
         b = rhs(k, n)
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         st = nsamg.solve(hs[which[k]], b, x, RTOL, MAXIT)
         tf = time.perf_counter() - t0
-        if k >= SERVE_WARM:
+        if k >= warm:
             lat2.append(tf - t_arr[k])
             tdone.append(tf)
             conv2 = conv2 and st["converged"] == 1
+            if now < t_arr[k]:
+                qlen2.append(1)
     for h in hs:
         h.close()
     lat2 = np.array(lat2)
     out["one_at_a_time_fp64"] = {"p50_ms": float(np.percentile(lat2, 50) * 1e3),
                                  "p99_ms": float(np.percentile(lat2, 99) * 1e3),
-                                 "solves_per_s": SERVE_REQS / max(span, tdone[-1] - t_arr[SERVE_WARM]),
-                                 "all_converged": conv2}
+                                 "solves_per_s": nreq_meas / max(span, tdone[-1] - t_arr[warm]),
+                                 "all_converged": conv2, "queue": _queue_summary(qlen2)}
     return out
 
 
@@ -659,42 +789,63 @@ def cpu_baseline(A, H, b, gpu_x: dict):
     return {"value": 1.0 / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"one full FP64 oracle solve (numpy/scipy, single thread) of the 128^3 system, first rhs: "
                       f"{ref.iters} Arnoldi steps in {dt:.1f} s",
-            "oracle_iters": ref.iters, "gpu_x_rel_err_vs_oracle": errs}
+            "oracle_iters": ref.iters, "gpu_x_rel_err_vs_oracle": errs, **host_info()}
+
+
+def cpu_baseline_all_cores(A, H, rhs, want: int = 32):
+    """The same oracle on all host cores: one whole solve per single-threaded worker, all workers
+    at once (bounded by cores and host memory); throughput = solves / wall time."""
+    P = oracle_workers(want)
+    pool = OraclePool(A, H, rhs, P)
+    try:
+        t0 = time.perf_counter()
+        res = pool.solves(range(P))
+        T = time.perf_counter() - t0
+    finally:
+        pool.close()
+    per = [r[0] for r in res]
+    return {"value": P / T, "unit": "solves/s", "cores": P, "kind": "oracle",
+            "sample": f"{P} whole FP64 oracle solves of the 128^3 system at once, one per single-threaded worker; "
+                      f"wall {T:.1f} s, median {statistics.median(per):.1f} s per solve",
+            "threads_per_worker": 1, **host_info()}
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, same workload, metric and config as the GPU arm: each
+    step is one whole oracle solve; the W warm-up and then the K timed solves run in a spawn
+    pool of single-threaded workers (one per core, bounded by host memory), so the timed region
+    is the wall time of the K solves and value = K / that time."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return
     A, H, rhs = build_inputs()
-    import oracle.kernels as K
-    from oracle.gmres import gmres_onereduce
-    from oracle.vcycle import vcycle
-    p = K.SmootherParams(smoother=K.HYBRID_ILU0, neumann_terms=2, ilu_terms_L=3, ilu_terms_U=3)
-    # warm-up: one full oracle solve gives its own iteration count for the workload
-    t0 = time.perf_counter()
-    full = gmres_onereduce(A, rhs[0], lambda v: vcycle(H, v, p), m=RESTART, rtol=RTOL, maxit=MAXIT)
-    t_full = time.perf_counter() - t0
-    for _ in range(max(0, args.warmup - 1)):
-        oracle_sample(A, H, rhs[0], 2)
-    per = []
-    ctx, cores = _single_thread()
-    with ctx:
-        for k in range(args.steps):
-            s, _ = oracle_sample(A, H, rhs[k % N_RHS], 3)
-            per.append(s)
-    s_step = statistics.mean(per)
-    value = 1.0 / (s_step * full.iters)
+    K, W = args.steps, args.warmup
+    P = oracle_workers(K)
+    pool = OraclePool(A, H, rhs, P)
+    try:
+        if W:
+            pool.solves(range(W))
+        t0 = time.perf_counter()
+        res = pool.solves(range(K))
+        T = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = K / T
+    per = [r[0] for r in res]
+    info = host_info()
     line = {"impl": "reference", "metric": "solves/s to rel-res 1e-8 (GMRES(50)+C-AMG, 128^3 pressure Poisson)",
-            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_iters": full.iters,
-                                                            "oracle_full_solve_s": t_full,
-                                                            "oracle_relres": full.relres_true},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step: 3 Arnoldi steps of the FP64 oracle on the full system; "
-                                       f"value = 1 / (s per step x {full.iters} steps)"},
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": T / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded lognormal-density 7-point FV pressure Poisson, b ~ U[-1,1])",
+            "config": main_config(A, H, world),
+            "results": {"oracle_iters": sorted(set(r[1] for r in res)), "max_relres_true": max(r[2] for r in res),
+                        "s_per_solve_median": statistics.median(per), "s_per_solve_max": max(per),
+                        "timed_wall_s": T},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": P, "kind": "oracle",
+                             "sample": f"{K} whole FP64 oracle solves (numpy/scipy, one thread each) on {P} "
+                                       f"concurrent workers; median {statistics.median(per):.1f} s per solve",
+                             **info},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -787,10 +938,17 @@ def run_profile_kernel(args):
         o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
         hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
         ss = torch.empty(1, dtype=torch.float64, device="cuda")
+        Vs = torch.empty(2 * (i + 2) * ld, dtype=torch.float32, device="cuda")
+        nsamg.split_basis(n, i + 1, V, ld, Vs, ld)
+        vin = torch.empty(n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         for _ in range(3):
             if kind == "gram":
                 nsamg.gram(n, i, V, ld, x, o)
+            elif kind == "gramsplit":
+                nsamg.gram_split(n, i, Vs, ld, x, o)
+            elif kind == "updatesplit":
+                nsamg.update_split(n, i, Vs, ld, x, 1.0, hc, vin, ss)
             else:
                 nsamg.update(n, i, V, ld, x, 1.0, hc, ss)
     torch.cuda.synchronize()
@@ -846,6 +1004,55 @@ def run_c3(args):
     print(json.dumps({"c3": res}))
 
 
+def run_c3_gpu_setup(nsamg, torch, edge: int) -> dict:
+    """192^3 graded 27-point Q1 operator (7,077,888 rows, 189,119,224 nnz): hierarchy built on the
+    GPU (nsamg_amg_build), then the FP32-V-cycle and FP64 flexible GMRES(30) solves with 2 + 2
+    l1-Jacobi sweeps (median of 3 after one warm-up); true residuals recomputed on the host with
+    scipy's FP64 product, FP32-V solution compared with the FP64 one."""
+    from workloads import rhs_uniform
+    from workloads.matrices import q1_27pt_graded
+    t0 = time.perf_counter()
+    A = q1_27pt_graded(edge, aspect=100.0, seed=SEED)
+    t_gen = time.perf_counter() - t0
+    b = rhs_uniform(A.shape[0], SEED)
+    db = torch.from_numpy(b).cuda()
+    opt = nsamg.amg_default_options(theta=0.25, coarse_max=512, seed=SEED, ilu_levels=0)
+    nsamg.amg_build(A, opt).close()  # warm-up build
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = nsamg.amg_build(A, opt)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    sizes = [g.level_info(l)["n"] for l in range(g.nlevels)]
+    res = {"workload": f"q1_27pt_graded_{edge}^3_aspect100_rcm", "n": int(A.shape[0]), "nnz": int(A.nnz),
+           "levels": sizes, "smoother": "l1_jacobi x2", "restart": 30, "rtol": RTOL, "host_matrix_gen_s": round(t_gen, 2),
+           "gpu_amg_build_s": round(t_setup, 3)}
+    xs = {}
+    for name, fp32 in (("fp32v", 1), ("fp64", 0)):
+        p = nsamg.default_params(smoother=nsamg.JACOBI_L1, pre_sweeps=2, post_sweeps=2, restart=30, vcycle_fp32=fp32)
+        h = g.setup_solver(p)
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.solve(h, db, x, RTOL, 2000)
+        ts = []
+        for _ in range(3):
+            x.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st = nsamg.solve(h, db, x, RTOL, 2000)
+            ts.append(time.perf_counter() - t1)
+        xh = x.cpu().numpy()
+        h.close()
+        rel = float(np.linalg.norm(b - A @ xh) / np.linalg.norm(b))
+        xs[name] = xh
+        res[name] = {"s_per_solve": statistics.median(ts), "iters": st["iters"], "restarts": st["restarts"],
+                     "relres_true_host_spmv": rel, "relres_reported": st["relres_true"],
+                     "converged": bool(st["converged"]) and rel <= RTOL}
+    g.close()
+    res["x_fp32v_vs_fp64_rel"] = float(np.linalg.norm(xs["fp32v"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    res["speedup_fp32v"] = res["fp64"]["s_per_solve"] / res["fp32v"]["s_per_solve"]
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -860,9 +1067,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
     ap.add_argument("--c3", action="store_true", help="run the 192^3 graded 27-point FP32-V-cycle case")
+    ap.add_argument("--skip-c3", action="store_true", help="leave the 192^3 case out of the default run")
     ap.add_argument("--c3-edge", type=int, default=C3_EDGE)
     ap.add_argument("--profile-kernel", choices=["spmv", "spmvcsr", "spmvsell", "l1spmv", "ilu", "gram", "update",
-                                                 "spmv32", "ilu32"],
+                                                 "gramsplit", "updatesplit", "spmv32", "ilu32"],
                     help="launch one kernel 3 times for a detailed ncu capture")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "nsamg":

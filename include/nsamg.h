@@ -100,12 +100,28 @@ typedef struct {
                             41, 14 or 22 (0 = 11). Every shape sums each row in the same order, so
                             the results do not depend on it. Ignored otherwise (the autotuner
                             picks the shape).                                                     */
+  int32_t krylov_fp64;   /* 0 (default): the Gram and update kernels (Algorithm 1 steps 6 and 12)
+                            form their i-dependent products in double-FP32 arithmetic (each FP64
+                            value split into two FP32 parts by integer operations, TwoProduct and
+                            TwoSum accumulation, Ogita-Rump-Oishi Dot2), accurate to ~2^-45 of
+                            sum |a_k b_k| per product sum, because B300 issues FP64 FMAs at ~1/80
+                            of its FP32 rate; vectors stay FP64 in memory, the vt . vt and vt . w
+                            products and all block/grid sums stay FP64, and blocks whose data
+                            leave the [2^-50, 2^60] magnitude window recompute in FP64.
+                            1: every product and sum in FP64.                                     */
+  int32_t stop_nrbe;     /* 0 (default): stop when ||b - A x|| / ||b|| <= rtol (eq. relres).
+                            1: stop when the norm-wise relative backward error
+                            beta(x) = ||b - A x|| / (||b|| + ||A||_inf ||x||) <= rtol (Sec. 3). Inside a
+                            restart cycle the implicit residual |g_{k+1}| is tested against
+                            rtol (||b|| + ||A||_inf ||x_0||) with x_0 the cycle's start (the only
+                            norm of x known before the x-update); the true residual at the cycle's
+                            end then decides with the exact beta(x), restarting if it fails.      */
 } nsamg_params;
 
 typedef struct {
   int32_t iters;          /* Arnoldi columns used, summed over restart cycles                   */
   int32_t restarts;       /* completed restart cycles after the first                           */
-  int32_t converged;      /* 1 if ||b - A x|| / ||b|| <= rtol                                   */
+  int32_t converged;      /* 1 if ||b - A x|| / ||b|| <= rtol (with stop_nrbe: nrbe <= rtol)    */
   int32_t status;         /* same value the call returned                                       */
   double relres_true;     /* ||b - A x|| / ||b|| from the final true residual (eq. relres)      */
   double relres_implicit; /* |g_{k+1}| / ||b|| from the Givens recurrence at exit               */
@@ -183,13 +199,48 @@ int nsamg_coarse_solve(nsamg_handle* h, const double* d_b, double* d_z);
  *                 n x i column-major block at d_V with leading dimension ldv (>= n) and vt is
  *                 column i of the same block (so the block holds i+1 columns). One pass over the
  *                 i+2 vectors, deterministic fixed-order reduction. 0 <= i < NSAMG_MAX_RESTART.
- *                 Uses library-owned device scratch (allocated on first use per device).
+ *                 The products with V_i are formed in double-FP32 arithmetic as in a solve with
+ *                 krylov_fp64 = 0 (accurate to ~2^-45 of sum |a_k b_k|); a block whose data lie
+ *                 outside the [2^-50, 2^60] magnitude window is computed in FP64.
  *   nsamg_update: given beta and h[0..i] (device), writes v_i = vt / beta in place of column i
  *                 and column i+1 = w / beta - sum_{j<=i} h_j v_j; returns ||column i+1||^2 in
- *                 *d_sumsq (device). */
+ *                 *d_sumsq (device). Double-FP32 products as nsamg_gram (rows outside the window
+ *                 in FP64).
+ *   nsamg_gram_fp64, nsamg_update_fp64: the same results with every product and sum in FP64
+ *                 (the kernels of a solve with krylov_fp64 = 1).
+ * All four use one library-owned device scratch per device (allocated on the first call): the
+ * Gram calls share one region and counter, the update calls another. Calls of the same family
+ * that overlap on the GPU (different streams, or threads without ordering) race and give wrong
+ * results, so serialise them. Errors: INVALID_ARG for n <= 0, i out of range, ldv < n, null
+ * pointers or beta = 0. */
 int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream);
 int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
                  double* d_sumsq, void* stream);
+int nsamg_gram_fp64(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream);
+int nsamg_update_fp64(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
+                      double* d_sumsq, void* stream);
+
+/* The split-basis kernels a solve with krylov_fp64 = 0 runs (Algorithm 1 steps 6-12 on its own
+ * basis layout), on caller data. The basis is stored as (hi, lo) float pairs, 8 bytes per entry
+ * (column j at d_Vs + 8 j lds bytes): hi = the first 24 significant bits of the FP64 value, lo
+ * the next 23 (|x - hi - lo| <= 2^-46 |x|; magnitudes below 2^-103 are stored as zero). Columns
+ * hold the unnormalised vectors vt_j.
+ *   nsamg_split_basis: column j of the FP64 block d_V (ldv) -> column j of d_Vs (lds), j < ncols.
+ *   nsamg_gram_split:  out[0..i] = vt_j . vt_i, out[i+1..2i+1] = vt_j . w for j = 0..i (raw
+ *                      products; a solve scales them by 1 / beta_j), double-FP32 per block and
+ *                      FP64 across blocks, deterministic; a block whose w lies outside the
+ *                      [2^-50, 2^60] window is computed in FP64 from the stored pairs.
+ *   nsamg_update_split: column i+1 = w / beta_i - sum_{j<=i} c_j vt_j with c_j (device, i+1
+ *                      doubles) the coefficients of the stored vectors (h_j / beta_j in a solve),
+ *                      stored as a pair; *d_sumsq (device) = its squared norm; d_vin (device, n
+ *                      doubles, may be NULL) receives its FP64 value.
+ * d_Vs and d_w must be 16-byte aligned and lds even (INVALID_ARG otherwise); 0 <= i <
+ * NSAMG_MAX_RESTART and the update writes column i+1, so the block needs i+2 columns. Scratch and
+ * serialisation as nsamg_gram / nsamg_update (the same two families). Asynchronous on `stream`. */
+int nsamg_split_basis(int64_t n, int ncols, const double* d_V, int64_t ldv, void* d_Vs, int64_t lds, void* stream);
+int nsamg_gram_split(int64_t n, int i, const void* d_Vs, int64_t lds, const double* d_w, double* d_out, void* stream);
+int nsamg_update_split(int64_t n, int i, void* d_Vs, int64_t lds, const double* d_w, double beta_i, const double* d_c,
+                       double* d_vin, double* d_sumsq, void* stream);
 
 /* Allocation-free variant of nsamg_gram (the paper has no counterpart; this is a service
  * to callers). Same arguments, same results: out[0..i] = [V_i, vt]^T vt, out[i+1..2i+1] =
@@ -216,6 +267,13 @@ int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const d
  * changes by at most 1e-15 relative (300 iterations at most); deterministic. Writes one double to
  * d_out on `stream` (asynchronous). 1 <= k <= NSAMG_MAX_RESTART, else INVALID_ARG. */
 int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream);
+
+/* Measurement probe (the paper has no counterpart): launches `blocks` x 256 threads, each
+ * running 8 independent FMA chains for `iters` rounds in FP64 (fp64 = 1) or FP32 (fp64 = 0), and
+ * stores one value per thread into d_sink (device, blocks x 256 elements of that type). Time the
+ * launch with events on `stream`; *fma_per_launch (host, may be NULL) receives the FMA count.
+ * Used to measure the FP64 and FP32 FMA rates that bound the FP64 and double-FP32 kernels. */
+int nsamg_fma_probe(int fp64, int64_t iters, int blocks, void* d_sink, void* stream, double* fma_per_launch);
 
 /* ---- batched solves of many independent systems ----------------------------------------
  * nsamg_batch_setup: `count` host hierarchies with the same number of levels (and either all or

@@ -22,6 +22,8 @@ struct BatchCtl {
   int active;       // systems still stepping in this cycle
   int running;      // systems not finished
   int cycles;
+  int stop_nrbe;    // 1: stop on the backward error instead of the relative residual
+  int pad;
 };
 
 struct BatchArgs {
@@ -302,8 +304,10 @@ __global__ void __launch_bounds__(kRedThreads) k_bupdate(BatchArgs a) {
       const double res = fabs(st->g[i + 1]);
       const double scale = st->bnorm > 0.0 ? st->bnorm : 1.0;
       st->relres_implicit = res / scale;
+      const double den = a.ctl->stop_nrbe ? st->bnorm + st->anorm_inf * st->xnorm : scale;
       const bool finite = isfinite(res) && isfinite(hsub) && isfinite(col[i]);
-      const int stop = (!finite) || res <= a.ctl->rtol * scale || hsub == 0.0 || k >= a.ctl->m || st->iters >= a.ctl->maxit;
+      const int stop = (!finite) || res <= a.ctl->rtol * (den > 0.0 ? den : 1.0) || hsub == 0.0 || k >= a.ctl->m ||
+                       st->iters >= a.ctl->maxit;
       if (!finite) st->status = -6;
       st->stop = stop;
       s_stop = stop;
@@ -431,8 +435,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bresid(BResidArgs ra) {
         st->relres_true = relres;
         const double den = st->bnorm + st->anorm_inf * sqrt(X2);
         st->nrbe = den > 0.0 ? sqrt(R2) / den : 0.0;
+        st->xnorm = sqrt(X2);
         const bool finite = isfinite(R2) && isfinite(st->bnorm);
-        const bool conv = finite && relres <= a.ctl->rtol;
+        const bool conv = finite && (a.ctl->stop_nrbe ? st->nrbe <= a.ctl->rtol : relres <= a.ctl->rtol);
         const bool err = !finite || st->status < 0;
         const bool no_progress = !ra.init && st->k == 0;
         const bool fin = no_progress || conv || err || st->iters >= a.ctl->maxit || st->cycles > a.ctl->maxit;

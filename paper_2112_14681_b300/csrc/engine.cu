@@ -79,6 +79,57 @@ void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Arg
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+template <typename... KArgs, typename... Args>
+void launch_k_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// The bulk-copy Gram's dynamic shared memory exceeds the 48 KB default: raise the limit once per
+// device (a host-side attribute; no allocation).
+std::mutex g_tma_mu;
+std::vector<char> g_tma_ready;
+cudaError_t gram_tma_prepare() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_tma_mu);
+  if ((int)g_tma_ready.size() <= dev) g_tma_ready.resize(dev + 1, 0);
+  if (g_tma_ready[dev]) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(k_gram_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gram_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_update_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_update_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gram_s, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_update_s, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) != cudaSuccess)
+    return e;
+  g_tma_ready[dev] = 1;
+  return cudaSuccess;
+}
+
+// The bulk-copy path needs every column start of V and w 16-byte aligned.
+bool gram_tma_aligned(const double* V, int64_t ldv, const double* w) {
+  return ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0 && (ldv & 1) == 0;
+}
+
 // ------------------------------------------------------------------------------------------
 // Device CSR
 // ------------------------------------------------------------------------------------------
@@ -512,14 +563,18 @@ struct nsamg_handle {
   // GMRES workspace
   int n = 0, m = 0;
   int64_t ld = 0;
-  double* V = nullptr;  // (m+1) columns
+  double* V = nullptr;  // (m+1) columns (FP64 basis: krylov_fp64 = 1, and batches)
+  float2* Vs = nullptr; // (m+1) columns of (hi, lo) pairs (split basis: krylov_fp64 = 0)
+  double* vin = nullptr;  // split basis: the FP64 residual / next V-cycle input
+  bool split = false;     // split basis in use
+  bool no_split = false;  // batches keep the FP64 basis
   double* Z = nullptr;  // m columns (FP64 V-cycle)
   float* Z32 = nullptr; // m columns (FP32 V-cycle)
   double* w = nullptr;
   GState* st = nullptr;
   GState* h_st = nullptr;  // pinned host mirror
   Scratch scr{};
-  int gram_blocks = 0, update_blocks = 0;
+  int gram_blocks = 0, update_blocks = 0, stream_blocks = 0;  // stream_blocks: x-update, column 0
   int64_t partial_cap = 0;
   // graph
   cudaGraphExec_t exec = nullptr;
@@ -996,9 +1051,13 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   const int* sel = &h->st->i;
   Ctx c{s, skip};
   VRef<const double> b;
-  b.p = h->V;
-  b.sel = sel;
-  b.ld = h->ld;
+  if (h->split) {  // split basis: the V-cycle input vt_i is the FP64 vector vin
+    b.p = h->vin;
+  } else {
+    b.p = h->V;
+    b.sel = sel;
+    b.ld = h->ld;
+  }
   if (!h->fp32) {
     VRef<double> z;
     z.p = h->Z;
@@ -1029,11 +1088,13 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   GramArgs ga{};
   ga.n = h->n;
   ga.V = h->V;
+  ga.Vs = h->Vs;
   ga.ldv = h->ld;
   ga.w = h->w;
   ga.st = h->st;
   ga.scr = h->scr;
-  launch_k(k_gram, h->gram_blocks, kGramThreads, s, ga);
+  if (h->split) launch_k_smem(k_gram_s, h->gram_blocks, kGramTmaThreads, kGramTmaSmem, s, ga);
+  else launch_k(k_gram, h->gram_blocks, kGramThreads, s, ga);
   g_launches += 2;
   UpdateArgs ua{};
   ua.n = h->n;
@@ -1045,13 +1106,16 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ua.scr = h->scr;
   ua.scr.ticket = h->scr.ticket + 1;
   ua.v32 = h->fp32 ? h->lv32[0].b : nullptr;
-  launch_k(k_update, h->update_blocks, kRedThreads, s, ua);
+  ua.Vs = h->Vs;
+  ua.vin = h->fp32 ? nullptr : h->vin;
+  if (h->split) launch_k_smem(k_update_s, h->update_blocks, kGramTmaThreads, kGramTmaSmem, s, ua);
+  else launch_k(k_update, h->update_blocks, kRedThreads, s, ua);
 }
 
 void enqueue_xupdate(nsamg_handle* h, cudaStream_t s) {
   ++g_launches;
-  if (h->fp32) launch_k(k_xupdate<float>, h->update_blocks, kRedThreads, s, h->n, h->Z32, h->ld, h->st);
-  else launch_k(k_xupdate<double>, h->update_blocks, kRedThreads, s, h->n, h->Z, h->ld, h->st);
+  if (h->fp32) launch_k(k_xupdate<float>, h->stream_blocks, kRedThreads, s, h->n, h->Z32, h->ld, h->st);
+  else launch_k(k_xupdate<double>, h->stream_blocks, kRedThreads, s, h->n, h->Z, h->ld, h->st);
 }
 
 void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long co, unsigned long long ci) {
@@ -1061,8 +1125,8 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
   ra.rp = A.rp;
   ra.ci = A.ci;
   ra.v = A.v;
-  ra.r = h->V;
-  ra.r32 = h->fp32 ? h->lv32[0].b : nullptr;
+  ra.r = h->split ? h->vin : h->V;
+  ra.r32 = (h->fp32 && !h->split) ? h->lv32[0].b : nullptr;
   ra.st = h->st;
   ra.init = init;
   ra.cond_outer = co;
@@ -1079,6 +1143,16 @@ void enqueue_resid(nsamg_handle* h, cudaStream_t s, int init, unsigned long long
     case 8: launch_k(k_resid<8>, nb, kRedThreads, s, ra); break;
     case 16: launch_k(k_resid<16>, nb, kRedThreads, s, ra); break;
     default: launch_k(k_resid<32>, nb, kRedThreads, s, ra); break;
+  }
+  if (h->split) {  // column 0 of the next cycle (returns at once when the solve is done)
+    Col0Args c0{};
+    c0.n = h->n;
+    c0.r = h->vin;
+    c0.r32 = h->fp32 ? h->lv32[0].b : nullptr;
+    c0.col = h->Vs;
+    c0.st = h->st;
+    ++g_launches;
+    launch_k(k_col0, h->stream_blocks, kRedThreads, s, c0);
   }
 }
 
@@ -1252,6 +1326,8 @@ int check_params(const nsamg_params& p) {
       p.sell_shape != 22)
     return fail(NSAMG_ERR_INVALID_ARG, "sell_shape must be 0, 11, 21, 41, 14 or 22");
   if (p.fuse_tail != 0 && p.fuse_tail != 1) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0 or 1");
+  if (p.krylov_fp64 != 0 && p.krylov_fp64 != 1) return fail(NSAMG_ERR_INVALID_ARG, "krylov_fp64 must be 0 or 1");
+  if (p.stop_nrbe != 0 && p.stop_nrbe != 1) return fail(NSAMG_ERR_INVALID_ARG, "stop_nrbe must be 0 or 1");
   return NSAMG_OK;
 }
 
@@ -1438,6 +1514,10 @@ void release_levels(std::vector<Level<T>>& lvs) {
   lvs.clear();
 }
 
+// A device buffer of at least n doubles the autotuner may overwrite: the Krylov basis (FP64 or
+// split, whichever the handle holds).
+double* tuning_scratch(nsamg_handle* h) { return h->split ? reinterpret_cast<double*>(h->Vs) : h->V; }
+
 // GMRES workspace of a handle or solver context: V (m+1 columns), Z (m columns), w, the device
 // state and reduction scratch; leading dimension padded to 64 entries.
 int alloc_workspace(nsamg_handle* h) {
@@ -1445,7 +1525,13 @@ int alloc_workspace(nsamg_handle* h) {
   h->n = h->lv[0].n;
   h->m = h->p.restart;
   h->ld = ((int64_t)h->n + 63) / 64 * 64;
-  if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
+  h->split = !h->p.krylov_fp64 && !h->no_split;
+  if (h->split) {
+    if ((rc = alloc_vec(&h->Vs, h->ld * (h->m + 1)))) return rc;
+    if ((rc = alloc_vec(&h->vin, h->ld))) return rc;
+  } else {
+    if ((rc = alloc_vec(&h->V, h->ld * (h->m + 1)))) return rc;
+  }
   if (h->fp32) {
     if ((rc = alloc_vec(&h->Z32, h->ld * h->m))) return rc;
   } else {
@@ -1457,15 +1543,17 @@ int alloc_workspace(nsamg_handle* h) {
   CK(cudaMallocHost(&h->h_st, sizeof(GState)));
   int sms = 148;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  h->gram_blocks = 2 * sms;
-  h->update_blocks = 8 * sms;
+  h->gram_blocks = h->split ? kDfGramBlocksPerSM * sms : 2 * sms;
+  CK(gram_tma_prepare());
+  h->update_blocks = h->split ? sms : 8 * sms;
+  h->stream_blocks = 8 * sms;
   const int resid_blocks = blocks_for((int64_t)h->n * 32);
   h->partial_cap = std::max<int64_t>({(int64_t)h->gram_blocks * 2 * (kMaxM + 1), (int64_t)h->update_blocks,
                                       3 * (int64_t)resid_blocks});
   CK(cudaMalloc(&h->scr.partials, sizeof(double) * h->partial_cap));
   CK(cudaMalloc(&h->scr.ticket, sizeof(unsigned) * 4));
   CK(cudaMemset(h->scr.ticket, 0, sizeof(unsigned) * 4));
-  h->ctx_bytes = sizeof(double) * h->ld * (h->m + 2) + (h->fp32 ? sizeof(float) : sizeof(double)) * h->ld * h->m +
+  h->ctx_bytes = sizeof(double) * h->ld * (h->m + 2 + (h->split ? 1 : 0)) + (h->fp32 ? sizeof(float) : sizeof(double)) * h->ld * h->m +
                  sizeof(GState) + sizeof(double) * h->partial_cap;
   return NSAMG_OK;
 }
@@ -1570,6 +1658,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   int rc = check_params(p);
   if (rc) return rc;
   h->p = p;
+  h->no_split = bi != nullptr;
   if (!H || H->nlevels < 1 || !H->levels) return fail(NSAMG_ERR_INVALID_ARG, "empty hierarchy");
   CK(cudaGetDevice(&h->device));
   if (stream) {
@@ -1644,7 +1733,7 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
   if (bi && (rc = setup_batch_data(h, *bi))) return rc;
   // Threads per row: fixed by the caller or tuned on the device.
-  if ((rc = tune_levels(h->lv, h->V, h->w, p.spmv_group, p.sell_shape, h->stream))) return rc;
+  if ((rc = tune_levels(h->lv, tuning_scratch(h), h->w, p.spmv_group, p.sell_shape, h->stream))) return rc;
   if (h->fp32) {
     // FP32 scratch for tuning: the finest level's work vectors are the largest
     if ((rc = tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, p.sell_shape, h->stream))) return rc;
@@ -1696,6 +1785,15 @@ int clone_level_vectors(const std::vector<Level<T>>& src, std::vector<Level<T>>&
   return NSAMG_OK;
 }
 
+// Device bytes of the per-context level vectors (six per level, in the V-cycle's precision):
+// what clone_context adds to a context's workspace, and what the server reserves for it.
+size_t level_vector_bytes(const nsamg_handle* h) {
+  size_t v = 0;
+  for (auto& L : h->lv) v += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
+  for (auto& L : h->lv32) v += 6 * sizeof(float) * (size_t)L.n;
+  return v;
+}
+
 int clone_context(nsamg_handle* parent, nsamg_handle** out) {
   int rc;
   *out = nullptr;
@@ -1722,10 +1820,7 @@ int clone_context(nsamg_handle* parent, nsamg_handle** out) {
   h->anorm_inf = parent->anorm_inf;
   if (cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(NSAMG_ERR_CUDA, "state"));
-  size_t vec_bytes = 0;
-  for (auto& L : h->lv) vec_bytes += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
-  for (auto& L : h->lv32) vec_bytes += 6 * sizeof(float) * (size_t)L.n;
-  h->ctx_bytes += vec_bytes;
+  h->ctx_bytes += level_vector_bytes(h);
   if ((rc = build_tail_any(h))) return bail(rc);
   if ((rc = finish_graph(h))) return bail(rc);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(fail(NSAMG_ERR_CUDA, "sync"));
@@ -1870,6 +1965,7 @@ int solve_batch_impl(nsamg_handle* h, const double* d_b, double* d_x, double rto
   c->maxit = maxit;
   c->m = h->m;
   c->t_exact = h->p.t_exact;
+  c->stop_nrbe = h->p.stop_nrbe;
   CK(cudaMemcpyAsync(B->d_ctl, c, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
   if (h->exec) {
     CK(cudaGraphLaunch(h->exec, s));
@@ -1937,6 +2033,8 @@ void destroy_impl(nsamg_handle* h) {
     cudaFree(h->coarse_inv32);
   }
   cudaFree(h->V);
+  cudaFree(h->Vs);
+  cudaFree(h->vin);
   cudaFree(h->Z);
   cudaFree(h->Z32);
   cudaFree(h->w);
@@ -1968,6 +2066,10 @@ void to64(nsamg_handle* h, const float* a, double* b, int64_t n) {
 std::mutex g_scr_mu;
 std::vector<Scratch> g_scr;
 
+// Per-device scratch of the standalone Gram / update entry points: the Gram family uses the
+// first kStandaloneGramPartials doubles and ticket 0, the update family the rest and ticket 1.
+constexpr int64_t kStandaloneGramPartials = 512 * 2 * (kMaxM + 1);
+
 int standalone_scratch(Scratch* out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1976,7 +2078,7 @@ int standalone_scratch(Scratch* out) {
   if (!g_scr[dev].partials) {
     int sms = 148;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t cap = std::max<int64_t>(2 * sms * 2 * (kMaxM + 1), 8 * sms);
+    const int64_t cap = kStandaloneGramPartials + 8 * (int64_t)sms;
     CK(cudaMalloc(&g_scr[dev].partials, sizeof(double) * cap));
     CK(cudaMalloc(&g_scr[dev].ticket, sizeof(unsigned) * 4));
     CK(cudaMemset(g_scr[dev].ticket, 0, sizeof(unsigned) * 4));
@@ -2016,7 +2118,7 @@ int noalloc_scratch(Scratch* out, int* blocks) {
   }
   out->ticket = (unsigned*)base;
   out->partials = (double*)((unsigned char*)base + 256);
-  *blocks = std::min(2 * sms, kNoAllocBlocks);
+  *blocks = std::min(kDfGramBlocksPerSM * sms, kNoAllocBlocks);
   return NSAMG_OK;
 }
 
@@ -2036,6 +2138,7 @@ int solve_impl(nsamg_handle* h, const double* d_b, double* d_x, double rtol, int
   hs->maxit = maxit;
   hs->m = h->m;
   hs->t_exact = h->p.t_exact;
+  hs->stop_nrbe = h->p.stop_nrbe;
   CK(cudaMemcpyAsync(h->st, hs, offsetof(GState, i), cudaMemcpyHostToDevice, s));
   if (h->exec) {
     CK(cudaGraphLaunch(h->exec, s));
@@ -2157,6 +2260,29 @@ int level_dispatch(nsamg_handle* h, int which, int level, int backward, int x_is
 
 // ==========================================================================================
 // C ABI
+// ------------------------------------------------------------------------------------------
+// FMA issue-rate probe (measurement only): every thread runs kProbeChains independent chains
+// a <- a * b + c for `iters` rounds and stores their sum, so no chain can be removed. FMAs per
+// launch = blocks * threads * kProbeChains * iters.
+// ------------------------------------------------------------------------------------------
+constexpr int kProbeChains = 8;
+constexpr int kProbeThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) k_fma_probe(int64_t iters, T b, T c, T* sink) {
+  T a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = (T)(threadIdx.x + k);
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], b, c);
+  }
+  T t = (T)0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) t += a[k];
+  sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 // ==========================================================================================
 extern "C" {
 
@@ -2176,6 +2302,8 @@ void nsamg_default_params(nsamg_params* p) {
   p->spmv_group = 0;
   p->sell_shape = 0;
   p->fuse_tail = 0;
+  p->krylov_fp64 = 0;
+  p->stop_nrbe = 0;
 }
 
 int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, void* cuda_stream, nsamg_handle** out) {
@@ -2290,7 +2418,9 @@ int nsamg_coarse_solve(nsamg_handle* h, const double* d_b, double* d_z) {
   return level_dispatch(h, 5, nlev(h) - 1, 0, 0, d_b, nullptr, d_z);
 }
 
-int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream) {
+namespace {
+int gram_standalone(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream,
+                    bool fp64) {
   if (n <= 0 || i < 0 || i >= kMaxM || !d_V || !d_w || !d_out || ldv < n) return fail(NSAMG_ERR_INVALID_ARG, "bad gram arguments");
   Scratch scr;
   int rc = standalone_scratch(&scr);
@@ -2307,7 +2437,126 @@ int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d
   ga.i_standalone = i;
   ga.out = d_out;
   ga.scr = scr;
-  launch_k(k_gram, 2 * sms, kGramThreads, (cudaStream_t)stream, ga);
+  if (fp64) launch_k(k_gram, 2 * sms, kGramThreads, (cudaStream_t)stream, ga);
+  else if (gram_tma_aligned(d_V, ldv, d_w)) {
+    CK(gram_tma_prepare());
+    launch_k_smem(k_gram_tma<true>, kDfGramBlocksPerSM * sms, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ga);
+  } else
+    launch_k(k_gram_df<true>, kDfGramBlocksPerSM * sms, kGramThreads, (cudaStream_t)stream, ga);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int update_standalone(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
+                      double* d_sumsq, void* stream, bool fp64) {
+  if (n <= 0 || i < 0 || i >= kMaxM || !d_V || !d_w || !d_h || !d_sumsq || ldv < n || !(beta != 0.0))
+    return fail(NSAMG_ERR_INVALID_ARG, "bad update arguments");
+  Scratch scr;
+  int rc = standalone_scratch(&scr);
+  if (rc) return rc;
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  UpdateArgs ua{};
+  ua.n = n;
+  ua.V = d_V;
+  ua.ldv = ldv;
+  ua.w = d_w;
+  ua.st = nullptr;
+  ua.i_standalone = i;
+  ua.invbeta_standalone = 1.0 / beta;
+  ua.h_standalone = d_h;
+  ua.sumsq_out = d_sumsq;
+  ua.scr.partials = scr.partials + kStandaloneGramPartials;
+  ua.scr.ticket = scr.ticket + 1;
+  if (fp64) launch_k(k_update, 8 * sms, kRedThreads, (cudaStream_t)stream, ua);
+  else if (gram_tma_aligned(d_V, ldv, d_w)) {
+    CK(gram_tma_prepare());
+    launch_k_smem(k_update_tma<true>, sms, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ua);
+  } else
+    launch_k(k_update_df<true>, kDfUpdateBlocksPerSM * sms, kRedThreads, (cudaStream_t)stream, ua);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+}  // namespace
+
+int nsamg_gram(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream) {
+  return gram_standalone(n, i, d_V, ldv, d_w, d_out, stream, false);
+}
+
+int nsamg_gram_fp64(int64_t n, int i, const double* d_V, int64_t ldv, const double* d_w, double* d_out, void* stream) {
+  return gram_standalone(n, i, d_V, ldv, d_w, d_out, stream, true);
+}
+
+int nsamg_split_basis(int64_t n, int ncols, const double* d_V, int64_t ldv, void* d_Vs, int64_t lds, void* stream) {
+  if (n <= 0 || ncols < 1 || !d_V || !d_Vs || ldv < n || lds < n)
+    return fail(NSAMG_ERR_INVALID_ARG, "bad split-basis arguments");
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  launch_k(k_split_cols, 8 * sms, kRedThreads, (cudaStream_t)stream, n, ncols, d_V, ldv, (float2*)d_Vs, lds);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+// The split-basis kernels need 16-byte aligned columns and w (the solve allocates them so).
+static bool split_aligned(const void* Vs, int64_t lds, const void* w) {
+  return ((reinterpret_cast<uintptr_t>(Vs) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0 && (lds & 1) == 0;
+}
+
+int nsamg_gram_split(int64_t n, int i, const void* d_Vs, int64_t lds, const double* d_w, double* d_out, void* stream) {
+  if (n <= 0 || i < 0 || i >= kMaxM || !d_Vs || !d_w || !d_out || lds < n)
+    return fail(NSAMG_ERR_INVALID_ARG, "bad gram arguments");
+  if (!split_aligned(d_Vs, lds, d_w))
+    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned and lds even");
+  Scratch scr;
+  int rc = standalone_scratch(&scr);
+  if (rc) return rc;
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(gram_tma_prepare());
+  GramArgs ga{};
+  ga.n = n;
+  ga.Vs = (const float2*)d_Vs;
+  ga.ldv = lds;
+  ga.w = d_w;
+  ga.st = nullptr;
+  ga.i_standalone = i;
+  ga.out = d_out;
+  ga.scr = scr;
+  launch_k_smem(k_gram_s, kDfGramBlocksPerSM * sms, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ga);
+  CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_update_split(int64_t n, int i, void* d_Vs, int64_t lds, const double* d_w, double beta_i, const double* d_c,
+                       double* d_vin, double* d_sumsq, void* stream) {
+  if (n <= 0 || i < 0 || i >= kMaxM || !d_Vs || !d_w || !d_c || !d_sumsq || lds < n || !(beta_i != 0.0))
+    return fail(NSAMG_ERR_INVALID_ARG, "bad update arguments");
+  if (!split_aligned(d_Vs, lds, d_w))
+    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned and lds even");
+  Scratch scr;
+  int rc = standalone_scratch(&scr);
+  if (rc) return rc;
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(gram_tma_prepare());
+  UpdateArgs ua{};
+  ua.n = n;
+  ua.Vs = (float2*)d_Vs;
+  ua.ldv = lds;
+  ua.w = d_w;
+  ua.st = nullptr;
+  ua.i_standalone = i;
+  ua.invbeta_standalone = 1.0 / beta_i;
+  ua.coef_standalone = d_c;
+  ua.vin = d_vin;
+  ua.sumsq_out = d_sumsq;
+  ua.scr.partials = scr.partials + kStandaloneGramPartials;
+  ua.scr.ticket = scr.ticket + 1;
+  launch_k_smem(k_update_s, sms, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ua);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
@@ -2333,36 +2582,23 @@ int nsamg_gram_noalloc(int64_t n, int i, const double* d_V, int64_t ldv, const d
   ga.i_standalone = i;
   ga.out = d_out;
   ga.scr = scr;
-  launch_k(k_gram, blocks, kGramThreads, (cudaStream_t)stream, ga);
+  if (gram_tma_aligned(d_V, ldv, d_w)) {
+    CK(gram_tma_prepare());
+    launch_k_smem(k_gram_tma<true>, blocks, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ga);
+  } else
+    launch_k(k_gram_df<true>, blocks, kGramThreads, (cudaStream_t)stream, ga);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }
 
 int nsamg_update(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
                  double* d_sumsq, void* stream) {
-  if (n <= 0 || i < 0 || i >= kMaxM || !d_V || !d_w || !d_h || !d_sumsq || ldv < n || !(beta != 0.0))
-    return fail(NSAMG_ERR_INVALID_ARG, "bad update arguments");
-  Scratch scr;
-  int rc = standalone_scratch(&scr);
-  if (rc) return rc;
-  int dev = 0, sms = 148;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  UpdateArgs ua{};
-  ua.n = n;
-  ua.V = d_V;
-  ua.ldv = ldv;
-  ua.w = d_w;
-  ua.st = nullptr;
-  ua.i_standalone = i;
-  ua.invbeta_standalone = 1.0 / beta;
-  ua.h_standalone = d_h;
-  ua.sumsq_out = d_sumsq;
-  ua.scr = scr;
-  ua.scr.ticket = scr.ticket + 1;
-  launch_k(k_update, 8 * sms, kRedThreads, (cudaStream_t)stream, ua);
-  CK(cudaGetLastError());
-  return NSAMG_OK;
+  return update_standalone(n, i, d_V, ldv, d_w, beta, d_h, d_sumsq, stream, false);
+}
+
+int nsamg_update_fp64(int64_t n, int i, double* d_V, int64_t ldv, const double* d_w, double beta, const double* d_h,
+                      double* d_sumsq, void* stream) {
+  return update_standalone(n, i, d_V, ldv, d_w, beta, d_h, d_sumsq, stream, true);
 }
 
 int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_params* p, void* cuda_stream,
@@ -2480,6 +2716,18 @@ int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream) 
   ++g_launches;
   launch_k(k_sknorm_matrix, 1, kSkThreads, (cudaStream_t)stream, d_L, ld, k, d_out);
   CK(cudaGetLastError());
+  return NSAMG_OK;
+}
+
+int nsamg_fma_probe(int fp64, int64_t iters, int blocks, void* d_sink, void* stream, double* fma_per_launch) {
+  if ((fp64 != 0 && fp64 != 1) || iters < 1 || blocks < 1 || !d_sink)
+    return fail(NSAMG_ERR_INVALID_ARG, "nsamg_fma_probe: bad arguments");
+  if (fp64)
+    k_fma_probe<double><<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, 0.999999, 1e-7, (double*)d_sink);
+  else
+    k_fma_probe<float><<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, 0.999999f, 1e-7f, (float*)d_sink);
+  CK(cudaGetLastError());
+  if (fma_per_launch) *fma_per_launch = (double)blocks * kProbeThreads * kProbeChains * (double)iters;
   return NSAMG_OK;
 }
 
@@ -2622,12 +2870,9 @@ void server_collect(nsamg_server* S) {
   }
 }
 
-size_t context_need(nsamg_handle* hier) {
-  size_t v = hier->ctx_bytes;
-  for (auto& L : hier->lv) v += L.dinv ? 6 * sizeof(double) * (size_t)L.n : 0;
-  for (auto& L : hier->lv32) v += 6 * sizeof(float) * (size_t)L.n;
-  return v;
-}
+// Bytes a new context of `hier` will hold: its workspace (the parent's, same parameters) plus its
+// level vectors, by the same formula clone_context uses.
+size_t context_need(nsamg_handle* hier) { return hier->ctx_bytes + level_vector_bytes(hier); }
 
 void finish_request(nsamg_server* S, ServerReq& r, int state, int status) {
   r.state = state;
@@ -2698,6 +2943,8 @@ bool server_try_start(nsamg_server* S, std::unique_lock<std::mutex>& lk) {
       S->cv.notify_all();
       return true;
     }
+    // the reservation becomes the context's own size (equal by construction; recorded as the
+    // context's so that eviction subtracts exactly what was added)
     S->used += c->ctx_bytes;
     S->used -= need;
     S->ctxs.push_back(ServerCtx{c, hier, false, 0});
@@ -2721,6 +2968,7 @@ bool server_try_start(nsamg_server* S, std::unique_lock<std::mutex>& lk) {
   hs->maxit = r->maxit;
   hs->m = h->m;
   hs->t_exact = h->p.t_exact;
+  hs->stop_nrbe = h->p.stop_nrbe;
   cudaEvent_t ready = r->ready;
   lk.unlock();
   cudaStream_t st = h->stream;

@@ -498,7 +498,7 @@ struct GState {
   int maxit;
   int m;
   int t_exact;
-  int pad0;
+  int stop_nrbe;  // 1: stop on the backward error nrbe <= rtol instead of the relative residual
   // loop control
   int i;          // current Arnoldi step within the cycle (column index of vt)
   int k;          // columns completed in this cycle
@@ -515,6 +515,9 @@ struct GState {
   double relres_implicit;
   double anorm_inf;   // ||A||_inf of the finest operator (set at setup)
   double nrbe;        // ||r|| / (||b|| + ||A||_inf ||x||) of the last true residual
+  double xnorm;       // ||x|| at the last true residual (the start of the current cycle)
+  double rnorm;       // ||b - A x|| at the last true residual
+  double r0_scale;    // split basis: column 0 holds r / r0_scale (r0_scale an exact power of two)
   double lsum;        // sum of squares of the L entries of the current cycle
   double orth_loss;   // sqrt(2 lsum): ||I - V^T V||_F of the last cycle (diagonal terms ~ eps)
   double sk_norm;     // ||S_k||_2, S_k = (I + L^T)^-1 L^T, of the last cycle

@@ -1509,7 +1509,7 @@ int dev_setup_impl(nsamg_amg* g, const nsamg_params* pp, void* stream, nsamg_han
   SK(alloc_workspace(h));
   h->anorm_inf = anorm;
   CK(cudaMemcpy(&h->st->anorm_inf, &h->anorm_inf, sizeof(double), cudaMemcpyHostToDevice));
-  SK(tune_levels(h->lv, h->V, h->w, p.spmv_group, p.sell_shape, s));
+  SK(tune_levels(h->lv, tuning_scratch(h), h->w, p.spmv_group, p.sell_shape, s));
   if (h->fp32) SK(tune_levels(h->lv32, h->lv32[0].t1, h->lv32[0].t2, p.spmv_group, p.sell_shape, s));
   CK(cudaStreamSynchronize(s));
   SK(build_tail_any(h));

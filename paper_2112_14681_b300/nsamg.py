@@ -43,7 +43,8 @@ class HierarchyDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("smoother", "neumann_terms", "ilu_terms_L", "ilu_terms_U", "pre_sweeps",
                                                "post_sweeps", "coarse_sweeps", "restart", "vcycle_fp32", "t_exact",
-                                               "use_graph", "spmv_group", "fuse_tail", "sell_shape")]
+                                               "use_graph", "spmv_group", "fuse_tail", "sell_shape", "krylov_fp64",
+                                               "stop_nrbe")]
 
 
 class AmgOptions(ctypes.Structure):
@@ -66,8 +67,9 @@ EXPORTS = [
     "nsamg_default_params", "nsamg_setup_hierarchy", "nsamg_solve", "nsamg_solve_host", "nsamg_apply_vcycle",
     "nsamg_num_levels", "nsamg_level_size", "nsamg_level_group", "nsamg_level_spmv", "nsamg_level_residual",
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
-    "nsamg_update", "nsamg_destroy", "nsamg_context_create", "nsamg_status_str", "nsamg_last_error",
-    "nsamg_launches_per_step",
+    "nsamg_update", "nsamg_gram_fp64", "nsamg_update_fp64", "nsamg_split_basis", "nsamg_gram_split",
+    "nsamg_update_split", "nsamg_destroy", "nsamg_context_create", "nsamg_status_str", "nsamg_last_error",
+    "nsamg_launches_per_step", "nsamg_fma_probe",
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
     "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
@@ -104,6 +106,11 @@ def load(path: str = LIB_PATH):
         "nsamg_coarse_solve": (i32, [vp, vp, vp]),
         "nsamg_gram": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_update": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
+        "nsamg_gram_fp64": (i32, [i64, i32, vp, i64, vp, vp, vp]),
+        "nsamg_split_basis": (i32, [i64, i32, vp, i64, vp, i64, vp]),
+        "nsamg_gram_split": (i32, [i64, i32, vp, i64, vp, vp, vp]),
+        "nsamg_update_split": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp, vp]),
+        "nsamg_update_fp64": (i32, [i64, i32, vp, i64, vp, f64, vp, vp, vp]),
         "nsamg_gram_noalloc": (i32, [i64, i32, vp, i64, vp, vp, vp]),
         "nsamg_batch_setup": (i32, [ctypes.POINTER(HierarchyDesc), i32, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]),
         "nsamg_batch_solve": (i32, [vp, vp, vp, f64, i32, ctypes.POINTER(Stats)]),
@@ -130,6 +137,7 @@ def load(path: str = LIB_PATH):
         "nsamg_destroy": (None, [vp]),
         "nsamg_context_create": (i32, [vp, ctypes.POINTER(vp)]),
         "nsamg_launches_per_step": (i32, [vp]),
+        "nsamg_fma_probe": (i32, [i32, i64, i32, vp, vp, ctypes.POINTER(f64)]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
         "nsamg_last_error": (ctypes.c_char_p, []),
     }
@@ -379,6 +387,56 @@ def gram_noalloc(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
 
 def update(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
     _check(load().nsamg_update(int(n), int(i), _ptr(V), int(ldv), _ptr(w), float(beta), _ptr(h), _ptr(sumsq), stream))
+
+
+def split_basis(n: int, ncols: int, V, ldv: int, Vs, lds: int, stream=None) -> None:
+    """FP64 columns -> (hi, lo) float pairs (the layout of a solve's basis); Vs: any contiguous
+    device buffer of at least 8 * lds * ncols bytes (e.g. a float32 tensor of 2 * lds * ncols)."""
+    _check(load().nsamg_split_basis(int(n), int(ncols), _ptr(V), int(ldv), _ptr(Vs), int(lds), stream))
+
+
+def gram_split(n: int, i: int, Vs, lds: int, w, out, stream=None) -> None:
+    """Raw products vt_j . vt_i and vt_j . w (j <= i) on the split basis (a solve's Gram kernel)."""
+    _check(load().nsamg_gram_split(int(n), int(i), _ptr(Vs), int(lds), _ptr(w), _ptr(out), stream))
+
+
+def update_split(n: int, i: int, Vs, lds: int, w, beta_i: float, c, vin, sumsq, stream=None) -> None:
+    """Column i+1 = w / beta_i - sum_j c_j vt_j on the split basis (a solve's update kernel)."""
+    _check(load().nsamg_update_split(int(n), int(i), _ptr(Vs), int(lds), _ptr(w), float(beta_i), _ptr(c),
+                                     None if vin is None else _ptr(vin), _ptr(sumsq), stream))
+
+
+def gram_fp64(n: int, i: int, V, ldv: int, w, out, stream=None) -> None:
+    """gram() with every product and sum in FP64."""
+    _check(load().nsamg_gram_fp64(int(n), int(i), _ptr(V), int(ldv), _ptr(w), _ptr(out), stream))
+
+
+def update_fp64(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=None) -> None:
+    """update() with every product and sum in FP64."""
+    _check(load().nsamg_update_fp64(int(n), int(i), _ptr(V), int(ldv), _ptr(w), float(beta), _ptr(h), _ptr(sumsq),
+                                    stream))
+
+
+def fma_rate(fp64: bool, iters: int = 1 << 16, blocks_per_sm: int = 8, reps: int = 5) -> float:
+    """FMA/s of the current device in FP64 or FP32 (nsamg_fma_probe, best of `reps` launches
+    timed with CUDA events after one warm-up launch)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * blocks_per_sm
+    sink = torch.empty(blocks * 256, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    cnt = ctypes.c_double()
+    lib = load()
+    _check(lib.nsamg_fma_probe(int(bool(fp64)), int(iters), blocks, _ptr(sink), s.cuda_stream, ctypes.byref(cnt)))
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(lib.nsamg_fma_probe(int(bool(fp64)), int(iters), blocks, _ptr(sink), s.cuda_stream, None))
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return cnt.value / best
 
 
 def sknorm(L, k: int | None = None, out=None, stream=None) -> float:

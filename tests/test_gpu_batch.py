@@ -86,6 +86,51 @@ def test_batch_solve_matches_oracle_per_system(fp32, smoother, graph):
         assert 0.0 < st["sk_norm"] <= st["orth_loss"] < 1e-6
 
 
+def test_batch_fp32v_solution_matches_fp64_oracle():
+    """Mixed precision (FP32 V-cycle inside FP64 flexible GMRES): every system's x within 1e-6
+    relative of the FP64 oracle's x. Both solve to rtol 1e-10, so the difference measures the
+    mixed-precision error rather than the kappa * rtol band that any two solutions meeting
+    rtol 1e-8 may differ by."""
+    S = systems()
+    m = 30
+    p = nsamg.default_params(vcycle_fp32=1, restart=m)
+    with nsamg.batch_setup([H for _, H, _ in S], p) as h:
+        off = h.offsets
+        b = np.concatenate([bb for _, _, bb in S])
+        x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+        stats = nsamg.batch_solve(h, dev(b), x, rtol=1e-10, maxit=400)
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy()
+    for k, (A, H, bb) in enumerate(S):
+        ref = gmres_onereduce(A, bb, lambda v: ovcycle(H, v, oparams(p)), m=m, rtol=1e-10)
+        xs = xg[off[k]:off[k + 1]]
+        assert stats[k]["converged"] == 1
+        assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6, k
+
+
+def test_batch_stops_on_backward_error():
+    """stop_nrbe = 1 in a batch: each system stops on beta(x) <= rtol (Sec. 3) like the oracle's
+    one-reduce GMRES with the same stop (iterations within 1, beta(x) recomputed on the host)."""
+    S = systems()
+    m = 6
+    p = nsamg.default_params(restart=m, stop_nrbe=1)
+    with nsamg.batch_setup([H for _, H, _ in S], p) as h:
+        off = h.offsets
+        b = np.concatenate([bb for _, _, bb in S])
+        x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+        stats = nsamg.batch_solve(h, dev(b), x, rtol=1e-8, maxit=400)
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy()
+    for k, (A, H, bb) in enumerate(S):
+        ref = gmres_onereduce(A, bb, lambda v: ovcycle(H, v, oparams(p)), m=m, rtol=1e-8, stop="nrbe")
+        xs = xg[off[k]:off[k + 1]]
+        Ad = A.toarray()
+        beta = np.linalg.norm(bb - Ad @ xs) / (np.linalg.norm(bb) + np.abs(Ad).sum(axis=1).max() * np.linalg.norm(xs))
+        assert stats[k]["converged"] == 1 and beta <= 1e-8
+        assert stats[k]["nrbe"] == pytest.approx(beta, rel=1e-6)
+        assert abs(stats[k]["iters"] - ref.iters) <= 1, (k, stats[k]["iters"], ref.iters)
+
+
 def test_batch_mixed_progress_and_restarts():
     """One system starts at its solution and one has b = 0: they finish at once while the others
     keep stepping; a short restart length forces restarts in lock step."""

@@ -96,17 +96,20 @@ def test_fullsize_vcycle():
         assert np.max(np.abs(host(z) - want)) <= 1e-11 * np.max(np.abs(want))
 
 
-def test_fullsize_gram_and_update_at_the_last_step():
-    """The one-reduce Gram and update at i = 49 (the last column of GMRES(50)) over n rows."""
-    n, i = 2 ** 21, RESTART - 1
-    rng = np.random.default_rng(11)
+@pytest.mark.parametrize("i", [0, 17, RESTART - 1, 63])
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_fullsize_gram_and_update(i, fp64):
+    """The one-reduce Gram and update at i = 0, 17, 49 (the last column of GMRES(50)) and 63 (the
+    largest restart) over 2^21 rows, double-FP32 and FP64 kernels."""
+    n = 2 ** 21
+    rng = np.random.default_rng(11 + i)
     ld = (n + 63) // 64 * 64
     Vb = np.zeros((i + 2, ld))
     Vb[: i + 1, :n] = rng.standard_normal((i + 1, n)) / np.sqrt(n)
     w = rng.standard_normal(n)
     Vt = dev(Vb.ravel())
     out = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
-    nsamg.gram(n, i, Vt, ld, dev(w), out)
+    (nsamg.gram_fp64 if fp64 else nsamg.gram)(n, i, Vt, ld, dev(w), out)
     a, sv = K.gram(Vb[:i, :n].T, Vb[i, :n], w)
     got = host(out)
     norms = np.sqrt(np.sum(Vb[: i + 1, :n] ** 2, axis=1))
@@ -115,12 +118,13 @@ def test_fullsize_gram_and_update_at_the_last_step():
     beta = float(np.sqrt(a[i]))
     hcoef = rng.standard_normal(i + 1) * 1e-2
     ss = torch.empty(1, dtype=torch.float64, device="cuda")
-    nsamg.update(n, i, Vt, ld, dev(w), beta, dev(hcoef), ss)
+    (nsamg.update_fp64 if fp64 else nsamg.update)(n, i, Vt, ld, dev(w), beta, dev(hcoef), ss)
     v_o, nxt_o = K.update(Vb[:i, :n].T, Vb[i, :n], w, beta, hcoef)
     Vg = host(Vt).reshape(i + 2, ld)
     assert np.max(np.abs(Vg[i, :n] - v_o)) <= TOL * np.max(np.abs(v_o))
     bound = np.abs(w) / beta + np.abs(Vb[:i, :n].T) @ np.abs(hcoef[:i]) + np.abs(v_o) * abs(hcoef[i])
     assert np.max(np.abs(Vg[i + 1, :n] - nxt_o) / bound) <= TOL
+    assert abs(host(ss)[0] - np.dot(nxt_o, nxt_o)) <= TOL * np.dot(bound, bound)
 
 
 def test_fullsize_solve_fp64_matches_oracle():

@@ -54,6 +54,9 @@ CASES = {
     "p30": lambda: (pressure3d_7pt(30, seed=8), dict(coarse_max=200)),
     # ILUT(1e-2, 5) factors with Ruiz-scaled U on every level (Algorithm 2)
     "p23t": lambda: (pressure3d_7pt(23, seed=3), dict(coarse_max=100, ilu="ilut", droptol=1e-2, lfil=5)),
+    # the same with Ruiz stopped by the dep(U) test of Sec. 5.3 (eq. depU)
+    "p23d": lambda: (pressure3d_7pt(23, seed=3), dict(coarse_max=100, ilu="ilut", droptol=1e-2, lfil=5,
+                                                      ruiz_stop="dep")),
 }
 
 _cache = {}
@@ -176,18 +179,25 @@ def test_vcycle(name, smoother):
         assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
 
 
-@pytest.mark.parametrize("n,i", [(1, 0), (1000, 0), (4097, 3), (100003, 17), (262144, 63)])
-def test_gram_and_update(n, i):
-    rng = np.random.default_rng(n + i)
-    ld = n + (7 if n > 1 else 0)
+def _gram_update_case(n, i, fp64, vscale=1.0, wscale=1.0, zero_rows=0, seed=0, aligned=False):
+    """Random orthonormal V_i, an unnormalised vt, scaled (vt, w) pair; checks the Gram (step 6)
+    and the update (steps 8, 12) against the oracle's gram / update componentwise: each dot
+    product within TOL of ||a|| ||b|| (Cauchy-Schwarz), each updated entry within TOL of the sum
+    of the absolute values of its terms."""
+    rng = np.random.default_rng(n + i + seed)
+    # aligned: every column start on a 16-byte boundary (the bulk-copy Gram); else an odd stride
+    ld = (n + 63) // 64 * 64 if aligned else n + (7 if n > 1 else 0)
     Vb = np.zeros((i + 2, ld))
     Q, _ = np.linalg.qr(rng.standard_normal((n, i + 1))) if n >= i + 1 else (rng.standard_normal((n, i + 1)), None)
     Vb[: i + 1, :n] = Q.T[: i + 1]
-    Vb[i, :n] = rng.standard_normal(n) * 3.0  # unnormalised newest vector
-    w = rng.standard_normal(n)
+    Vb[i, :n] = rng.standard_normal(n) * 3.0 * vscale  # unnormalised newest vector
+    w = rng.standard_normal(n) * wscale
+    if zero_rows:
+        Vb[:, :zero_rows] = 0.0
+        w[:zero_rows] = 0.0
     Vt = dev(Vb.ravel())
     out = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
-    nsamg.gram(n, i, Vt, ld, dev(w), out)
+    (nsamg.gram_fp64 if fp64 else nsamg.gram)(n, i, Vt, ld, dev(w), out)
     a, s = K.gram(Vb[:i, :n].T, Vb[i, :n], w)
     got = host(out)
     scale_a = np.sqrt(np.sum(Vb[: i + 1, :n] ** 2, axis=1)) * np.linalg.norm(Vb[i, :n])
@@ -195,24 +205,123 @@ def test_gram_and_update(n, i):
     assert np.all(np.abs(got[: i + 1] - a) <= TOL * scale_a)
     assert np.all(np.abs(got[i + 1:] - s) <= TOL * scale_s)
     beta = float(np.sqrt(a[i]))
-    hcoef = rng.standard_normal(i + 1)
+    hcoef = rng.standard_normal(i + 1) * wscale / max(vscale, 1e-300)
     ss = torch.empty(1, dtype=torch.float64, device="cuda")
-    nsamg.update(n, i, Vt, ld, dev(w), beta, dev(hcoef), ss)
+    (nsamg.update_fp64 if fp64 else nsamg.update)(n, i, Vt, ld, dev(w), beta, dev(hcoef), ss)
     v_o, nxt_o = K.update(Vb[:i, :n].T, Vb[i, :n], w, beta, hcoef)
     Vg = host(Vt).reshape(i + 2, ld)
     assert np.max(np.abs(Vg[i, :n] - v_o)) <= TOL * np.max(np.abs(v_o))
     bound = np.abs(w) / beta + np.abs(Vb[:i, :n].T) @ np.abs(hcoef[:i]) + np.abs(v_o) * abs(hcoef[i])
-    assert np.max(np.abs(Vg[i + 1, :n] - nxt_o) / bound) <= TOL
+    nz = bound > 0
+    assert np.all(Vg[i + 1, :n][~nz] == 0.0)
+    assert np.max(np.abs(Vg[i + 1, :n] - nxt_o)[nz] / bound[nz]) <= TOL
     assert abs(host(ss)[0] - np.dot(nxt_o, nxt_o)) <= TOL * np.dot(bound, bound)
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+@pytest.mark.parametrize("n,i", [(1, 0), (1000, 0), (1000, 1), (4097, 3), (100003, 17), (262144, 63), (70001, 10)])
+def test_gram_and_update(n, i, fp64):
+    _gram_update_case(n, i, fp64)
+
+
+@pytest.mark.parametrize("n,i", [(1, 0), (2, 1), (3, 2), (1000, 0), (1001, 1), (4097, 3), (100003, 17), (262147, 63),
+                                 (70001, 10), (148 * 96 + 1, 40), (5000, 8), (33333, 33)])
+def test_gram_and_update_aligned_columns(n, i):
+    """16-byte aligned columns: the Gram runs its bulk-copy pipeline (ragged tiles, odd last rows,
+    one-row tiles, empty blocks)."""
+    _gram_update_case(n, i, 0, aligned=True)
+
+
+@pytest.mark.parametrize("vscale,wscale", [(1e30, 1e30), (1e-30, 1e-30), (1.0, 1e25), (1.0, 1e-20), (1e-12, 1.0)])
+def test_gram_and_update_outside_the_double_fp32_window(vscale, wscale):
+    """vt and w far from unit scale: the double-FP32 kernels fall back to FP64 for the blocks
+    (Gram) and rows (update) whose magnitudes leave [2^-50, 2^60]; results still within TOL."""
+    _gram_update_case(50021, 12, 0, vscale=vscale, wscale=wscale)
+    _gram_update_case(50021, 12, 0, vscale=vscale, wscale=wscale, aligned=True)
+
+
+def _split_case(n, i, wscale=1.0, seed=0):
+    """The solve's split-basis kernels: unnormalised columns vt_0..vt_i stored as (hi, lo) pairs by
+    nsamg_split_basis; the Gram's raw products against the oracle's gram on the FP64 columns, the
+    update against the oracle's update with v_j = vt_j / beta_j (coefficients c_j = h_j / beta_j),
+    and the stored pair of the new column against its FP64 value."""
+    rng = np.random.default_rng(7 * n + i + seed)
+    ld = (n + 63) // 64 * 64
+    Vb = np.zeros((i + 2, ld))
+    Vb[: i + 1, :n] = rng.standard_normal((i + 1, n)) * rng.uniform(0.3, 3.0, (i + 1, 1))
+    w = rng.standard_normal(n) * wscale
+    Vs = torch.zeros(2 * ld * (i + 2), dtype=torch.float32, device="cuda")
+    nsamg.split_basis(n, i + 1, dev(Vb.ravel()), ld, Vs, ld)
+    out = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
+    dw = dev(w)
+    nsamg.gram_split(n, i, Vs, ld, dw, out)
+    a, s_ = K.gram(Vb[:i, :n].T, Vb[i, :n], w)
+    got = host(out)
+    norms = np.sqrt(np.sum(Vb[: i + 1, :n] ** 2, axis=1))
+    assert np.all(np.abs(got[: i + 1] - a) <= TOL * norms * norms[i])
+    assert np.all(np.abs(got[i + 1:] - s_) <= TOL * norms * np.linalg.norm(w))
+    betas = norms * rng.uniform(0.5, 2.0, i + 1)
+    hcoef = rng.standard_normal(i + 1)
+    c = hcoef / betas
+    vin = torch.empty(n, dtype=torch.float64, device="cuda")
+    ss = torch.empty(1, dtype=torch.float64, device="cuda")
+    nsamg.update_split(n, i, Vs, ld, dw, float(betas[i]), dev(c), vin, ss)
+    Vn = (Vb[:i, :n] / betas[:i, None]).T
+    _, nxt_o = K.update(Vn, Vb[i, :n], w, float(betas[i]), hcoef)
+    bound = np.abs(w) / betas[i] + np.abs(Vn) @ np.abs(hcoef[:i]) + np.abs(Vb[i, :n] / betas[i]) * abs(hcoef[i])
+    g = host(vin)
+    assert np.max(np.abs(g - nxt_o) / bound) <= TOL
+    assert abs(host(ss)[0] - np.dot(nxt_o, nxt_o)) <= TOL * np.dot(bound, bound)
+    pairs = host(Vs).reshape(i + 2, ld, 2)[i + 1, :n].astype(np.float64)
+    assert np.max(np.abs(pairs.sum(axis=1) - g) / np.maximum(np.abs(g), 1e-300)) <= 2.0 ** -44
+
+
+@pytest.mark.parametrize("n,i", [(1, 0), (2, 1), (999, 0), (1001, 1), (4097, 3), (70001, 10), (100003, 17),
+                                 (148 * 96 + 1, 40), (262147, 63), (33333, 30)])
+def test_split_basis_gram_and_update(n, i):
+    _split_case(n, i)
+
+
+@pytest.mark.parametrize("wscale", [1e30, 1e-30])
+def test_split_basis_w_outside_the_window(wscale):
+    """w far from unit scale: the Gram's blocks and the update's rows fall back to FP64."""
+    _split_case(50021, 12, wscale=wscale)
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30, 2.0 ** -100])
+def test_solve_is_scale_invariant(scale):
+    """b scaled by a constant: the split basis stores the residual at unit scale (the exact power of
+    two goes into g_0), so the solve takes the same iterations and returns the scaled x."""
+    A, H = case("p23")
+    b = rhs_uniform(A.shape[0], 3)
+    xs = []
+    its = []
+    with nsamg.setup_hierarchy(H, nsamg.default_params(smoother=K.HYBRID_ILU0)) as h:
+        for f in (1.0, scale):
+            x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+            st = nsamg.solve(h, dev(b * f), x, rtol=1e-8, maxit=500)
+            assert st["converged"] == 1
+            xs.append(host(x) / f)
+            its.append(st["iters"])
+    assert its[0] == its[1]
+    assert np.linalg.norm(xs[1] - xs[0]) <= 1e-10 * np.linalg.norm(xs[0])
+
+
+def test_gram_and_update_with_zero_rows():
+    """Exact zeros (a block of zero rows in every vector) split to (0, 0) and add nothing."""
+    _gram_update_case(40000, 9, 0, zero_rows=5000)
+    _gram_update_case(40000, 9, 1, zero_rows=5000)
+    _gram_update_case(40000, 9, 0, zero_rows=5000, aligned=True)
 
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.JACOBI_L1])
-@pytest.mark.parametrize("graph", [1, 0])
-def test_solve_matches_oracle(name, smoother, graph):
+@pytest.mark.parametrize("graph,krylov_fp64", [(1, 0), (0, 0), (1, 1)])
+def test_solve_matches_oracle(name, smoother, graph, krylov_fp64):
     A, H = case(name)
     m = 30
-    p = nsamg.default_params(**params_for(smoother), restart=m, use_graph=graph, spmv_group=-1 if name == "p30" else 0)
+    p = nsamg.default_params(**params_for(smoother), restart=m, use_graph=graph, krylov_fp64=krylov_fp64,
+                             spmv_group=-1 if name == "p30" else 0)
     op = oracle_params(p)
     b = rhs_uniform(A.shape[0], 0)
     ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=m, rtol=1e-8)
@@ -228,11 +337,12 @@ def test_solve_matches_oracle(name, smoother, graph):
     assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
 
 
-def test_solve_restarts_and_texact():
+@pytest.mark.parametrize("krylov_fp64", [0, 1])
+def test_solve_restarts_and_texact(krylov_fp64):
     A, H = case("c1")
     b = rhs_uniform(A.shape[0], 4)
     for t_exact in (0, 1):
-        p = nsamg.default_params(restart=4, t_exact=t_exact)
+        p = nsamg.default_params(restart=4, t_exact=t_exact, krylov_fp64=krylov_fp64)
         op = oracle_params(p)
         ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, op), m=4, rtol=1e-9,
                               T_mode="exact" if t_exact else "trunc")
@@ -242,6 +352,33 @@ def test_solve_restarts_and_texact():
         assert st["converged"] and st["restarts"] >= 1
         assert abs(st["iters"] - ref.iters) <= 1
         assert np.linalg.norm(host(x) - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+
+
+@pytest.mark.parametrize("m", [6, 30])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_solve_stops_on_backward_error(m, graph):
+    """stop_nrbe = 1: the solve stops on beta(x) = ||r|| / (||b|| + ||A||_inf ||x||) <= rtol (Sec. 3)
+    like the oracle's one-reduce GMRES with the same stop; with restarts (m = 6) it needs fewer
+    steps than the relative-residual stop."""
+    A, H = case("c1")
+    b = rhs_uniform(A.shape[0], 0)
+    p = nsamg.default_params(restart=m, stop_nrbe=1, use_graph=graph)
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, oracle_params(p)), m=m, rtol=1e-8, stop="nrbe")
+    with nsamg.setup_hierarchy(H, p) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+        xs = host(x)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(restart=m, use_graph=graph)) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st_rel = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+    Ad = A.toarray()
+    beta = np.linalg.norm(b - Ad @ xs) / (np.linalg.norm(b) + np.abs(Ad).sum(axis=1).max() * np.linalg.norm(xs))
+    assert st["converged"] == 1 and beta <= 1e-8 and st["nrbe"] == pytest.approx(beta, rel=1e-6)
+    assert abs(st["iters"] - ref.iters) <= 1
+    assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+    assert st["iters"] <= st_rel["iters"]
+    if m == 6:
+        assert st["iters"] < st_rel["iters"]
 
 
 def test_solve_edge_cases():
@@ -404,27 +541,32 @@ def test_c3_type_graded_27pt_fp32_vcycle():
 
 
 @pytest.mark.parametrize("name", ["c1", "p23"])
-def test_backward_error_and_orthogonality_diagnostics(name):
+@pytest.mark.parametrize("krylov_fp64", [1, 0])
+def test_backward_error_and_orthogonality_diagnostics(name, krylov_fp64):
     """NRBE (Sec. 3: ||r|| / (||b|| + ||A||_inf ||x||)) matches the value computed from the
-    returned x on the host; the loss of orthogonality of the last cycle is O(eps * kappa(B))."""
+    returned x on the host; the loss of orthogonality of the last cycle is O(eps * kappa(B))
+    (Sec. 3), with eps the precision of the basis inner products: FP64 (then also the same size
+    as the oracle's loss) or double-FP32 (eps ~ 2^-45: the bound, not the oracle's value)."""
     A, H = case(name)
     b = rhs_uniform(A.shape[0], 0)
-    with nsamg.setup_hierarchy(H, nsamg.default_params()) as h:
+    with nsamg.setup_hierarchy(H, nsamg.default_params(krylov_fp64=krylov_fp64)) as h:
         x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
         st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
         xs = host(x)
     r = b - A @ xs
     nrbe = np.linalg.norm(r) / (np.linalg.norm(b) + abs(A).sum(axis=1).max() * np.linalg.norm(xs))
     assert st["nrbe"] == pytest.approx(nrbe, rel=1e-6)
-    assert 0.0 < st["orth_loss"] <= 1e3 * np.finfo(float).eps / st["relres_implicit"]
-    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, K.SmootherParams()), m=30, rtol=1e-8)
-    ref_loss = np.sqrt(2.0) * np.linalg.norm(ref.L)
-    assert st["orth_loss"] == pytest.approx(ref_loss, rel=0.5, abs=1e-15)
-    # ||S_k||_2 of the same cycle: the same order as the oracle's, and at most ||L||_F / (1 - ||L||_F)
+    eps = np.finfo(float).eps if krylov_fp64 else 2.0 ** -45
+    assert 0.0 < st["orth_loss"] <= 1e3 * eps / st["relres_implicit"]
     from oracle.gmres import sk_norm
     lf = st["orth_loss"] / np.sqrt(2.0)
     assert 0.0 < st["sk_norm"] <= lf / (1.0 - lf) * (1 + 1e-12)
-    assert st["sk_norm"] == pytest.approx(sk_norm(ref.L), rel=0.5, abs=1e-15)
+    if krylov_fp64:
+        ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, K.SmootherParams()), m=30, rtol=1e-8)
+        ref_loss = np.sqrt(2.0) * np.linalg.norm(ref.L)
+        assert st["orth_loss"] == pytest.approx(ref_loss, rel=0.5, abs=1e-15)
+        # ||S_k||_2 of the same cycle: the same order as the oracle's
+        assert st["sk_norm"] == pytest.approx(sk_norm(ref.L), rel=0.5, abs=1e-15)
 
 
 @pytest.mark.parametrize("k", [1, 2, 7, 33, 64])
