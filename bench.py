@@ -292,26 +292,34 @@ def time_kernels(nsamg, torch, h, A, H, stream, fma64: float, reps=24):
                                   "note": "4 triangular passes (2 L_s, 2 U_s) from a zero guess"}
         out["ilu_sweep_x0_l0"]["GBps"] = out["ilu_sweep_x0_l0"]["bytes"] / tl / 1e9
         del b_ilu
-    # one-reduce Gram and basis update over n rows at step i = 10 and i = 40, in double-FP32 (the
-    # solve's default) and FP64; columns normalised like the solver's basis
+    # one-reduce Gram and basis update over n rows at steps i = 10 and i = 29: the solve's kernels
+    # (split basis, double-FP32 products; columns of unit-order unnormalised vectors) and the FP64
+    # kernels (krylov_fp64 = 1) on the same data
     hbm, _ = peaks()
     sp = stream.cuda_stream
     ld = (n + 63) // 64 * 64
-    for i in (10, 40):
+    for i in (10, 29):
         V = torch.rand((i + 2) * ld, dtype=torch.float64, device="cuda")
         Vv = V.view(i + 2, ld)
         Vv[:, n:] = 0.0
         Vv /= torch.linalg.norm(Vv, dim=1, keepdim=True)
+        Vs = torch.empty(2 * (i + 2) * ld, dtype=torch.float32, device="cuda")
+        nsamg.split_basis(n, i + 1, V, ld, Vs, ld, sp)
         w = torch.rand(n, dtype=torch.float64, device="cuda")
         o = torch.empty(2 * (i + 1), dtype=torch.float64, device="cuda")
         hc = torch.rand(i + 1, dtype=torch.float64, device="cuda") * 1e-3
         ss = torch.empty(1, dtype=torch.float64, device="cuda")
-        for tag, g, u, fg, fu in (("", nsamg.gram, nsamg.update, 2 * n, 3 * n),
-                                  ("_fp64", nsamg.gram_fp64, nsamg.update_fp64, 2 * (i + 1) * n, (i + 4) * n)):
-            tg = timed(lambda k: g(n, i, V, ld, w, o, sp))
-            tu = timed(lambda k: u(n, i, V, ld, w, 1.0, hc, ss, sp))
-            for name, t, b, f in ((f"gram{tag}_i{i}", tg, 8 * (i + 2) * n, fg), (f"update{tag}_i{i}", tu, 8 * (i + 4) * n, fu)):
-                out[name] = kernel_roofline(t, b, f, hbm, fma64)
+        vin = torch.empty(n, dtype=torch.float64, device="cuda")
+        tg = timed(lambda k: nsamg.gram_split(n, i, Vs, ld, w, o, sp))
+        tu = timed(lambda k: nsamg.update_split(n, i, Vs, ld, w, 1.0, hc, vin, ss, sp))
+        out[f"gram_i{i}"] = kernel_roofline(tg, 8 * (i + 2) * n, 0, hbm, fma64)
+        out[f"gram_i{i}"]["kernel"] = "k_gram_s (split basis, double-FP32, bulk-copy pipeline)"
+        out[f"update_i{i}"] = kernel_roofline(tu, 8 * (i + 4) * n, 2 * n, hbm, fma64)
+        out[f"update_i{i}"]["kernel"] = "k_update_s (split basis, double-FP32, bulk-copy pipeline)"
+        tg = timed(lambda k: nsamg.gram_fp64(n, i, V, ld, w, o, sp))
+        tu = timed(lambda k: nsamg.update_fp64(n, i, V, ld, w, 1.0, hc, ss, sp))
+        out[f"gram_fp64_i{i}"] = kernel_roofline(tg, 8 * (i + 2) * n, 2 * (i + 1) * n, hbm, fma64)
+        out[f"update_fp64_i{i}"] = kernel_roofline(tu, 8 * (i + 4) * n, (i + 4) * n, hbm, fma64)
     return out
 
 
