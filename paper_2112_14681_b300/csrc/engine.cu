@@ -950,69 +950,77 @@ struct TuneScratch {
 };
 
 // One launch timed after L2 has been swept, as in a V-cycle where the other passes have evicted
-// the matrix (a matrix smaller than L2 would otherwise be timed from cache); best of five.
+// the matrix (a matrix smaller than L2 would otherwise be timed from cache).
 template <typename T>
-float time_spmv(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
-                const TuneScratch& fl) {
+float time_spmv_once(DCSR<T>& M, T* x, T* y, int G, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                     const TuneScratch& fl) {
   auto op = op_mat(M, cref((const T*)x));
   op.out = vref(y);
+  if (fl.buf) k_l2_sweep<<<fl.blocks, 256, 0, s>>>(fl.buf, fl.n, fl.sink);
+  cudaEventRecord(e0, s);
   launch_row(op, G, s);
-  float best = 1e30f;
-  for (int round = 0; round < 5; ++round) {
-    if (fl.buf) k_l2_sweep<<<fl.blocks, 256, 0, s>>>(fl.buf, fl.n, fl.sink);
-    cudaEventRecord(e0, s);
-    launch_row(op, G, s);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    best = std::min(best, ms);
-  }
-  return best;
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms;
 }
 
 // Timed choice among CSR with G = 1, 2, ..., 32 threads per row and the SELL shapes of
-// launch_sell (best of five single launches, each after an L2 sweep).
+// launch_sell. The candidates are timed in interleaved rounds (each round times every candidate
+// once, after an L2 sweep), so that a clock or neighbour change during tuning shifts all of them
+// alike; each keeps its best of kTuneRounds. A later candidate must beat the best earlier one by
+// more than kTuneMargin to be chosen, so shapes the timing cannot separate resolve to the
+// simpler one (CSR before SELL, fewer threads, fewer chunks a warp) the same way on every run.
+constexpr int kTuneRounds = 9;
+constexpr float kTuneMargin = 0.015f;
+
 template <typename T>
 int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s, const TuneScratch& fl) {
   if (M.n < 20000 || M.nnz == 0) return NSAMG_OK;
+  struct Cand {
+    int G, K, U;  // K = 0: CSR with G threads a row; else SELL with K chunks a warp, U-way unrolled
+    float best;
+  };
+  Cand cands[16];
+  int nc = 0;
+  const double avg = (double)M.nnz / M.n;
+  for (int G : {1, 2, 4, 8, 16, 32}) {
+    if (G > 2 * avg + 2) break;
+    cands[nc++] = {G, 0, 1, 1e30f};
+  }
+  if (M.nchunks > 0)
+    for (const auto& ku : {std::pair<int, int>{1, 1}, {2, 1}, {4, 1}, {1, 4}, {2, 2}})
+      cands[nc++] = {1, ku.first, ku.second, 1e30f};
+  auto apply = [&M](const Cand& c) {
+    M.use_sell = c.K > 0;
+    if (c.K) {
+      M.sell_k = c.K;
+      M.sell_u = c.U;
+    } else {
+      M.G = c.G;
+    }
+  };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int cands[] = {1, 2, 4, 8, 16, 32};
-  float best = 1e30f;
-  int bestG = M.G, bestK = 0;
-  const double avg = (double)M.nnz / M.n;
-  M.use_sell = false;
-  for (int G : cands) {
-    if (G > 2 * avg + 2) break;
-    const float ms = time_spmv(M, x, y, G, s, e0, e1, fl);
-    if (ms < best) {
-      best = ms;
-      bestG = G;
+  for (int c = 0; c < nc; ++c) {  // one untimed launch of each shape (instruction cache, first-launch cost)
+    apply(cands[c]);
+    time_spmv_once(M, x, y, cands[c].G, s, e0, e1, TuneScratch{});
+  }
+  for (int round = 0; round < kTuneRounds; ++round)
+    for (int c = 0; c < nc; ++c) {
+      apply(cands[c]);
+      cands[c].best = std::min(cands[c].best, time_spmv_once(M, x, y, cands[c].G, s, e0, e1, fl));
     }
-  }
-  int bestU = 1;
-  if (M.nchunks > 0) {
-    const int shapes[][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 4}, {2, 2}};
-    for (const auto& ku : shapes) {
-      M.use_sell = true;
-      M.sell_k = ku[0];
-      M.sell_u = ku[1];
-      const float ms = time_spmv(M, x, y, 1, s, e0, e1, fl);
-      if (ms < best) {
-        best = ms;
-        bestK = ku[0];
-        bestU = ku[1];
-      }
-    }
-  }
-  M.G = bestG;
-  M.use_sell = bestK > 0;
-  if (bestK) {
-    M.sell_k = bestK;
-    M.sell_u = bestU;
-  }
+  int pick = 0;
+  for (int c = 1; c < nc; ++c)
+    if (cands[c].best < cands[pick].best * (1.f - kTuneMargin)) pick = c;
+  int pick_csr = 0;  // the CSR group kept for passes that take the CSR arrays of a SELL matrix
+  for (int c = 1; c < nc && cands[c].K == 0; ++c)
+    if (cands[c].best < cands[pick_csr].best * (1.f - kTuneMargin)) pick_csr = c;
+  apply(cands[pick_csr]);
+  apply(cands[pick]);
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -674,9 +674,7 @@ __device__ bool ring_produce(const Ring& g, int nitems, NSeg nseg, Rows rows, Se
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// The same with one thread issuing every copy (the Gram's producer: with its heavier consumers,
-// issuing from one lane measured faster than from the whole warp; the update, whose consumers are
-// light, is faster with the warp form).
+// The same with one thread issuing every copy (k_gram_tma's producer).
 template <typename NSeg, typename Rows, typename Seg>
 __device__ bool ring_produce_lane0(const Ring& g, int nitems, NSeg nseg, Rows rows, Seg seg, volatile int* abort) {
   int issued = 0;
@@ -709,15 +707,20 @@ __device__ bool ring_produce_lane0(const Ring& g, int nitems, NSeg nseg, Rows ro
   return ok;
 }
 
-// Consumer warp: wait for item k (lane 0 polls); false if the wait gave up.
+// Consumer warp: wait for item k (every lane polls, so that no branch on the lane index leaves
+// the warp split for the tile's work); false if the wait gave up in any lane.
 __device__ __forceinline__ bool ring_acquire(const Ring& g, int k) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(g.full(k), g.round(k)) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  const bool ok = mbar_wait(g.full(k), g.round(k));
+  return __all_sync(0xffffffffu, ok);
 }
+// One arrive per warp on the stage's empty barrier, by lane 0 through a predicate (no branch).
 __device__ __forceinline__ void ring_release(const Ring& g, int k) {
   __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(g.empty(k));
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %1, 0;\n\t@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(
+          g.empty(k)),
+      "r"(threadIdx.x & 31)
+      : "memory");
 }
 
 // Gram consumer work on one staged tile: rows [rb, re) (all in shared memory, stride 32 over the
@@ -1487,37 +1490,160 @@ __global__ void __launch_bounds__(kRedThreads) k_split_cols(int64_t n, int ncols
       Vs[(int64_t)j * lds + r] = split2(V[(int64_t)j * ldv + r]);
 }
 
-// Gram products on one staged tile, split basis: rows [rb, re) x the warp's NS columns, against
-// column i (the stage's column nv - 1, already split) and w (FP64 at stage column nv, split here).
-template <int NS>
-__device__ __forceinline__ void gram_rows_s(const double* __restrict__ sb, int T, int nv, int C, int cg, int rg, int R,
-                                            int te, float (&sa)[kDfSlots], float (&ca)[kDfSlots],
-                                            float (&sw)[kDfSlots], float (&cw)[kDfSlots], unsigned& mx) {
-  const int lane = threadIdx.x & 31;
-  const float2* __restrict__ sp = reinterpret_cast<const float2*>(sb);
-  // per-slot column bases (only the last slot can pass the last column; its discarded products
-  // then read column nv - 1)
-  const float2* colp[NS];
+// Packed FP32 pairs (the f32x2 instructions of sm_100 and later): one instruction applies the
+// operation, correctly rounded, to both 32-bit lanes of a 64-bit register pair, so each lane's
+// result is bitwise that of the scalar instruction. Low lane = first argument of f2_pack.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// 32-bit shared-memory load (kept scalar so that two loads can fill the two halves of a pair)
+__device__ __forceinline__ float lds_f32(unsigned addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// dot2_step in both lanes: (s, c) += (xh + xl)(bh + bl), with nbh = -bh. The product is formed
+// negated (exact), which turns TwoSum's p terms into subtractions; every lane's sequence of
+// rounded operations is that of dot2_step, so the results are bitwise the same.
+__device__ __forceinline__ void dot2_step2(f2_t& s, f2_t& c, f2_t xh, f2_t xl, f2_t bh, f2_t bl, f2_t nbh) {
+  const f2_t np = f2_mul(xh, nbh);  // -p
+  f2_t e = f2_fma(xh, bh, np);       // xh bh - p, exact
+  e = f2_fma(xh, bl, e);
+  e = f2_fma(xl, bh, e);
+  const f2_t t = f2_sub(s, np);  // s + p
+  const f2_t z = f2_sub(t, s);
+  const f2_t err = f2_sub(f2_sub(s, f2_sub(t, z)), f2_add(np, z));  // (s - (t - z)) + (p - z)
+  s = t;
+  c = f2_add(c, f2_add(err, e));
+}
+
+// Column groups C of k_gram_s (a power of two <= 16), whose warps take their columns in pairs
+// (the two lanes of the packed instructions): the smallest C * pairs per warp with at most
+// kDfSlots / 2 pairs; ties go to the smaller C (more columns share each row's fixed work).
+__device__ __forceinline__ int df_pair_groups(int nv) {
+  int best = 16, cost = 16 * (((nv + 15) / 16 + 1) / 2);
 #pragma unroll
-  for (int sl = 0; sl < NS; ++sl) colp[sl] = sp + ((sl == NS - 1) ? min(cg + sl * C, nv - 1) : cg + sl * C) * T;
-  const float2* vi = sp + (nv - 1) * T;
-  const double* wp = sb + nv * T;
-  // 32-row groups of the tile dealt round-robin to the R row-group warps
-  for (int r = rg * 32 + lane; r < te; r += 32 * R) {
-    const float2 q = vi[r];
-    const double xw = wp[r];
-    mx = max(mx, abs_hiword(xw));
-    float q2, q3;
-    split_df(xw, q2, q3);
-    float2 xv[NS];
-#pragma unroll
-    for (int sl = 0; sl < NS; ++sl) xv[sl] = colp[sl][r];
-#pragma unroll
-    for (int sl = 0; sl < NS; ++sl) {
-      dot2_step(sa[sl], ca[sl], xv[sl].x, xv[sl].y, q.x, q.y);
-      dot2_step(sw[sl], cw[sl], xv[sl].x, xv[sl].y, q2, q3);
+  for (int c = 8; c >= 1; c >>= 1) {
+    const int np = ((nv + c - 1) / c + 1) / 2;
+    if (np <= kDfSlots / 2 && c * np <= cost) {
+      best = c;
+      cost = c * np;
     }
   }
+  return best;
+}
+
+// Consumer warp of k_gram_s: every tile of the block's chunk, rows dealt to the R row-group warps
+// in 32-row groups (round robin), times the warp's 2 NP columns cg + sl C, taken in pairs
+// (slots 2p, 2p + 1) by the packed instructions; slots past the last column read column nv - 1
+// and their products are discarded. The products are against column i (the stage's column
+// nv - 1, already split) and w (FP64 at stage column nv, split here). The tile loop sits inside
+// the pair-count specialisation so the accumulators keep their registers from tile to tile.
+// Returns false if a wait gave up.
+template <int NP>
+__device__ __forceinline__ bool gram_consume_s(const Ring& g, const float2* __restrict__ Vs, const double* __restrict__ w,
+                                               int64_t ldv, int nv, int T, int C, int cg, int rg, int R, int64_t r0,
+                                               int64_t r1, int ntiles, float (&sa)[kDfSlots], float (&ca)[kDfSlots],
+                                               float (&sw)[kDfSlots], float (&cw)[kDfSlots], unsigned& mx) {
+  constexpr int NS = 2 * NP;
+  const int lane = threadIdx.x & 31;
+  f2_t s_a[NP], c_a[NP], s_w[NP], c_w[NP];
+  unsigned offb[NS];  // byte offset of each slot's column in a stage
+#pragma unroll
+  for (int q = 0; q < NP; ++q) s_a[q] = c_a[q] = s_w[q] = c_w[q] = 0ull;
+#pragma unroll
+  for (int sl = 0; sl < NS; ++sl) offb[sl] = 8u * (unsigned)(min(cg + sl * C, nv - 1) * T);
+  const int offv = (nv - 1) * T, offw = nv * T;
+  const int step = 32 * R;
+  bool ok = true;
+  int64_t t0 = r0;
+  for (int k = 0; k < ntiles; ++k, t0 += T) {
+    if (!ring_acquire(g, k)) {
+      ok = false;
+      break;
+    }
+    const int tn = (int)min((int64_t)T, r1 - t0), te = tn & ~1;
+    const double* sb = g.buf(k);
+    const float2* __restrict__ sp = reinterpret_cast<const float2*>(sb);
+    const unsigned base = smem_u32(sb);
+    // unrolled by two so that the TwoSum results alternate registers instead of moving back
+#pragma unroll 2
+    for (int r = rg * 32 + lane; r < te; r += step) {
+      const float2 q = sp[offv + r];
+      const double xw = sb[offw + r];
+      mx = max(mx, abs_hiword(xw));
+      float q2, q3;
+      split_df(xw, q2, q3);
+      const f2_t ah = f2_pack(q.x, q.x), al = f2_pack(q.y, q.y), nah = f2_pack(-q.x, -q.x);
+      const f2_t bh = f2_pack(q2, q2), bl = f2_pack(q3, q3), nbh = f2_pack(-q2, -q2);
+      const unsigned rb = base + 8u * (unsigned)r;
+      f2_t xh[NP], xl[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        xh[p] = f2_pack(lds_f32(rb + offb[2 * p]), lds_f32(rb + offb[2 * p + 1]));
+        xl[p] = f2_pack(lds_f32(rb + offb[2 * p] + 4u), lds_f32(rb + offb[2 * p + 1] + 4u));
+      }
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        dot2_step2(s_a[p], c_a[p], xh[p], xl[p], ah, al, nah);
+        dot2_step2(s_w[p], c_w[p], xh[p], xl[p], bh, bl, nbh);
+      }
+    }
+    if (te < tn && (te >> 5) % R == rg && lane == 0) {  // the odd last row (its 32-row group's warp)
+      const int64_t row = t0 + te;
+      const float2 q = Vs[(int64_t)(nv - 1) * ldv + row];
+      const double xw = w[row];
+      mx = max(mx, abs_hiword(xw));
+      float q2, q3;
+      split_df(xw, q2, q3);
+      const f2_t ah = f2_pack(q.x, q.x), al = f2_pack(q.y, q.y), nah = f2_pack(-q.x, -q.x);
+      const f2_t bh = f2_pack(q2, q2), bl = f2_pack(q3, q3), nbh = f2_pack(-q2, -q2);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float2 x0 = Vs[(int64_t)min(cg + 2 * p * C, nv - 1) * ldv + row];
+        const float2 x1 = Vs[(int64_t)min(cg + (2 * p + 1) * C, nv - 1) * ldv + row];
+        const f2_t xh = f2_pack(x0.x, x1.x), xl = f2_pack(x0.y, x1.y);
+        dot2_step2(s_a[p], c_a[p], xh, xl, ah, al, nah);
+        dot2_step2(s_w[p], c_w[p], xh, xl, bh, bl, nbh);
+      }
+    }
+    ring_release(g, k);
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    f2_unpack(s_a[p], sa[2 * p], sa[2 * p + 1]);
+    f2_unpack(c_a[p], ca[2 * p], ca[2 * p + 1]);
+    f2_unpack(s_w[p], sw[2 * p], sw[2 * p + 1]);
+    f2_unpack(c_w[p], cw[2 * p], cw[2 * p + 1]);
+  }
+  return ok;
 }
 
 // Gram on the split basis with the bulk-copy ring: a_j = vt_j . vt_i and s_j = vt_j . w for
@@ -1536,9 +1662,9 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
   const int i = st ? st->i : a.i_standalone;
   const int nv = i + 1;  // columns 0..i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = df_groups(nv);
+  const int C = df_pair_groups(nv);
   const int R = kGramWarps / C;
-  const int S = (nv + C - 1) / C;
+  const int S = 2 * (((nv + C - 1) / C + 1) / 2);  // slots per warp (pairs of columns)
   // rows per tile: the largest multiple of 32 for which the stage (columns 0..i and w) fits
   const int T = min(2048, kGramTmaStageBytes / (8 * (nv + 1)) / 32 * 32);
   const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + T - 1) / T * T;
@@ -1562,8 +1688,8 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
     return (int)((r1 - t0) < (int64_t)T ? (r1 - t0) : (int64_t)T);
   };
   if (warp == kGramTmaConsumers) {
-    if (lane == 0) {  // producer (one thread): per tile the columns 0..i and w
-      const bool ok = ring_produce_lane0(
+    {  // producer warp: per tile the columns 0..i and w
+      const bool ok = ring_produce(
           g, ntiles, [&](int) { return nv + 1; }, tile_rows,
           [&](int k, int q, const double** src, int* off) {
             const int64_t t0 = r0 + (int64_t)k * T;
@@ -1574,48 +1700,20 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
       if (!ok && lane == 0) s_abort = 1;
     }
   } else {
-    for (int k = 0; k < ntiles; ++k) {
-      if (!ring_acquire(g, k)) {
-        s_abort = 1;
-        break;
-      }
-      const int tn = tile_rows(k), te = tn & ~1;
-      const double* sb = g.buf(k);
-      switch (S) {
-#define NSAMG_GRAM_ROWS_S(NS)                                                  \
-  case NS:                                                                     \
-    gram_rows_s<NS>(sb, T, nv, C, cg, rg, R, te, sa, ca, sw, cw, mx);          \
+    bool ok = true;
+    switch (S / 2) {
+#define NSAMG_GRAM_CONSUME_S(NP)                                                                         \
+  case NP:                                                                                               \
+    ok = gram_consume_s<NP>(g, Vs, a.w, a.ldv, nv, T, C, cg, rg, R, r0, r1, ntiles, sa, ca, sw, cw, mx); \
     break;
-        NSAMG_GRAM_ROWS_S(1)
-        NSAMG_GRAM_ROWS_S(2)
-        NSAMG_GRAM_ROWS_S(3)
-        NSAMG_GRAM_ROWS_S(4)
-        NSAMG_GRAM_ROWS_S(5)
-        NSAMG_GRAM_ROWS_S(6)
-        NSAMG_GRAM_ROWS_S(7)
-        NSAMG_GRAM_ROWS_S(8)
-#undef NSAMG_GRAM_ROWS_S
-        default: break;
-      }
-      if (te < tn && (te >> 5) % R == rg && lane == 0) {  // the odd last row (its 32-row group's warp)
-        const int64_t row = r0 + (int64_t)k * T + te;
-        const float2 q = Vs[(int64_t)i * a.ldv + row];
-        const double xw = a.w[row];
-        mx = max(mx, abs_hiword(xw));
-        float q2, q3;
-        split_df(xw, q2, q3);
-#pragma unroll
-        for (int sl = 0; sl < kDfSlots; ++sl) {
-          const int j = cg + sl * C;
-          if (sl < S && j < nv) {
-            const float2 x = Vs[(int64_t)j * a.ldv + row];
-            dot2_step(sa[sl], ca[sl], x.x, x.y, q.x, q.y);
-            dot2_step(sw[sl], cw[sl], x.x, x.y, q2, q3);
-          }
-        }
-      }
-      ring_release(g, k);
+      NSAMG_GRAM_CONSUME_S(1)
+      NSAMG_GRAM_CONSUME_S(2)
+      NSAMG_GRAM_CONSUME_S(3)
+      NSAMG_GRAM_CONSUME_S(4)
+#undef NSAMG_GRAM_CONSUME_S
+      default: break;
     }
+    if (!ok) s_abort = 1;
   }
   if (warp < kGramTmaConsumers) {
     mx = __reduce_max_sync(0xffffffffu, mx);
@@ -1704,6 +1802,88 @@ __device__ __forceinline__ void upd_cols_s(const float2* __restrict__ col, const
   }
 }
 
+// The end of one row of k_update_s: the four (sum, error) pairs summed and normalised, stored as
+// the pair of column i+1 and (if requested) as FP64 in vin or FP32 in v32, its square added to the
+// thread's ||vt_{i+1}||^2. A row that left the double-FP32 window (ok false) is recomputed in
+// FP64 from w / beta_i and the stored pairs.
+__device__ __forceinline__ void upd_finish_s(const UpdateArgs& a, const double* __restrict__ s_c, int i, int64_t row,
+                                             bool ok, double wb, float (&ps)[4], float (&pc)[4], float2* vnext,
+                                             float& qs, float& qc, double& q64) {
+  double acc;
+  if (ok) {
+    df_add(ps[0], pc[0], ps[1], pc[1]);
+    df_add(ps[2], pc[2], ps[3], pc[3]);
+    df_add(ps[0], pc[0], ps[2], pc[2]);
+    // normalised pair (TwoSum): stored, squared and rounded for the FP32 copy
+    const float tt = __fadd_rn(ps[0], pc[0]);
+    const float z = __fsub_rn(tt, ps[0]);
+    const float e = __fadd_rn(__fsub_rn(ps[0], __fsub_rn(tt, z)), __fsub_rn(pc[0], z));
+    vnext[row] = make_float2(tt, e);
+    acc = widen_normal(tt) + widen_normal(e);
+    if (a.v32) a.v32[row] = tt;
+    dot2_step(qs, qc, tt, e, tt, e);
+  } else {
+    acc = wb;
+    for (int j = 0; j <= i; ++j) acc = fma(-s_c[j], join2(a.Vs[(int64_t)j * a.ldv + row]), acc);
+    vnext[row] = split2(acc);
+    if (a.v32) a.v32[row] = narrow_f64(acc);
+    q64 = fma(acc, acc, q64);
+  }
+  if (a.vin) a.vin[row] = acc;
+}
+
+constexpr int kUpdRegCoefs = 12;
+
+// Consumer of k_update_s when w and all NW = i + 1 basis columns fit one chunk (i < kUpdChunk - 1):
+// the coefficients stay in registers and the tile loop sits inside the width specialisation.
+// Returns false if a wait gave up.
+template <int NW>
+__device__ __forceinline__ bool upd_consume1_s(const Ring& g, const UpdateArgs& a, const double* __restrict__ s_c,
+                                               const float2* __restrict__ s_cs, int i, double invb, bool cok,
+                                               int64_t r0, int64_t r1, int ntiles, float2* vnext, float& qs, float& qc,
+                                               double& q64) {
+  const int t = threadIdx.x;
+  // coefficients: in registers up to kUpdRegCoefs columns, else read (broadcast) from shared memory
+  constexpr bool kReg = NW <= kUpdRegCoefs;
+  float2 hc[kReg ? NW : 1];
+#pragma unroll
+  for (int k = 0; k < (kReg ? NW : 1); ++k) hc[k] = s_cs[k];
+  int64_t t0 = r0;
+  for (int kt = 0; kt < ntiles; ++kt, t0 += kUpdTile) {
+    if (!ring_acquire(g, kt)) return false;
+    const int tn = (int)min((int64_t)kUpdTile, r1 - t0), te = tn & ~1;
+    const int64_t row = t0 + t;
+    float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
+    double wb = 0.0;
+    if (t < te) {  // from the stage: column 0 is w, column 1 + j is vt_j
+      const double* sb = g.buf(kt);
+      wb = sb[t] * invb;
+      split_df(wb, ps[0], pc[0]);
+      const float2* __restrict__ col = reinterpret_cast<const float2*>(sb) + kUpdTile + t;
+      float2 x[NW];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) x[k] = col[k * kUpdTile];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        const float2 h = kReg ? hc[kReg ? k : 0] : s_cs[k];
+        dot2_step(ps[(k + 1) & 3], pc[(k + 1) & 3], h.x, h.y, x[k].x, x[k].y);
+      }
+    } else if (t < tn) {  // the odd last row: global memory
+      wb = a.w[row] * invb;
+      split_df(wb, ps[0], pc[0]);
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        const float2 x = a.Vs[(int64_t)k * a.ldv + row];
+        const float2 h = s_cs[k];
+        dot2_step(ps[(k + 1) & 3], pc[(k + 1) & 3], h.x, h.y, x.x, x.y);
+      }
+    }
+    ring_release(g, kt);
+    if (t < tn) upd_finish_s(a, s_c, i, row, cok && df_window(abs_hiword(wb)), wb, ps, pc, vnext, qs, qc, q64);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
   pdl_enter();
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -1764,6 +1944,21 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
           &s_abort);
       if (!ok && lane == 0) s_abort = 1;
     }
+  } else if (nchunks == 1) {
+    bool ok = true;
+    switch (i + 1) {
+#define NSAMG_UPD_CONSUME1(NW)                                                                           \
+  case NW:                                                                                               \
+    ok = upd_consume1_s<NW>(g, a, s_c, s_cs, i, invb, cok, r0, r1, ntiles, vnext, qs, qc, q64);          \
+    break;
+      NSAMG_UPD_CONSUME1(1) NSAMG_UPD_CONSUME1(2) NSAMG_UPD_CONSUME1(3) NSAMG_UPD_CONSUME1(4)
+      NSAMG_UPD_CONSUME1(5) NSAMG_UPD_CONSUME1(6) NSAMG_UPD_CONSUME1(7) NSAMG_UPD_CONSUME1(8)
+      NSAMG_UPD_CONSUME1(9) NSAMG_UPD_CONSUME1(10) NSAMG_UPD_CONSUME1(11) NSAMG_UPD_CONSUME1(12)
+      NSAMG_UPD_CONSUME1(13) NSAMG_UPD_CONSUME1(14) NSAMG_UPD_CONSUME1(15)
+#undef NSAMG_UPD_CONSUME1
+      default: break;
+    }
+    if (!ok) s_abort = 1;
   } else {
     const int t = threadIdx.x;
     for (int kt = 0; kt < ntiles; ++kt) {
@@ -1828,29 +2023,7 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
         s_abort = 1;
         break;
       }
-      if (t < tn) {
-        double acc;
-        if (ok) {
-          df_add(ps[0], pc[0], ps[1], pc[1]);
-          df_add(ps[2], pc[2], ps[3], pc[3]);
-          df_add(ps[0], pc[0], ps[2], pc[2]);
-          // normalised pair (TwoSum): stored, squared and rounded for the FP32 copy
-          const float tt = __fadd_rn(ps[0], pc[0]);
-          const float z = __fsub_rn(tt, ps[0]);
-          const float e = __fadd_rn(__fsub_rn(ps[0], __fsub_rn(tt, z)), __fsub_rn(pc[0], z));
-          vnext[row] = make_float2(tt, e);
-          acc = widen_normal(tt) + widen_normal(e);
-          if (a.v32) a.v32[row] = tt;
-          dot2_step(qs, qc, tt, e, tt, e);
-        } else {
-          acc = wb;
-          for (int j = 0; j <= i; ++j) acc = fma(-s_c[j], join2(Vs[(int64_t)j * a.ldv + row]), acc);
-          vnext[row] = split2(acc);
-          if (a.v32) a.v32[row] = narrow_f64(acc);
-          q64 = fma(acc, acc, q64);
-        }
-        if (a.vin) a.vin[row] = acc;
-      }
+      if (t < tn) upd_finish_s(a, s_c, i, row, ok, wb, ps, pc, vnext, qs, qc, q64);
     }
   }
 #pragma unroll
