@@ -221,10 +221,13 @@ int nsamg_update_fp64(int64_t n, int i, double* d_V, int64_t ldv, const double* 
                       double* d_sumsq, void* stream);
 
 /* The split-basis kernels a solve with krylov_fp64 = 0 runs (Algorithm 1 steps 6-12 on its own
- * basis layout), on caller data. The basis is stored as (hi, lo) float pairs, 8 bytes per entry
+ * basis layout), on caller data. Each entry is stored as a (hi, lo) float pair, 8 bytes per entry
  * (column j at d_Vs + 8 j lds bytes): hi = the first 24 significant bits of the FP64 value, lo
- * the next 23 (|x - hi - lo| <= 2^-46 |x|; magnitudes below 2^-103 are stored as zero). Columns
- * hold the unnormalised vectors vt_j.
+ * the next 23 (|x - hi - lo| <= 2^-46 |x|; magnitudes below 2^-103 are stored as zero). Rows are
+ * stored in pairs: the 16 bytes of group g of a column are (hi_2g, hi_2g+1, lo_2g, lo_2g+1) as
+ * four floats, so each column takes 8 * (n rounded up to even) bytes. When n is odd, the row-n
+ * lane of the last group must be zero (nsamg_split_basis and nsamg_update_split write it so).
+ * Columns hold the unnormalised vectors vt_j.
  *   nsamg_split_basis: column j of the FP64 block d_V (ldv) -> column j of d_Vs (lds), j < ncols.
  *   nsamg_gram_split:  out[0..i] = vt_j . vt_i, out[i+1..2i+1] = vt_j . w for j = 0..i (raw
  *                      products; a solve scales them by 1 / beta_j), double-FP32 per block and
@@ -234,7 +237,8 @@ int nsamg_update_fp64(int64_t n, int i, double* d_V, int64_t ldv, const double* 
  *                      doubles) the coefficients of the stored vectors (h_j / beta_j in a solve),
  *                      stored as a pair; *d_sumsq (device) = its squared norm; d_vin (device, n
  *                      doubles, may be NULL) receives its FP64 value.
- * d_Vs and d_w must be 16-byte aligned and lds even (INVALID_ARG otherwise); 0 <= i <
+ * d_Vs and d_w must be 16-byte aligned, lds even and lds >= n rounded up to even (INVALID_ARG
+ * otherwise); 0 <= i <
  * NSAMG_MAX_RESTART and the update writes column i+1, so the block needs i+2 columns. Scratch and
  * serialisation as nsamg_gram / nsamg_update (the same two families). Asynchronous on `stream`. */
 int nsamg_split_basis(int64_t n, int ncols, const double* d_V, int64_t ldv, void* d_Vs, int64_t lds, void* stream);

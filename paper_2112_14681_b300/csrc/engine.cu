@@ -2496,9 +2496,18 @@ int nsamg_gram_fp64(int64_t n, int i, const double* d_V, int64_t ldv, const doub
   return gram_standalone(n, i, d_V, ldv, d_w, d_out, stream, true);
 }
 
+// The split-basis kernels need 16-byte aligned columns and w (the solve allocates them so), and
+// room for the last row pair.
+static bool split_aligned(const void* Vs, int64_t lds, const void* w, int64_t n) {
+  return ((reinterpret_cast<uintptr_t>(Vs) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0 && (lds & 1) == 0 &&
+         lds >= n + (n & 1);
+}
+
 int nsamg_split_basis(int64_t n, int ncols, const double* d_V, int64_t ldv, void* d_Vs, int64_t lds, void* stream) {
   if (n <= 0 || ncols < 1 || !d_V || !d_Vs || ldv < n || lds < n)
     return fail(NSAMG_ERR_INVALID_ARG, "bad split-basis arguments");
+  if (!split_aligned(d_Vs, lds, d_Vs, n))
+    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs must be 16-byte aligned, lds even and >= n rounded up to even");
   int dev = 0, sms = 148;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -2507,16 +2516,11 @@ int nsamg_split_basis(int64_t n, int ncols, const double* d_V, int64_t ldv, void
   return NSAMG_OK;
 }
 
-// The split-basis kernels need 16-byte aligned columns and w (the solve allocates them so).
-static bool split_aligned(const void* Vs, int64_t lds, const void* w) {
-  return ((reinterpret_cast<uintptr_t>(Vs) | reinterpret_cast<uintptr_t>(w)) & 15u) == 0 && (lds & 1) == 0;
-}
-
 int nsamg_gram_split(int64_t n, int i, const void* d_Vs, int64_t lds, const double* d_w, double* d_out, void* stream) {
   if (n <= 0 || i < 0 || i >= kMaxM || !d_Vs || !d_w || !d_out || lds < n)
     return fail(NSAMG_ERR_INVALID_ARG, "bad gram arguments");
-  if (!split_aligned(d_Vs, lds, d_w))
-    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned and lds even");
+  if (!split_aligned(d_Vs, lds, d_w, n))
+    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned, lds even and >= n rounded up to even");
   Scratch scr;
   int rc = standalone_scratch(&scr);
   if (rc) return rc;
@@ -2542,8 +2546,8 @@ int nsamg_update_split(int64_t n, int i, void* d_Vs, int64_t lds, const double* 
                        double* d_vin, double* d_sumsq, void* stream) {
   if (n <= 0 || i < 0 || i >= kMaxM || !d_Vs || !d_w || !d_c || !d_sumsq || lds < n || !(beta_i != 0.0))
     return fail(NSAMG_ERR_INVALID_ARG, "bad update arguments");
-  if (!split_aligned(d_Vs, lds, d_w))
-    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned and lds even");
+  if (!split_aligned(d_Vs, lds, d_w, n))
+    return fail(NSAMG_ERR_INVALID_ARG, "split basis: d_Vs, d_w must be 16-byte aligned, lds even and >= n rounded up to even");
   Scratch scr;
   int rc = standalone_scratch(&scr);
   if (rc) return rc;

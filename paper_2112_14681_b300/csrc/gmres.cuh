@@ -378,12 +378,12 @@ constexpr int kDfTile = 1024;
 // Column groups C (a power of two <= 16): the smallest C * ceil(nv / C) (the busiest warp's
 // share) with at most kDfSlots columns per warp; ties go to the smaller C, i.e. more columns per
 // warp, over which each row's fixed work (loading and splitting vt and w) is spread.
-__device__ __forceinline__ int df_groups(int nv) {
+__device__ __forceinline__ int df_groups(int nv, int max_slots = kDfSlots) {
   int best = 16, cost = 16 * ((nv + 15) / 16);
 #pragma unroll
   for (int c = 8; c >= 1; c >>= 1) {
     const int sl = (nv + c - 1) / c;
-    if (sl <= kDfSlots && c * sl <= cost) {
+    if (sl <= max_slots && c * sl <= cost) {
       best = c;
       cost = c * sl;
     }
@@ -590,9 +590,10 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
 // ------------------------------------------------------------------------------------------
 constexpr int kGramTmaConsumers = 16;
 constexpr int kGramTmaThreads = 32 * (kGramTmaConsumers + 1);
+constexpr int kRingBytes = 192 * 1024;  // stage area of a ring (all its stages)
 constexpr int kGramTmaStages = 3;
-constexpr int kGramTmaStageBytes = 64 * 1024;
-constexpr int kGramTmaSmem = kGramTmaStages * kGramTmaStageBytes + 2 * kGramTmaStages * 8;
+constexpr int kGramTmaStageBytes = kRingBytes / kGramTmaStages;
+constexpr int kGramTmaSmem = kRingBytes + 2 * 3 * 8;  // stages + full/empty barriers (up to 3 stages)
 
 // Rows per tile: the largest multiple of 32 R for which a stage (i columns + vt + w) fits,
 // at most 2048 (for i <= 64 this is always at least 32 R).
@@ -602,26 +603,29 @@ __device__ __forceinline__ int tma_tile_rows(int i, int R) {
   return t < 2048 ? t : 2048;
 }
 
-// One stage ring: kGramTmaStages buffers of kGramTmaStageBytes followed by the full and empty
-// mbarriers. Item k uses stage k % kGramTmaStages in round k / kGramTmaStages.
-struct Ring {
+// One stage ring: NST buffers of kRingBytes / NST bytes followed by the full and empty mbarriers.
+// Item k uses stage k % NST in round k / NST.
+template <int NST>
+struct RingT {
+  static constexpr int kStages = NST;
+  static constexpr int kStageBytes = kRingBytes / NST;
   double* stage;
   unsigned full0, empty0;
-  __device__ __forceinline__ double* buf(int k) const {
-    return stage + (int64_t)(k % kGramTmaStages) * (kGramTmaStageBytes / 8);
-  }
-  __device__ __forceinline__ unsigned full(int k) const { return full0 + 8u * (unsigned)(k % kGramTmaStages); }
-  __device__ __forceinline__ unsigned empty(int k) const { return empty0 + 8u * (unsigned)(k % kGramTmaStages); }
-  __device__ __forceinline__ unsigned round(int k) const { return (unsigned)(k / kGramTmaStages) & 1u; }
+  __device__ __forceinline__ double* buf(int k) const { return stage + (int64_t)(k % NST) * (kStageBytes / 8); }
+  __device__ __forceinline__ unsigned full(int k) const { return full0 + 8u * (unsigned)(k % NST); }
+  __device__ __forceinline__ unsigned empty(int k) const { return empty0 + 8u * (unsigned)(k % NST); }
+  __device__ __forceinline__ unsigned round(int k) const { return (unsigned)(k / NST) & 1u; }
 };
+using Ring = RingT<kGramTmaStages>;
 
-__device__ __forceinline__ Ring ring_init(unsigned char* dsm) {
-  Ring g;
+template <int NST>
+__device__ __forceinline__ RingT<NST> ring_init_t(unsigned char* dsm) {
+  RingT<NST> g;
   g.stage = reinterpret_cast<double*>(dsm);
-  g.full0 = smem_u32(dsm + kGramTmaStages * kGramTmaStageBytes);
-  g.empty0 = g.full0 + 8u * kGramTmaStages;
+  g.full0 = smem_u32(dsm + kRingBytes);
+  g.empty0 = g.full0 + 8u * NST;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kGramTmaStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(g.full0 + 8u * s, 1u);
       mbar_init(g.empty0 + 8u * s, (unsigned)kGramTmaConsumers);
     }
@@ -629,6 +633,7 @@ __device__ __forceinline__ Ring ring_init(unsigned char* dsm) {
   }
   return g;
 }
+__device__ __forceinline__ Ring ring_init(unsigned char* dsm) { return ring_init_t<kGramTmaStages>(dsm); }
 
 // Producer (one warp): for every item k < nitems, lane 0 waits until the item's stage is free
 // and arms its full barrier with the item's byte count, then the 32 lanes issue the item's
@@ -636,8 +641,8 @@ __device__ __forceinline__ Ring ring_init(unsigned char* dsm) {
 // of item k (nseg(k) of them), each rows(k) doubles (rounded down to even) long. Returns false
 // (in every lane) if a wait gave up; before returning, lane 0 waits (bounded) for the copies
 // still in flight.
-template <typename NSeg, typename Rows, typename Seg>
-__device__ bool ring_produce(const Ring& g, int nitems, NSeg nseg, Rows rows, Seg seg, volatile int* abort) {
+template <class RG, typename NSeg, typename Rows, typename Seg>
+__device__ bool ring_produce(const RG& g, int nitems, NSeg nseg, Rows rows, Seg seg, volatile int* abort) {
   const int lane = threadIdx.x & 31;
   int issued = 0;
   bool ok = true;
@@ -669,14 +674,14 @@ __device__ bool ring_produce(const Ring& g, int nitems, NSeg nseg, Rows rows, Se
     issued = k + 1;
   }
   if (lane == 0)
-    for (int k = (issued > kGramTmaStages ? issued - kGramTmaStages : 0); k < issued; ++k)
+    for (int k = (issued > RG::kStages ? issued - RG::kStages : 0); k < issued; ++k)
       if (!mbar_wait(g.full(k), g.round(k))) ok = false;
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
 // The same with one thread issuing every copy (k_gram_tma's producer).
-template <typename NSeg, typename Rows, typename Seg>
-__device__ bool ring_produce_lane0(const Ring& g, int nitems, NSeg nseg, Rows rows, Seg seg, volatile int* abort) {
+template <class RG, typename NSeg, typename Rows, typename Seg>
+__device__ bool ring_produce_lane0(const RG& g, int nitems, NSeg nseg, Rows rows, Seg seg, volatile int* abort) {
   int issued = 0;
   bool ok = true;
   for (int k = 0; k < nitems; ++k) {
@@ -702,19 +707,21 @@ __device__ bool ring_produce_lane0(const Ring& g, int nitems, NSeg nseg, Rows ro
     }
     issued = k + 1;
   }
-  for (int k = (issued > kGramTmaStages ? issued - kGramTmaStages : 0); k < issued; ++k)
+  for (int k = (issued > RG::kStages ? issued - RG::kStages : 0); k < issued; ++k)
     if (!mbar_wait(g.full(k), g.round(k))) ok = false;
   return ok;
 }
 
 // Consumer warp: wait for item k (every lane polls, so that no branch on the lane index leaves
 // the warp split for the tile's work); false if the wait gave up in any lane.
-__device__ __forceinline__ bool ring_acquire(const Ring& g, int k) {
+template <class RG>
+__device__ __forceinline__ bool ring_acquire(const RG& g, int k) {
   const bool ok = mbar_wait(g.full(k), g.round(k));
   return __all_sync(0xffffffffu, ok);
 }
 // One arrive per warp on the stage's empty barrier, by lane 0 through a predicate (no branch).
-__device__ __forceinline__ void ring_release(const Ring& g, int k) {
+template <class RG>
+__device__ __forceinline__ void ring_release(const RG& g, int k) {
   __syncwarp();
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %1, 0;\n\t@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(
@@ -1444,6 +1451,12 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_tma(UpdateArgs a)
 // exact power of two to unit order (k_col0) so that every stored vector lies well inside the FP32
 // range (later columns inherit unit order from the normalised Arnoldi process); the scale goes
 // into g_0, the right-hand side of the least-squares problem.
+//
+// Row-pair layout: rows 2g and 2g + 1 of a column share the 16-byte group g, stored as
+// (hi_2g, hi_2g+1, lo_2g, lo_2g+1). One 16-byte load then gives the hi parts and the lo parts of
+// two rows as the two lanes of packed FP32 pairs (below), which the Gram and update feed straight
+// into packed instructions, one row per lane. A column's bytes for rows [2g0, 2g1) are contiguous
+// as in a plain layout. When n is odd, the second lane of the last group (row n) is zero.
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 split2(double x) {
   float h, l;
@@ -1454,16 +1467,29 @@ __device__ __forceinline__ float2 split2(double x) {
 // FP64 value of a stored pair (widened by integer operations, one FP64 add)
 __device__ __forceinline__ double join2(float2 p) { return widen_normal(p.x) + widen_normal(p.y); }
 
+// (hi, lo) of row r of a row-pair column
+__device__ __forceinline__ float2 rp_get(const float2* col, int64_t r) {
+  const float* f = reinterpret_cast<const float*>(col) + 4 * (r >> 1) + (r & 1);
+  return make_float2(f[0], f[2]);
+}
+__device__ __forceinline__ void rp_set(float2* col, int64_t r, float2 v) {
+  float* f = reinterpret_cast<float*>(col) + 4 * (r >> 1) + (r & 1);
+  f[0] = v.x;
+  f[2] = v.y;
+}
+// the group of rows (2g, 2g + 1) from their pairs
+__device__ __forceinline__ float4 rp_group(float2 a, float2 b) { return make_float4(a.x, b.x, a.y, b.y); }
+
 struct Col0Args {
   int64_t n;
   double* r;      // the FP64 residual (k_resid's output); scaled in place
   float* r32;     // if set: FP32 copy of the scaled residual (FP32 V-cycle input)
-  float2* col;    // basis column 0
+  float2* col;    // basis column 0 (row-pair layout)
   GState* st;
 };
 
 // Column 0 of a cycle: s = 2^-e with ||r|| = f 2^e, f in [0.5, 1); r <- s r (exact), column 0 =
-// split(r), r0_scale = 2^e.
+// split(r), r0_scale = 2^e. One thread per row pair.
 __global__ void __launch_bounds__(kRedThreads) k_col0(Col0Args a) {
   pdl_enter();
   GState* st = a.st;
@@ -1473,21 +1499,37 @@ __global__ void __launch_bounds__(kRedThreads) k_col0(Col0Args a) {
   if (rn > 0.0 && isfinite(rn)) frexp(rn, &e);
   const double sc = ldexp(1.0, -e);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->r0_scale = ldexp(1.0, e);
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += (int64_t)gridDim.x * blockDim.x) {
-    const double x = a.r[r] * sc;
-    a.r[r] = x;
-    a.col[r] = split2(x);
-    if (a.r32) a.r32[r] = narrow_f64(x);
+  float4* col = reinterpret_cast<float4*>(a.col);
+  const int64_t ng = (a.n + 1) >> 1;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = 2 * g;
+    const bool two = r + 1 < a.n;
+    const double x0 = a.r[r] * sc;
+    const double x1 = two ? a.r[r + 1] * sc : 0.0;
+    a.r[r] = x0;
+    if (two) a.r[r + 1] = x1;
+    col[g] = rp_group(split2(x0), split2(x1));
+    if (a.r32) {
+      a.r32[r] = narrow_f64(x0);
+      if (two) a.r32[r + 1] = narrow_f64(x1);
+    }
   }
 }
 
-// Standalone conversion of FP64 columns into split pairs (column j of V -> column j of Vs).
+// Standalone conversion of FP64 columns into split row-pair columns (column j of V -> column j of
+// Vs; the second lane of the last group is zero when n is odd).
 __global__ void __launch_bounds__(kRedThreads) k_split_cols(int64_t n, int ncols, const double* __restrict__ V,
                                                             int64_t ldv, float2* __restrict__ Vs, int64_t lds) {
   pdl_enter();
-  for (int j = 0; j < ncols; ++j)
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-      Vs[(int64_t)j * lds + r] = split2(V[(int64_t)j * ldv + r]);
+  const int64_t ng = (n + 1) >> 1;
+  for (int j = 0; j < ncols; ++j) {
+    const double* v = V + (int64_t)j * ldv;
+    float4* col = reinterpret_cast<float4*>(Vs + (int64_t)j * lds);
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t r = 2 * g;
+      col[g] = rp_group(split2(v[r]), split2(r + 1 < n ? v[r + 1] : 0.0));
+    }
+  }
 }
 
 // Packed FP32 pairs (the f32x2 instructions of sm_100 and later): one instruction applies the
@@ -1522,11 +1564,13 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-// 32-bit shared-memory load (kept scalar so that two loads can fill the two halves of a pair)
-__device__ __forceinline__ float lds_f32(unsigned addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
+// 16-byte shared-memory loads: a row-pair group as two packed pairs (hi lanes, lo lanes), and two
+// FP64 values
+__device__ __forceinline__ void lds_group(unsigned addr, f2_t& hi, f2_t& lo) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(hi), "=l"(lo) : "r"(addr));
+}
+__device__ __forceinline__ void lds_d2(unsigned addr, double& x0, double& x1) {
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(x0), "=d"(x1) : "r"(addr));
 }
 
 // dot2_step in both lanes: (s, c) += (xh + xl)(bh + bl), with nbh = -bh. The product is formed
@@ -1544,43 +1588,43 @@ __device__ __forceinline__ void dot2_step2(f2_t& s, f2_t& c, f2_t xh, f2_t xl, f
   c = f2_add(c, f2_add(err, e));
 }
 
-// Column groups C of k_gram_s (a power of two <= 16), whose warps take their columns in pairs
-// (the two lanes of the packed instructions): the smallest C * pairs per warp with at most
-// kDfSlots / 2 pairs; ties go to the smaller C (more columns share each row's fixed work).
-__device__ __forceinline__ int df_pair_groups(int nv) {
-  int best = 16, cost = 16 * (((nv + 15) / 16 + 1) / 2);
-#pragma unroll
-  for (int c = 8; c >= 1; c >>= 1) {
-    const int np = ((nv + c - 1) / c + 1) / 2;
-    if (np <= kDfSlots / 2 && c * np <= cost) {
-      best = c;
-      cost = c * np;
-    }
-  }
-  return best;
+// df_add in both lanes: (s, c) += (s2, c2)
+__device__ __forceinline__ void df_add2(f2_t& s, f2_t& c, f2_t s2, f2_t c2) {
+  const f2_t t = f2_add(s, s2);
+  const f2_t z = f2_sub(t, s);
+  const f2_t err = f2_add(f2_sub(s, f2_sub(t, z)), f2_sub(s2, z));
+  s = t;
+  c = f2_add(c, f2_add(c2, err));
 }
 
-// Consumer warp of k_gram_s: every tile of the block's chunk, rows dealt to the R row-group warps
-// in 32-row groups (round robin), times the warp's 2 NP columns cg + sl C, taken in pairs
-// (slots 2p, 2p + 1) by the packed instructions; slots past the last column read column nv - 1
-// and their products are discarded. The products are against column i (the stage's column
-// nv - 1, already split) and w (FP64 at stage column nv, split here). The tile loop sits inside
-// the pair-count specialisation so the accumulators keep their registers from tile to tile.
-// Returns false if a wait gave up.
-template <int NP>
-__device__ __forceinline__ bool gram_consume_s(const Ring& g, const float2* __restrict__ Vs, const double* __restrict__ w,
+// Columns per warp in k_gram_s: its packed (sum, error) accumulators take 8 registers a column,
+// and a 17-warp block leaves at most 96 registers a thread; fewer columns a warp also give each
+// warp more row pairs of a tile (measured best at 4).
+constexpr int kGramSSlots = 4;
+
+// Consumer warp of k_gram_s: every tile of the block's chunk, row pairs dealt to the R row-group
+// warps in groups of 32 pairs (round robin), times the warp's NS columns cg + sl C (only the last
+// slot can pass the last column; its discarded products then read column nv - 1), against column
+// i (the stage's column nv - 1) and w (FP64 at stage column nv, split here). Each thread works on
+// a row pair with packed instructions, one row per lane, and keeps (sum, error) pairs per lane;
+// the two lanes are added at the end. The tile loop sits inside the slot-count specialisation so
+// the accumulators keep their registers from tile to tile. Returns false if a wait gave up.
+template <int NS, class RG>
+__device__ __forceinline__ bool gram_consume_s(const RG& g, const float2* __restrict__ Vs, const double* __restrict__ w,
                                                int64_t ldv, int nv, int T, int C, int cg, int rg, int R, int64_t r0,
-                                               int64_t r1, int ntiles, float (&sa)[kDfSlots], float (&ca)[kDfSlots],
-                                               float (&sw)[kDfSlots], float (&cw)[kDfSlots], unsigned& mx) {
-  constexpr int NS = 2 * NP;
+                                               int64_t r1, int ntiles, float (&sa)[kGramSSlots],
+                                               float (&ca)[kGramSSlots], float (&sw)[kGramSSlots],
+                                               float (&cw)[kGramSSlots], unsigned& mx) {
   const int lane = threadIdx.x & 31;
-  f2_t s_a[NP], c_a[NP], s_w[NP], c_w[NP];
+  f2_t s_a[NS], c_a[NS], s_w[NS], c_w[NS];
   unsigned offb[NS];  // byte offset of each slot's column in a stage
 #pragma unroll
-  for (int q = 0; q < NP; ++q) s_a[q] = c_a[q] = s_w[q] = c_w[q] = 0ull;
-#pragma unroll
-  for (int sl = 0; sl < NS; ++sl) offb[sl] = 8u * (unsigned)(min(cg + sl * C, nv - 1) * T);
-  const int offv = (nv - 1) * T, offw = nv * T;
+  for (int sl = 0; sl < NS; ++sl) {
+    s_a[sl] = c_a[sl] = s_w[sl] = c_w[sl] = 0ull;
+    offb[sl] = 8u * (unsigned)(min(cg + sl * C, nv - 1) * T);
+  }
+  const unsigned offv = 8u * (unsigned)((nv - 1) * T), offw = 8u * (unsigned)(nv * T);
+  const f2_t m1 = f2_pack(-1.f, -1.f);
   const int step = 32 * R;
   bool ok = true;
   int64_t t0 = r0;
@@ -1590,60 +1634,125 @@ __device__ __forceinline__ bool gram_consume_s(const Ring& g, const float2* __re
       break;
     }
     const int tn = (int)min((int64_t)T, r1 - t0), te = tn & ~1;
-    const double* sb = g.buf(k);
-    const float2* __restrict__ sp = reinterpret_cast<const float2*>(sb);
-    const unsigned base = smem_u32(sb);
-    // unrolled by two so that the TwoSum results alternate registers instead of moving back
-#pragma unroll 2
-    for (int r = rg * 32 + lane; r < te; r += step) {
-      const float2 q = sp[offv + r];
-      const double xw = sb[offw + r];
-      mx = max(mx, abs_hiword(xw));
-      float q2, q3;
-      split_df(xw, q2, q3);
-      const f2_t ah = f2_pack(q.x, q.x), al = f2_pack(q.y, q.y), nah = f2_pack(-q.x, -q.x);
-      const f2_t bh = f2_pack(q2, q2), bl = f2_pack(q3, q3), nbh = f2_pack(-q2, -q2);
-      const unsigned rb = base + 8u * (unsigned)r;
-      f2_t xh[NP], xl[NP];
+    const unsigned base = smem_u32(g.buf(k));
+    for (int pr = rg * 32 + lane; pr < (te >> 1); pr += step) {
+      const unsigned rb = base + 16u * (unsigned)pr;
+      f2_t qh, ql;
+      lds_group(rb + offv, qh, ql);
+      double w0, w1;
+      lds_d2(rb + offw, w0, w1);
+      mx = max(mx, max(abs_hiword(w0), abs_hiword(w1)));
+      float wh0, wl0, wh1, wl1;
+      split_df(w0, wh0, wl0);
+      split_df(w1, wh1, wl1);
+      const f2_t wh = f2_pack(wh0, wh1), wl = f2_pack(wl0, wl1);
+      const f2_t nqh = f2_mul(qh, m1), nwh = f2_mul(wh, m1);
+      f2_t xh[NS], xl[NS];
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        xh[p] = f2_pack(lds_f32(rb + offb[2 * p]), lds_f32(rb + offb[2 * p + 1]));
-        xl[p] = f2_pack(lds_f32(rb + offb[2 * p] + 4u), lds_f32(rb + offb[2 * p + 1] + 4u));
-      }
+      for (int sl = 0; sl < NS; ++sl) lds_group(rb + offb[sl], xh[sl], xl[sl]);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        dot2_step2(s_a[p], c_a[p], xh[p], xl[p], ah, al, nah);
-        dot2_step2(s_w[p], c_w[p], xh[p], xl[p], bh, bl, nbh);
+      for (int sl = 0; sl < NS; ++sl) {
+        dot2_step2(s_a[sl], c_a[sl], xh[sl], xl[sl], qh, ql, nqh);
+        dot2_step2(s_w[sl], c_w[sl], xh[sl], xl[sl], wh, wl, nwh);
       }
     }
-    if (te < tn && (te >> 5) % R == rg && lane == 0) {  // the odd last row (its 32-row group's warp)
+    if (te < tn && ((te >> 1) >> 5) % R == rg && lane == 0) {  // the odd last row (its pair group's warp)
       const int64_t row = t0 + te;
-      const float2 q = Vs[(int64_t)(nv - 1) * ldv + row];
+      const float2 q = rp_get(Vs + (int64_t)(nv - 1) * ldv, row);
       const double xw = w[row];
       mx = max(mx, abs_hiword(xw));
       float q2, q3;
       split_df(xw, q2, q3);
-      const f2_t ah = f2_pack(q.x, q.x), al = f2_pack(q.y, q.y), nah = f2_pack(-q.x, -q.x);
-      const f2_t bh = f2_pack(q2, q2), bl = f2_pack(q3, q3), nbh = f2_pack(-q2, -q2);
+      const f2_t qh = f2_pack(q.x, 0.f), ql = f2_pack(q.y, 0.f), nqh = f2_pack(-q.x, 0.f);
+      const f2_t wh = f2_pack(q2, 0.f), wl = f2_pack(q3, 0.f), nwh = f2_pack(-q2, 0.f);
 #pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const float2 x0 = Vs[(int64_t)min(cg + 2 * p * C, nv - 1) * ldv + row];
-        const float2 x1 = Vs[(int64_t)min(cg + (2 * p + 1) * C, nv - 1) * ldv + row];
-        const f2_t xh = f2_pack(x0.x, x1.x), xl = f2_pack(x0.y, x1.y);
-        dot2_step2(s_a[p], c_a[p], xh, xl, ah, al, nah);
-        dot2_step2(s_w[p], c_w[p], xh, xl, bh, bl, nbh);
+      for (int sl = 0; sl < NS; ++sl) {
+        const float2 x = rp_get(Vs + (int64_t)min(cg + sl * C, nv - 1) * ldv, row);
+        const f2_t xh = f2_pack(x.x, 0.f), xl = f2_pack(x.y, 0.f);
+        dot2_step2(s_a[sl], c_a[sl], xh, xl, qh, ql, nqh);
+        dot2_step2(s_w[sl], c_w[sl], xh, xl, wh, wl, nwh);
       }
     }
     ring_release(g, k);
   }
 #pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    f2_unpack(s_a[p], sa[2 * p], sa[2 * p + 1]);
-    f2_unpack(c_a[p], ca[2 * p], ca[2 * p + 1]);
-    f2_unpack(s_w[p], sw[2 * p], sw[2 * p + 1]);
-    f2_unpack(c_w[p], cw[2 * p], cw[2 * p + 1]);
+  for (int sl = 0; sl < NS; ++sl) {  // lane sums: even rows + odd rows
+    float s0, s1, c0, c1;
+    f2_unpack(s_a[sl], s0, s1);
+    f2_unpack(c_a[sl], c0, c1);
+    df_add(s0, c0, s1, c1);
+    sa[sl] = s0;
+    ca[sl] = c0;
+    f2_unpack(s_w[sl], s0, s1);
+    f2_unpack(c_w[sl], c0, c1);
+    df_add(s0, c0, s1, c1);
+    sw[sl] = s0;
+    cw[sl] = c0;
   }
   return ok;
+}
+
+// The streaming part of k_gram_s with an NST-stage ring: tiles of T rows (the largest multiple of
+// 32 for which a stage holds columns 0..i and w, at most 2048), the block's row range [r0, r1),
+// the producer warp and the consumer warps' products. Few columns stream best through three
+// stages; many columns (short tiles) through two larger ones.
+constexpr int kGramTwoStageCols = 30;
+
+template <int NST>
+__device__ __forceinline__ void gram_s_stream(const GramArgs& a, unsigned char* dsm, int nv, int C, int cg, int rg,
+                                              int R, int S, int& T_out, int64_t& r0_out, int64_t& r1_out,
+                                              float (&sa)[kGramSSlots], float (&ca)[kGramSSlots],
+                                              float (&sw)[kGramSSlots], float (&cw)[kGramSSlots], unsigned& mx,
+                                              unsigned* s_max,
+                                              volatile int* s_abort) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = min(2048, RingT<NST>::kStageBytes / (8 * (nv + 1)) / 32 * 32);
+  const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + T - 1) / T * T;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk;
+  const int64_t r1 = min(a.n, r0 + chunk);
+  T_out = T;
+  r0_out = r0;
+  r1_out = r1;
+  const int ntiles = r1 > r0 ? (int)((r1 - r0 + T - 1) / T) : 0;
+  const float2* Vs = a.Vs;
+  const RingT<NST> g = ring_init_t<NST>(dsm);
+  if (threadIdx.x == 0) {
+    *s_max = 0u;
+    *s_abort = 0;
+  }
+  __syncthreads();
+  auto tile_rows = [&](int k) -> int {
+    const int64_t t0 = r0 + (int64_t)k * T;
+    return (int)((r1 - t0) < (int64_t)T ? (r1 - t0) : (int64_t)T);
+  };
+  if (warp == kGramTmaConsumers) {
+    {  // producer warp: per tile the columns 0..i and w
+      const bool ok = ring_produce(
+          g, ntiles, [&](int) { return nv + 1; }, tile_rows,
+          [&](int k, int q, const double** src, int* off) {
+            const int64_t t0 = r0 + (int64_t)k * T;
+            *src = q < nv ? reinterpret_cast<const double*>(Vs + (int64_t)q * a.ldv + t0) : a.w + t0;
+            *off = q * T;
+          },
+          s_abort);
+      if (!ok && lane == 0) *s_abort = 1;
+    }
+  } else {
+    bool ok = true;
+    switch (S) {
+#define NSAMG_GRAM_CONSUME_S(NS)                                                                         \
+  case NS:                                                                                               \
+    ok = gram_consume_s<NS>(g, Vs, a.w, a.ldv, nv, T, C, cg, rg, R, r0, r1, ntiles, sa, ca, sw, cw, mx); \
+    break;
+      NSAMG_GRAM_CONSUME_S(1)
+      NSAMG_GRAM_CONSUME_S(2)
+      NSAMG_GRAM_CONSUME_S(3)
+      NSAMG_GRAM_CONSUME_S(4)
+#undef NSAMG_GRAM_CONSUME_S
+      default: break;
+    }
+    if (!ok) *s_abort = 1;
+  }
 }
 
 // Gram on the split basis with the bulk-copy ring: a_j = vt_j . vt_i and s_j = vt_j . w for
@@ -1662,59 +1771,21 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
   const int i = st ? st->i : a.i_standalone;
   const int nv = i + 1;  // columns 0..i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = df_pair_groups(nv);
+  const int C = df_groups(nv, kGramSSlots);
   const int R = kGramWarps / C;
-  const int S = 2 * (((nv + C - 1) / C + 1) / 2);  // slots per warp (pairs of columns)
-  // rows per tile: the largest multiple of 32 for which the stage (columns 0..i and w) fits
-  const int T = min(2048, kGramTmaStageBytes / (8 * (nv + 1)) / 32 * 32);
-  const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + T - 1) / T * T;
-  const int64_t r0 = (int64_t)blockIdx.x * chunk;
-  const int64_t r1 = min(a.n, r0 + chunk);
-  const int ntiles = r1 > r0 ? (int)((r1 - r0 + T - 1) / T) : 0;
-  const float2* Vs = a.Vs;
-  const Ring g = ring_init(dsm);
-  if (threadIdx.x == 0) {
-    s_max = 0u;
-    s_abort = 0;
-  }
-  __syncthreads();
-  float sa[kDfSlots], ca[kDfSlots], sw[kDfSlots], cw[kDfSlots];
+  const int S = (nv + C - 1) / C;
+  float sa[kGramSSlots], ca[kGramSSlots], sw[kGramSSlots], cw[kGramSSlots];
 #pragma unroll
-  for (int sl = 0; sl < kDfSlots; ++sl) sa[sl] = ca[sl] = sw[sl] = cw[sl] = 0.f;
+  for (int sl = 0; sl < kGramSSlots; ++sl) sa[sl] = ca[sl] = sw[sl] = cw[sl] = 0.f;
   unsigned mx = 0u;
   const int cg = warp % C, rg = warp / C;
-  auto tile_rows = [&](int k) -> int {
-    const int64_t t0 = r0 + (int64_t)k * T;
-    return (int)((r1 - t0) < (int64_t)T ? (r1 - t0) : (int64_t)T);
-  };
-  if (warp == kGramTmaConsumers) {
-    {  // producer warp: per tile the columns 0..i and w
-      const bool ok = ring_produce(
-          g, ntiles, [&](int) { return nv + 1; }, tile_rows,
-          [&](int k, int q, const double** src, int* off) {
-            const int64_t t0 = r0 + (int64_t)k * T;
-            *src = q < nv ? reinterpret_cast<const double*>(Vs + (int64_t)q * a.ldv + t0) : a.w + t0;
-            *off = q * T;
-          },
-          &s_abort);
-      if (!ok && lane == 0) s_abort = 1;
-    }
-  } else {
-    bool ok = true;
-    switch (S / 2) {
-#define NSAMG_GRAM_CONSUME_S(NP)                                                                         \
-  case NP:                                                                                               \
-    ok = gram_consume_s<NP>(g, Vs, a.w, a.ldv, nv, T, C, cg, rg, R, r0, r1, ntiles, sa, ca, sw, cw, mx); \
-    break;
-      NSAMG_GRAM_CONSUME_S(1)
-      NSAMG_GRAM_CONSUME_S(2)
-      NSAMG_GRAM_CONSUME_S(3)
-      NSAMG_GRAM_CONSUME_S(4)
-#undef NSAMG_GRAM_CONSUME_S
-      default: break;
-    }
-    if (!ok) s_abort = 1;
-  }
+  int T;
+  int64_t r0, r1;
+  const float2* Vs = a.Vs;
+  if (nv < kGramTwoStageCols)
+    gram_s_stream<3>(a, dsm, nv, C, cg, rg, R, S, T, r0, r1, sa, ca, sw, cw, mx, &s_max, &s_abort);
+  else
+    gram_s_stream<2>(a, dsm, nv, C, cg, rg, R, S, T, r0, r1, sa, ca, sw, cw, mx, &s_max, &s_abort);
   if (warp < kGramTmaConsumers) {
     mx = __reduce_max_sync(0xffffffffu, mx);
     if (lane == 0) atomicMax(&s_max, mx);
@@ -1727,10 +1798,10 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
       float as[16], ac[16];
 #pragma unroll
       for (int sl = 0; sl < kDfSlots; ++sl) {
-        as[2 * sl] = sa[sl];
-        ac[2 * sl] = ca[sl];
-        as[2 * sl + 1] = sw[sl];
-        ac[2 * sl + 1] = cw[sl];
+        as[2 * sl] = sl < kGramSSlots ? sa[sl < kGramSSlots ? sl : 0] : 0.f;
+        ac[2 * sl] = sl < kGramSSlots ? ca[sl < kGramSSlots ? sl : 0] : 0.f;
+        as[2 * sl + 1] = sl < kGramSSlots ? sw[sl < kGramSSlots ? sl : 0] : 0.f;
+        ac[2 * sl + 1] = sl < kGramSSlots ? cw[sl < kGramSSlots ? sl : 0] : 0.f;
       }
       df_warp_reduce16(as, ac);
       const int qd = lane >> 1, sl = qd >> 1, j = cg + sl * C;
@@ -1747,8 +1818,8 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
           const float2* vj = Vs + (int64_t)j * a.ldv;
           for (int64_t t0 = r0; t0 < r1; t0 += T)
             for (int r = rg * 32 + lane; r < T && t0 + r < r1; r += 32 * R) {
-              const double x = join2(vj[t0 + r]);
-              fa = fma(x, join2(vi[t0 + r]), fa);
+              const double x = join2(rp_get(vj, t0 + r));
+              fa = fma(x, join2(rp_get(vi, t0 + r)), fa);
               fw = fma(x, a.w[t0 + r], fw);
             }
         }
@@ -1778,117 +1849,71 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Update on the split basis with the bulk-copy ring (one consumer thread per row of a 512-row
-// tile, columns streamed in chunks of kUpdChunk: w first, then vt_0 .. vt_i):
+// Update on the split basis with the bulk-copy ring (one consumer thread per row pair of a
+// 1024-row tile, columns streamed through three 64 KB stages in chunks of kUpdSChunk: w first,
+// then vt_0 .. vt_i):
 //   vt_{i+1} = w / beta_i - sum_{j<=i} (h_j / beta_j) vt_j,
-// w / beta_i formed in FP64 (one multiply) and split, the sum in four (sum, error) pairs; the
-// result is stored as a normalised pair in column i+1 and, for the next V-cycle, as FP64 in vin
-// or rounded to FP32 in v32. ||vt_{i+1}||^2 in double-FP32 per thread, FP64 across blocks. Rows
-// whose w / beta_i leaves the double-FP32 window, and every row when the coefficients do, are
-// computed in FP64 from the stored pairs.
+// w / beta_i formed in FP64 (one multiply a row) and split, the sum in four (sum, error) pairs
+// of packed instructions (one row per lane); the result is stored as a normalised row-pair group
+// in column i+1 and, for the next V-cycle, as FP64 in vin or rounded to FP32 in v32.
+// ||vt_{i+1}||^2 in double-FP32 per thread, FP64 across blocks. Row pairs in which w / beta_i
+// leaves the double-FP32 window, and every row when the coefficients do, are computed in FP64
+// from the stored pairs, as is the odd last row of an odd n.
 // ------------------------------------------------------------------------------------------
-// NW columns of a staged chunk for one row: column k (stride kUpdTile pairs) with coefficient
-// hs[k] into pair k mod 4.
-template <int NW>
-__device__ __forceinline__ void upd_cols_s(const float2* __restrict__ col, const float2* __restrict__ hs,
-                                           float (&ps)[4], float (&pc)[4]) {
-  float2 x[NW];
+constexpr int kUpdPairs = 32 * kGramTmaConsumers;                   // row pairs per tile (one per consumer)
+constexpr int kUpdSTile = 2 * kUpdPairs;                            // rows per tile (1024)
+constexpr int kUpdSStages = 3;                                      // three 64 KB stages
+constexpr int kUpdSChunk = RingT<kUpdSStages>::kStageBytes / (8 * kUpdSTile);  // columns per stage (8)
+constexpr unsigned kUpdColBytes = 8u * kUpdSTile;                   // bytes of one column in a stage
+static_assert(kUpdSChunk == 8, "k_update_s dispatches chunk widths 1..8");
+
+// Coefficient of basis column j in shared memory: the split (h, l) of -h_j / beta_j as the pairs
+// (h, h), (l, l) and (-h, -h), each value in both lanes.
+struct __align__(16) UpdCoef {
+  float4 hl;  // (h, h, l, l)
+  float4 nh;  // (-h, -h, 0, 0)
+};
+
+__device__ __forceinline__ f2_t lds_pair(unsigned addr) {
+  f2_t v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
+
+// NW staged columns of a chunk for one row pair: column k at byte k * kUpdColBytes from addr,
+// coefficient record cf + k, into pair accumulator (K0 + k) mod 4 (the global column's index
+// mod 4, with column 0 = w).
+template <int NW, int K0>
+__device__ __forceinline__ void upd_cols_s(unsigned addr, unsigned cf, f2_t (&ps)[4], f2_t (&pc)[4]) {
+  f2_t xh[NW], xl[NW];
 #pragma unroll
-  for (int k = 0; k < NW; ++k) x[k] = col[k * kUpdTile];
+  for (int k = 0; k < NW; ++k) lds_group(addr + (unsigned)k * kUpdColBytes, xh[k], xl[k]);
 #pragma unroll
   for (int k = 0; k < NW; ++k) {
-    const float2 h = hs[k];
-    dot2_step(ps[k & 3], pc[k & 3], h.x, h.y, x[k].x, x[k].y);
+    f2_t hh, hl;
+    lds_group(cf + 32u * k, hh, hl);
+    const f2_t nh = lds_pair(cf + 32u * k + 16u);
+    dot2_step2(ps[(K0 + k) & 3], pc[(K0 + k) & 3], xh[k], xl[k], hh, hl, nh);
   }
 }
 
-// The end of one row of k_update_s: the four (sum, error) pairs summed and normalised, stored as
-// the pair of column i+1 and (if requested) as FP64 in vin or FP32 in v32, its square added to the
-// thread's ||vt_{i+1}||^2. A row that left the double-FP32 window (ok false) is recomputed in
-// FP64 from w / beta_i and the stored pairs.
-__device__ __forceinline__ void upd_finish_s(const UpdateArgs& a, const double* __restrict__ s_c, int i, int64_t row,
-                                             bool ok, double wb, float (&ps)[4], float (&pc)[4], float2* vnext,
-                                             float& qs, float& qc, double& q64) {
-  double acc;
-  if (ok) {
-    df_add(ps[0], pc[0], ps[1], pc[1]);
-    df_add(ps[2], pc[2], ps[3], pc[3]);
-    df_add(ps[0], pc[0], ps[2], pc[2]);
-    // normalised pair (TwoSum): stored, squared and rounded for the FP32 copy
-    const float tt = __fadd_rn(ps[0], pc[0]);
-    const float z = __fsub_rn(tt, ps[0]);
-    const float e = __fadd_rn(__fsub_rn(ps[0], __fsub_rn(tt, z)), __fsub_rn(pc[0], z));
-    vnext[row] = make_float2(tt, e);
-    acc = widen_normal(tt) + widen_normal(e);
-    if (a.v32) a.v32[row] = tt;
-    dot2_step(qs, qc, tt, e, tt, e);
-  } else {
-    acc = wb;
-    for (int j = 0; j <= i; ++j) acc = fma(-s_c[j], join2(a.Vs[(int64_t)j * a.ldv + row]), acc);
-    vnext[row] = split2(acc);
-    if (a.v32) a.v32[row] = narrow_f64(acc);
-    q64 = fma(acc, acc, q64);
-  }
+// FP64 recomputation of one row (outside the double-FP32 window, or the odd last row)
+__device__ __forceinline__ double upd_row_fp64(const UpdateArgs& a, const double* __restrict__ s_c, int i, int64_t row,
+                                               double wb, float2* vnext, double& q64) {
+  double acc = wb;
+  for (int j = 0; j <= i; ++j) acc = fma(-s_c[j], join2(rp_get(a.Vs + (int64_t)j * a.ldv, row)), acc);
+  rp_set(vnext, row, split2(acc));
+  if (a.v32) a.v32[row] = narrow_f64(acc);
   if (a.vin) a.vin[row] = acc;
-}
-
-constexpr int kUpdRegCoefs = 12;
-
-// Consumer of k_update_s when w and all NW = i + 1 basis columns fit one chunk (i < kUpdChunk - 1):
-// the coefficients stay in registers and the tile loop sits inside the width specialisation.
-// Returns false if a wait gave up.
-template <int NW>
-__device__ __forceinline__ bool upd_consume1_s(const Ring& g, const UpdateArgs& a, const double* __restrict__ s_c,
-                                               const float2* __restrict__ s_cs, int i, double invb, bool cok,
-                                               int64_t r0, int64_t r1, int ntiles, float2* vnext, float& qs, float& qc,
-                                               double& q64) {
-  const int t = threadIdx.x;
-  // coefficients: in registers up to kUpdRegCoefs columns, else read (broadcast) from shared memory
-  constexpr bool kReg = NW <= kUpdRegCoefs;
-  float2 hc[kReg ? NW : 1];
-#pragma unroll
-  for (int k = 0; k < (kReg ? NW : 1); ++k) hc[k] = s_cs[k];
-  int64_t t0 = r0;
-  for (int kt = 0; kt < ntiles; ++kt, t0 += kUpdTile) {
-    if (!ring_acquire(g, kt)) return false;
-    const int tn = (int)min((int64_t)kUpdTile, r1 - t0), te = tn & ~1;
-    const int64_t row = t0 + t;
-    float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
-    double wb = 0.0;
-    if (t < te) {  // from the stage: column 0 is w, column 1 + j is vt_j
-      const double* sb = g.buf(kt);
-      wb = sb[t] * invb;
-      split_df(wb, ps[0], pc[0]);
-      const float2* __restrict__ col = reinterpret_cast<const float2*>(sb) + kUpdTile + t;
-      float2 x[NW];
-#pragma unroll
-      for (int k = 0; k < NW; ++k) x[k] = col[k * kUpdTile];
-#pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const float2 h = kReg ? hc[kReg ? k : 0] : s_cs[k];
-        dot2_step(ps[(k + 1) & 3], pc[(k + 1) & 3], h.x, h.y, x[k].x, x[k].y);
-      }
-    } else if (t < tn) {  // the odd last row: global memory
-      wb = a.w[row] * invb;
-      split_df(wb, ps[0], pc[0]);
-#pragma unroll
-      for (int k = 0; k < NW; ++k) {
-        const float2 x = a.Vs[(int64_t)k * a.ldv + row];
-        const float2 h = s_cs[k];
-        dot2_step(ps[(k + 1) & 3], pc[(k + 1) & 3], h.x, h.y, x.x, x.y);
-      }
-    }
-    ring_release(g, kt);
-    if (t < tn) upd_finish_s(a, s_c, i, row, cok && df_window(abs_hiword(wb)), wb, ps, pc, vnext, qs, qc, q64);
-  }
-  return true;
+  q64 = fma(acc, acc, q64);
+  return acc;
 }
 
 __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
   pdl_enter();
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ double s_c[kMaxM + 1];   // h_j / beta_j
-  __shared__ float2 s_cs[kMaxM + 1];  // -h_j / beta_j as (hi, lo)
+  __shared__ double s_c[kMaxM + 1];    // h_j / beta_j
+  __shared__ UpdCoef s_cf[kMaxM + 1];  // -h_j / beta_j split, in both lanes
   __shared__ double s_red[kGramTmaConsumers];
   __shared__ unsigned s_cmax;
   __shared__ volatile int s_abort;
@@ -1899,7 +1924,7 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
   }
   const int i = st ? st->i : a.i_standalone;
   const double invb = st ? st->invbeta[i] : a.invbeta_standalone;
-  const Ring g = ring_init(dsm);
+  const RingT<kUpdSStages> g = ring_init_t<kUpdSStages>(dsm);
   if (threadIdx.x == 0) {
     s_cmax = 0u;
     s_abort = 0;
@@ -1908,123 +1933,147 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_update_s(UpdateArgs a) {
   for (int j = threadIdx.x; j <= i; j += blockDim.x) {
     const double cj = st ? st->h[j] * st->invbeta[j] : a.coef_standalone[j];
     s_c[j] = cj;
-    s_cs[j] = split2(-cj);
+    const float2 h = split2(-cj);
+    s_cf[j].hl = make_float4(h.x, h.x, h.y, h.y);
+    s_cf[j].nh = make_float4(-h.x, -h.x, 0.f, 0.f);
     atomicMax(&s_cmax, abs_hiword(cj));
   }
   __syncthreads();
   const bool cok = df_window(s_cmax);
   const float2* Vs = a.Vs;
   float2* vnext = a.Vs + (int64_t)(i + 1) * a.ldv;
-  const int ncols = i + 2, nchunks = (ncols + kUpdChunk - 1) / kUpdChunk;  // column 0: w, 1 + j: vt_j
-  const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + kUpdTile - 1) / kUpdTile * kUpdTile;
+  const int ncols = i + 2, nchunks = (ncols + kUpdSChunk - 1) / kUpdSChunk;  // column 0: w, 1 + j: vt_j
+  const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + kUpdSTile - 1) / kUpdSTile * kUpdSTile;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(a.n, r0 + chunk);
-  const int ntiles = r1 > r0 ? (int)((r1 - r0 + kUpdTile - 1) / kUpdTile) : 0;
+  const int ntiles = r1 > r0 ? (int)((r1 - r0 + kUpdSTile - 1) / kUpdSTile) : 0;
   const int nitems = ntiles * nchunks;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto tile_rows = [&](int kt) -> int {
-    const int64_t t0 = r0 + (int64_t)kt * kUpdTile;
-    return (int)((r1 - t0) < (int64_t)kUpdTile ? (r1 - t0) : (int64_t)kUpdTile);
+    const int64_t t0 = r0 + (int64_t)kt * kUpdSTile;
+    return (int)((r1 - t0) < (int64_t)kUpdSTile ? (r1 - t0) : (int64_t)kUpdSTile);
   };
   auto col_ptr = [&](int c) -> const double* {
     return c == 0 ? a.w : reinterpret_cast<const double*>(Vs + (int64_t)(c - 1) * a.ldv);
   };
-  float qs = 0.f, qc = 0.f;
+  const bool vin16 = a.vin && (reinterpret_cast<uintptr_t>(a.vin) & 15u) == 0;
+  f2_t qs2 = 0ull, qc2 = 0ull;
   double q64 = 0.0;
   if (warp == kGramTmaConsumers) {
     {  // producer warp
       const bool ok = ring_produce(
-          g, nitems, [&](int k) { const int cb = (k % nchunks) * kUpdChunk; return min(ncols, cb + kUpdChunk) - cb; },
+          g, nitems, [&](int k) { const int cb = (k % nchunks) * kUpdSChunk; return min(ncols, cb + kUpdSChunk) - cb; },
           [&](int k) { return tile_rows(k / nchunks); },
           [&](int k, int q, const double** src, int* off) {
-            const int c = (k % nchunks) * kUpdChunk + q;
-            *src = col_ptr(c) + r0 + (int64_t)(k / nchunks) * kUpdTile;
-            *off = q * kUpdTile;
+            const int c = (k % nchunks) * kUpdSChunk + q;
+            *src = col_ptr(c) + r0 + (int64_t)(k / nchunks) * kUpdSTile;
+            *off = q * kUpdSTile;
           },
           &s_abort);
       if (!ok && lane == 0) s_abort = 1;
     }
-  } else if (nchunks == 1) {
-    bool ok = true;
-    switch (i + 1) {
-#define NSAMG_UPD_CONSUME1(NW)                                                                           \
-  case NW:                                                                                               \
-    ok = upd_consume1_s<NW>(g, a, s_c, s_cs, i, invb, cok, r0, r1, ntiles, vnext, qs, qc, q64);          \
-    break;
-      NSAMG_UPD_CONSUME1(1) NSAMG_UPD_CONSUME1(2) NSAMG_UPD_CONSUME1(3) NSAMG_UPD_CONSUME1(4)
-      NSAMG_UPD_CONSUME1(5) NSAMG_UPD_CONSUME1(6) NSAMG_UPD_CONSUME1(7) NSAMG_UPD_CONSUME1(8)
-      NSAMG_UPD_CONSUME1(9) NSAMG_UPD_CONSUME1(10) NSAMG_UPD_CONSUME1(11) NSAMG_UPD_CONSUME1(12)
-      NSAMG_UPD_CONSUME1(13) NSAMG_UPD_CONSUME1(14) NSAMG_UPD_CONSUME1(15)
-#undef NSAMG_UPD_CONSUME1
-      default: break;
-    }
-    if (!ok) s_abort = 1;
   } else {
     const int t = threadIdx.x;
-    for (int kt = 0; kt < ntiles; ++kt) {
+    const unsigned cf0 = smem_u32(s_cf);
+    const f2_t m1 = f2_pack(-1.f, -1.f);
+    bool aborted = false;
+    for (int kt = 0; kt < ntiles && !aborted; ++kt) {
       const int tn = tile_rows(kt), te = tn & ~1;
-      const int64_t row = r0 + (int64_t)kt * kUpdTile + t;
-      float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
-      double wb = 0.0;
-      bool ok = cok;
-      bool aborted = false;
+      const int64_t row = r0 + (int64_t)kt * kUpdSTile + 2 * t;  // this thread's rows: row, row + 1
+      const bool staged = 2 * t < te;
+      f2_t ps[4] = {0ull, 0ull, 0ull, 0ull}, pc[4] = {0ull, 0ull, 0ull, 0ull};
+      double wb0 = 0.0, wb1 = 0.0;
       for (int kc = 0; kc < nchunks; ++kc) {
         const int k = kt * nchunks + kc;
         if (!ring_acquire(g, k)) {
           aborted = true;
           break;
         }
-        const int cb = kc * kUpdChunk, ce = min(ncols, cb + kUpdChunk);
-        const double* sb = g.buf(k);
-        if (t < te) {  // from the stage: a branch-free body per chunk width
-          int c = 0;
+        if (staged) {
+          const int cb = kc * kUpdSChunk, ce = min(ncols, cb + kUpdSChunk);
+          const unsigned addr = smem_u32(g.buf(k)) + 16u * (unsigned)t;
           if (kc == 0) {  // column 0 is w
-            wb = sb[t] * invb;
-            ok = ok && df_window(abs_hiword(wb));
-            split_df(wb, ps[0], pc[0]);
-            c = 1;
-          }
-          const float2* col = reinterpret_cast<const float2*>(sb) + c * kUpdTile + t;
-          const float2* hs = s_cs + cb + c - 1;
-          switch (ce - cb - c) {
+            double w0, w1;
+            lds_d2(addr, w0, w1);
+            wb0 = w0 * invb;
+            wb1 = w1 * invb;
+            float h0, l0, h1, l1;
+            split_df(wb0, h0, l0);
+            split_df(wb1, h1, l1);
+            ps[0] = f2_pack(h0, h1);
+            pc[0] = f2_pack(l0, l1);
+            switch (ce - 1) {
+#define NSAMG_UPD_COLS0(NW) \
+  case NW:                  \
+    upd_cols_s<NW, 1>(addr + kUpdColBytes, cf0, ps, pc); \
+    break;
+              NSAMG_UPD_COLS0(1) NSAMG_UPD_COLS0(2) NSAMG_UPD_COLS0(3) NSAMG_UPD_COLS0(4)
+              NSAMG_UPD_COLS0(5) NSAMG_UPD_COLS0(6) NSAMG_UPD_COLS0(7)
+#undef NSAMG_UPD_COLS0
+              default: break;
+            }
+          } else {
+            const unsigned cf = cf0 + 32u * (unsigned)(cb - 1);
+            switch (ce - cb) {
 #define NSAMG_UPD_COLS(NW) \
   case NW:                 \
-    upd_cols_s<NW>(col, hs, ps, pc); \
+    upd_cols_s<NW, 0>(addr, cf, ps, pc); \
     break;
-            NSAMG_UPD_COLS(1) NSAMG_UPD_COLS(2) NSAMG_UPD_COLS(3) NSAMG_UPD_COLS(4)
-            NSAMG_UPD_COLS(5) NSAMG_UPD_COLS(6) NSAMG_UPD_COLS(7) NSAMG_UPD_COLS(8)
-            NSAMG_UPD_COLS(9) NSAMG_UPD_COLS(10) NSAMG_UPD_COLS(11) NSAMG_UPD_COLS(12)
-            NSAMG_UPD_COLS(13) NSAMG_UPD_COLS(14) NSAMG_UPD_COLS(15) NSAMG_UPD_COLS(16)
+              NSAMG_UPD_COLS(1) NSAMG_UPD_COLS(2) NSAMG_UPD_COLS(3) NSAMG_UPD_COLS(4)
+              NSAMG_UPD_COLS(5) NSAMG_UPD_COLS(6) NSAMG_UPD_COLS(7) NSAMG_UPD_COLS(8)
 #undef NSAMG_UPD_COLS
-            default: break;
-          }
-        } else if (t < tn) {  // the odd last row of a chunk: global memory
-          int c = cb;
-          if (c == 0) {
-            wb = a.w[row] * invb;
-            ok = ok && df_window(abs_hiword(wb));
-            split_df(wb, ps[0], pc[0]);
-            c = 1;
-          }
-          for (; c < ce; ++c) {  // one thread in the grid: plain loop, pair chosen by branches
-            const float2 x = Vs[(int64_t)(c - 1) * a.ldv + row];
-            const float2 hh = s_cs[c - 1];
-            switch (c & 3) {
-              case 0: dot2_step(ps[0], pc[0], hh.x, hh.y, x.x, x.y); break;
-              case 1: dot2_step(ps[1], pc[1], hh.x, hh.y, x.x, x.y); break;
-              case 2: dot2_step(ps[2], pc[2], hh.x, hh.y, x.x, x.y); break;
-              default: dot2_step(ps[3], pc[3], hh.x, hh.y, x.x, x.y); break;
+              default: break;
             }
           }
         }
         ring_release(g, k);
       }
-      if (aborted) {
-        s_abort = 1;
-        break;
+      if (aborted) break;
+      if (staged) {
+        if (cok && df_window(abs_hiword(wb0)) && df_window(abs_hiword(wb1))) {
+          df_add2(ps[0], pc[0], ps[1], pc[1]);
+          df_add2(ps[2], pc[2], ps[3], pc[3]);
+          df_add2(ps[0], pc[0], ps[2], pc[2]);
+          // normalised pairs (TwoSum): stored, squared and rounded for the FP32 copy
+          const f2_t tt = f2_add(ps[0], pc[0]);
+          const f2_t z = f2_sub(tt, ps[0]);
+          const f2_t e = f2_add(f2_sub(ps[0], f2_sub(tt, z)), f2_sub(pc[0], z));
+          asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(vnext + row), "l"(tt), "l"(e) : "memory");
+          float t0f, t1f, e0f, e1f;
+          f2_unpack(tt, t0f, t1f);
+          f2_unpack(e, e0f, e1f);
+          const double acc0 = widen_normal(t0f) + widen_normal(e0f);
+          const double acc1 = widen_normal(t1f) + widen_normal(e1f);
+          if (a.v32) {
+            a.v32[row] = t0f;
+            a.v32[row + 1] = t1f;
+          }
+          if (vin16) {
+            *reinterpret_cast<double2*>(a.vin + row) = make_double2(acc0, acc1);
+          } else if (a.vin) {
+            a.vin[row] = acc0;
+            a.vin[row + 1] = acc1;
+          }
+          dot2_step2(qs2, qc2, tt, e, tt, e, f2_mul(tt, m1));
+        } else {
+          upd_row_fp64(a, s_c, i, row, wb0, vnext, q64);
+          upd_row_fp64(a, s_c, i, row + 1, wb1, vnext, q64);
+        }
+      } else if (2 * t == te && te < tn) {  // the odd last row (n odd): FP64; its group's second lane stays 0
+        upd_row_fp64(a, s_c, i, row, a.w[row] * invb, vnext, q64);
+        rp_set(vnext, row + 1, make_float2(0.f, 0.f));
       }
-      if (t < tn) upd_finish_s(a, s_c, i, row, ok, wb, ps, pc, vnext, qs, qc, q64);
     }
+    if (aborted) s_abort = 1;
+  }
+  float qs, qc;
+  {
+    float q0, q1, c0, c1;
+    f2_unpack(qs2, q0, q1);
+    f2_unpack(qc2, c0, c1);
+    df_add(q0, c0, q1, c1);
+    qs = q0;
+    qc = c0;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -81,3 +81,19 @@ def test_params_are_rejected_before_any_device_work(bad):
         nsamg.setup_hierarchy(H, nsamg.default_params(**bad))
     assert e.value.status == -1
     assert nsamg.load().nsamg_last_error()
+
+
+@pytest.mark.parametrize("vs,lds", [(0x1008, 1000), (0x1000, 999), (0x1000, 998)])
+def test_split_basis_layout_is_checked_before_any_device_work(vs, lds):
+    """The row-pair split layout needs 16-byte aligned columns (an even leading dimension) and
+    room for the last row pair: the three split-basis entry points reject anything else with
+    INVALID_ARG before touching memory (the pointers here are never dereferenced)."""
+    import ctypes
+    from paper_2112_14681_b300 import nsamg
+    lib = nsamg.load()
+    n, p, w = 999, ctypes.c_void_p(vs), ctypes.c_void_p(0x2000)
+    assert lib.nsamg_split_basis(n, 1, ctypes.c_void_p(0x3000), n, p, lds, None) == -1
+    assert lib.nsamg_gram_split(n, 0, p, lds, w, ctypes.c_void_p(0x4000), None) == -1
+    assert lib.nsamg_update_split(n, 0, p, lds, w, 1.0, ctypes.c_void_p(0x5000), None, ctypes.c_void_p(0x6000),
+                                  None) == -1
+    assert lib.nsamg_last_error()

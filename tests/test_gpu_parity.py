@@ -272,8 +272,11 @@ def _split_case(n, i, wscale=1.0, seed=0):
     g = host(vin)
     assert np.max(np.abs(g - nxt_o) / bound) <= TOL
     assert abs(host(ss)[0] - np.dot(nxt_o, nxt_o)) <= TOL * np.dot(bound, bound)
-    pairs = host(Vs).reshape(i + 2, ld, 2)[i + 1, :n].astype(np.float64)
-    assert np.max(np.abs(pairs.sum(axis=1) - g) / np.maximum(np.abs(g), 1e-300)) <= 2.0 ** -44
+    # row-pair layout: group q of a column = (hi_2q, hi_2q+1, lo_2q, lo_2q+1)
+    grp = host(Vs).reshape(i + 2, ld // 2, 2, 2)[i + 1].astype(np.float64)
+    hi, lo = grp[:, 0, :].reshape(-1), grp[:, 1, :].reshape(-1)
+    assert np.max(np.abs(hi[:n] + lo[:n] - g) / np.maximum(np.abs(g), 1e-300)) <= 2.0 ** -44
+    assert np.all(hi[n:] == 0) and np.all(lo[n:] == 0)  # rows past n (padding) stay zero
 
 
 @pytest.mark.parametrize("n,i", [(1, 0), (2, 1), (999, 0), (1001, 1), (4097, 3), (70001, 10), (100003, 17),
