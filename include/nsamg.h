@@ -92,9 +92,12 @@ typedef struct {
                             smoother pass with all its Neumann terms, residual, transfers and the
                             coarse solve) runs as one thread-block-cluster kernel that stages each
                             pass's source vector in shared memory; bitwise the same result as the
-                            separate launches. 0 (default): one launch per pass, which measured
-                            faster on B300 (16 SMs of a cluster are latency bound where 148 SMs
-                            finish a pass in one wave). Batches ignore it.                        */
+                            separate launches. 2: the passes below the first level with at most
+                            32768 rows whose passes are all CSR row passes run as one cooperative
+                            kernel over every SM (one block per SM), a bounded grid barrier
+                            between dependent passes (a wait that gives up ends the solve with
+                            NSAMG_ERR_TIMEOUT); bitwise the same result as the separate launches.
+                            0 (default): one launch per pass. Batches ignore it.                  */
   int32_t sell_shape;    /* with spmv_group = -1: the SELL launch shape 10 K + U, K chunks of 32
                             rows per warp and U entries of each chunk staged per round: 11, 21,
                             41, 14 or 22 (0 = 11). Every shape sums each row in the same order, so
@@ -278,6 +281,15 @@ int nsamg_sknorm(const double* d_L, int ld, int k, double* d_out, void* stream);
  * launch with events on `stream`; *fma_per_launch (host, may be NULL) receives the FMA count.
  * Used to measure the FP64 and FP32 FMA rates that bound the FP64 and double-FP32 kernels. */
 int nsamg_fma_probe(int fp64, int64_t iters, int blocks, void* d_sink, void* stream, double* fma_per_launch);
+
+/* Test of the bounded grid barrier that the grid-wide fused tail (fuse_tail = 2) places between
+ * its passes (the paper has none: each of its V-cycle passes is a kernel launch). One cooperative
+ * launch of one 256-thread block per SM runs `rounds` barriers, each expecting the grid's blocks
+ * plus `missing` arrivals; with missing > 0 no barrier can complete, and every block gives up
+ * after `spin_limit` polls of about 0.1 us. On return (synchronous) *passed = barriers completed,
+ * summed over blocks (rounds x SMs when missing = 0), *status = 0, or NSAMG_ERR_TIMEOUT if a
+ * wait gave up. INVALID_ARG for rounds < 1, missing < 0, spin_limit < 1 or null pointers. */
+int nsamg_grid_barrier_test(int rounds, int missing, unsigned spin_limit, int* passed, int* status);
 
 /* ---- batched solves of many independent systems ----------------------------------------
  * nsamg_batch_setup: `count` host hierarchies with the same number of levels (and either all or

@@ -583,10 +583,13 @@ struct nsamg_handle {
   struct BatchData* batch = nullptr;  // set for handles made by nsamg_batch_setup
   bool shared_mats = false;           // a solver context: matrices belong to another handle
   double anorm_inf = 0.0;             // ||A_0||_inf (for the backward error)
-  // fused V-cycle tail (levels >= tail_l0 run by one cluster kernel); tail_l0 = 0: off
+  // fused V-cycle tail (levels >= tail_l0 run by one cluster kernel, or by one cooperative grid
+  // kernel when tail_grid); tail_l0 = 0: off
   int tail_l0 = 0;
   int tail_np = 0;
-  int tail_ncl = 0;
+  int tail_ncl = 0;               // cluster tail: CTAs of the cluster
+  int tail_grid = 0;              // grid tail: blocks of the cooperative launch (one per SM)
+  unsigned long long* tail_ctr = nullptr;  // grid tail: barrier counter (zeroed before each launch)
   void* tail_passes = nullptr;  // TailPass<double> or TailPass<float> array (device)
   size_t ctx_bytes = 0;               // device bytes of the per-solve workspace (server accounting)
 };
@@ -876,6 +879,21 @@ void coarse_solve(nsamg_handle* h, Level<T>& L, VC<T> b, VRef<T> x, const Ctx& c
 template <typename T>
 void launch_tail(nsamg_handle* h, const Ctx& c) {
   ++g_launches;
+  if (h->tail_grid) {  // cooperative: every block resident, so the grid barrier can complete
+    cudaMemsetAsync(h->tail_ctr, 0, sizeof(unsigned long long), c.s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->tail_grid);
+    cfg.blockDim = dim3(kGridTailThreads);
+    cfg.stream = c.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_tail_grid<T>, (const TailPass<T>*)h->tail_passes, h->tail_np, c.skip, h->tail_ctr,
+                       &h->st->status, kGridSpinLimit);
+    return;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->tail_ncl);
   cfg.blockDim = dim3(kTailThreads);
@@ -1333,7 +1351,7 @@ int check_params(const nsamg_params& p) {
   if (p.sell_shape != 0 && p.sell_shape != 11 && p.sell_shape != 21 && p.sell_shape != 41 && p.sell_shape != 14 &&
       p.sell_shape != 22)
     return fail(NSAMG_ERR_INVALID_ARG, "sell_shape must be 0, 11, 21, 41, 14 or 22");
-  if (p.fuse_tail != 0 && p.fuse_tail != 1) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0 or 1");
+  if (p.fuse_tail < 0 || p.fuse_tail > 2) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0, 1 or 2");
   if (p.krylov_fp64 != 0 && p.krylov_fp64 != 1) return fail(NSAMG_ERR_INVALID_ARG, "krylov_fp64 must be 0 or 1");
   if (p.stop_nrbe != 0 && p.stop_nrbe != 1) return fail(NSAMG_ERR_INVALID_ARG, "stop_nrbe must be 0 or 1");
   return NSAMG_OK;
@@ -1566,6 +1584,44 @@ int alloc_workspace(nsamg_handle* h) {
   return NSAMG_OK;
 }
 
+// Grid tail (fuse_tail = 2): the passes below the first level with at most kGridTailRows rows
+// whose passes are all CSR row passes (a SELL pass cannot be recorded; then the next level is
+// tried), one block per SM in a cooperative launch. Leaves the tail off when nothing would be
+// fused or the device cannot host the grid.
+template <typename T>
+int build_tail_grid(nsamg_handle* h, std::vector<Level<T>>& lv) {
+  const int nl = (int)lv.size();
+  std::vector<TailPass<T>> rec;
+  int l0 = 0;
+  for (int l = 1; l < nl - 1; ++l) {  // at least one smoothed level below the cut
+    if (lv[l].n > kGridTailRows) continue;
+    rec.clear();
+    tail_recorder<T>() = &rec;
+    vcycle(h, lv, l, cref((const T*)lv[l].b), vref(lv[l].x), Ctx{h->stream, nullptr});
+    tail_recorder<T>() = nullptr;
+    bool ok = true;
+    for (const auto& P : rec)
+      if (P.epi == -100) ok = false;
+    if (ok) {
+      l0 = l;
+      break;
+    }
+  }
+  if (l0 == 0) return NSAMG_OK;
+  int occ = 0, sms = 0, coop = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tail_grid<T>, kGridTailThreads, 0));
+  if (!coop || occ < 1) return NSAMG_OK;
+  if (!h->tail_ctr) CK(cudaMalloc(&h->tail_ctr, sizeof(unsigned long long)));
+  CK(cudaMalloc(&h->tail_passes, sizeof(TailPass<T>) * rec.size()));
+  CK(cudaMemcpy(h->tail_passes, rec.data(), sizeof(TailPass<T>) * rec.size(), cudaMemcpyHostToDevice));
+  h->tail_l0 = l0;
+  h->tail_np = (int)rec.size();
+  h->tail_grid = sms;
+  return NSAMG_OK;
+}
+
 // Record the passes of the V-cycle below the first level with at most kTailStage rows and keep
 // them on the device for k_tail; picks the largest cluster (16, else 8 CTAs) the device can host.
 // Leaves the tail off (separate launches) when nothing would be fused.
@@ -1575,8 +1631,9 @@ int build_tail(nsamg_handle* h, std::vector<Level<T>>& lv) {
     cudaFree(h->tail_passes);
     h->tail_passes = nullptr;
   }
-  h->tail_l0 = h->tail_np = h->tail_ncl = 0;
+  h->tail_l0 = h->tail_np = h->tail_ncl = h->tail_grid = 0;
   if (!h->p.fuse_tail || h->batch) return NSAMG_OK;
+  if (h->p.fuse_tail == 2) return build_tail_grid(h, lv);
   const int nl = (int)lv.size();
   int l0 = 0;
   for (int l = 1; l < nl; ++l)
@@ -2030,6 +2087,7 @@ void destroy_impl(nsamg_handle* h) {
   h->batch = nullptr;
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->tail_passes) cudaFree(h->tail_passes);
+  if (h->tail_ctr) cudaFree(h->tail_ctr);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->shared_mats) {
     release_level_vectors(h->lv);
@@ -2740,6 +2798,43 @@ int nsamg_fma_probe(int fp64, int64_t iters, int blocks, void* d_sink, void* str
     k_fma_probe<float><<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, 0.999999f, 1e-7f, (float*)d_sink);
   CK(cudaGetLastError());
   if (fma_per_launch) *fma_per_launch = (double)blocks * kProbeThreads * kProbeChains * (double)iters;
+  return NSAMG_OK;
+}
+
+int nsamg_grid_barrier_test(int rounds, int missing, unsigned spin_limit, int* passed, int* status) {
+  if (rounds < 1 || missing < 0 || spin_limit < 1 || !passed || !status)
+    return fail(NSAMG_ERR_INVALID_ARG, "nsamg_grid_barrier_test: bad arguments");
+  int dev = 0, sms = 0, coop = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(NSAMG_ERR_CUDA, "nsamg_grid_barrier_test: no cooperative launch on this device");
+  unsigned long long* ctr = nullptr;
+  int* d = nullptr;
+  CK(cudaMalloc(&ctr, sizeof(unsigned long long)));
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(ctr);
+    return fail(NSAMG_ERR_CUDA, "nsamg_grid_barrier_test: allocation failed");
+  }
+  cudaMemset(ctr, 0, sizeof(unsigned long long));
+  cudaMemset(d, 0, 2 * sizeof(int));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sms);
+  cfg.blockDim = dim3(256);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_grid_barrier_test, ctr, rounds, missing, spin_limit, d, d + 1);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int hv[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(hv, d, sizeof(hv), cudaMemcpyDeviceToHost);
+  cudaFree(ctr);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(NSAMG_ERR_CUDA, cudaGetErrorString(e));
+  *passed = hv[0];
+  *status = hv[1];
   return NSAMG_OK;
 }
 

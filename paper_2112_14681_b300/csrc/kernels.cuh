@@ -488,6 +488,134 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailPass<T>* __rest
 }
 
 // ------------------------------------------------------------------------------------------
+// Grid-wide fused V-cycle tail: the same recorded passes as k_tail (every pass below a level of
+// at most kGridTailRows rows), run by one cooperative launch over the whole GPU, one block per
+// SM, with a grid barrier between dependent passes instead of a kernel boundary. Rows of a pass
+// are dealt to all threads of the grid, G lanes per row, with k_row's accumulation order,
+// shuffle reduction and epilogue, so the result equals the separate launches bit for bit. The
+// source vector of a pass is read through L2 (it was written by other SMs in an earlier pass).
+// Every barrier wait is bounded: after `spin_limit` polls the block records NSAMG_ERR_TIMEOUT in
+// *status and the kernel returns, leaving the context usable.
+// ------------------------------------------------------------------------------------------
+constexpr int kGridTailThreads = 512;
+constexpr int kGridTailRows = 32768;
+constexpr unsigned kGridSpinLimit = 1u << 20;  // polls of ~0.1 us: about 0.1 s before giving up
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over `nb` co-resident blocks on a monotonic 64-bit counter (zeroed before the launch):
+// arrival k of the counter belongs to barrier k / nb. True once every block has arrived; false
+// if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned nb, unsigned spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // the block's writes of this pass before its arrival
+    const unsigned long long old = atomicAdd(ctr, 1ull);
+    const unsigned long long target = (old / nb + 1) * nb;
+    int ok = 1;
+    for (unsigned k = 0; ld_acquire_u64(ctr) < target; ++k) {
+      if (k >= spin_limit) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int EPI, typename T>
+__device__ __forceinline__ void tail_grid_row_pass(const RowOp<T, T, T>& op, int G) {
+  const T* __restrict__ src = op.src.p;
+  const int64_t t_end = (int64_t)op.n * G, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < t_end; t += stride) {
+    const int row = (int)(t / G);
+    T acc = T(0);
+    if (op.v) {
+      const int lane = (int)(t & (G - 1));
+      const int b = __ldg(op.rp + row), e = __ldg(op.rp + row + 1);
+#pragma unroll 4
+      for (int p = b + lane; p < e; p += G) {
+        const int c = __ldg(op.ci + p);
+        acc = fma((T)__ldg(op.v + p), __ldcg(src + c), acc);
+      }
+      if (G > 1) {
+        const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(seg, acc, o, G);
+      }
+      if (lane != 0) continue;
+    }
+    row_epilogue<EPI>(op, row, acc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGridTailThreads) k_tail_grid(const TailPass<T>* __restrict__ passes, int np,
+                                                               const int* skip, unsigned long long* ctr, int* status,
+                                                               unsigned spin_limit) {
+  pdl_enter();
+  if (skip && *skip) return;  // the same value in every block: the whole grid leaves
+  for (int q = 0; q < np; ++q) {
+    const TailPass<T>& P = passes[q];
+    const RowOp<T, T, T>& op = P.op;
+    if (P.dense) {
+      const T* __restrict__ src = op.src.p;
+      const int n = op.n, lane = threadIdx.x & 31;
+      const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+      for (int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); row < n; row += warps) {
+        T acc = T(0);
+        for (int j = lane; j < n; j += 32) acc = fma(P.C[(int64_t)row * n + j], __ldcg(src + j), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) op.out.p[row] = acc;
+      }
+    } else {
+      const int G = op.v ? P.G : 1;
+      switch (P.epi) {
+        case 0: tail_grid_row_pass<0>(op, G); break;
+        case 2: tail_grid_row_pass<2>(op, G); break;
+        case 3: tail_grid_row_pass<3>(op, G); break;
+        case 6: tail_grid_row_pass<6>(op, G); break;
+        case 7: tail_grid_row_pass<7>(op, G); break;
+        case 11: tail_grid_row_pass<11>(op, G); break;
+        case 16: tail_grid_row_pass<16>(op, G); break;
+        case 18: tail_grid_row_pass<18>(op, G); break;
+        case 19: tail_grid_row_pass<19>(op, G); break;
+        case 27: tail_grid_row_pass<27>(op, G); break;
+        default: tail_grid_row_pass<E_RUNTIME>(op, G); break;
+      }
+    }
+    if (q + 1 < np && !grid_barrier(ctr, gridDim.x, spin_limit)) {
+      if (threadIdx.x == 0 && status) atomicExch(status, -5);  // NSAMG_ERR_TIMEOUT
+      return;
+    }
+  }
+}
+
+// The grid barrier alone, for its tests: `rounds` barriers, each expecting gridDim.x + missing
+// arrivals (missing > 0: arrivals that never come, so that every wait runs out); each block adds
+// 1 to *passed per barrier it completed, and a block that gave up records NSAMG_ERR_TIMEOUT in
+// *status.
+__global__ void __launch_bounds__(256) k_grid_barrier_test(unsigned long long* ctr, int rounds, int missing,
+                                                            unsigned spin_limit, int* passed, int* status) {
+  for (int r = 0; r < rounds; ++r) {
+    if (!grid_barrier(ctr, gridDim.x + (unsigned)missing, spin_limit)) {
+      if (threadIdx.x == 0) atomicExch(status, -5);
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // GMRES device state (one per handle, in device memory).
 // ------------------------------------------------------------------------------------------
 struct GState {

@@ -69,7 +69,7 @@ EXPORTS = [
     "nsamg_level_smooth", "nsamg_level_restrict", "nsamg_level_prolong", "nsamg_coarse_solve", "nsamg_gram",
     "nsamg_update", "nsamg_gram_fp64", "nsamg_update_fp64", "nsamg_split_basis", "nsamg_gram_split",
     "nsamg_update_split", "nsamg_destroy", "nsamg_context_create", "nsamg_status_str", "nsamg_last_error",
-    "nsamg_launches_per_step", "nsamg_fma_probe",
+    "nsamg_launches_per_step", "nsamg_fma_probe", "nsamg_grid_barrier_test",
     "nsamg_gram_noalloc", "nsamg_batch_setup", "nsamg_batch_solve", "nsamg_batch_count", "nsamg_batch_offsets",
     "nsamg_server_create", "nsamg_server_submit", "nsamg_server_poll", "nsamg_server_wait", "nsamg_server_cancel",
     "nsamg_server_info", "nsamg_server_destroy", "nsamg_ilu0_fixed_point",
@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
         "nsamg_context_create": (i32, [vp, ctypes.POINTER(vp)]),
         "nsamg_launches_per_step": (i32, [vp]),
         "nsamg_fma_probe": (i32, [i32, i64, i32, vp, vp, ctypes.POINTER(f64)]),
+        "nsamg_grid_barrier_test": (i32, [i32, i32, ctypes.c_uint, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "nsamg_status_str": (ctypes.c_char_p, [i32]),
         "nsamg_last_error": (ctypes.c_char_p, []),
     }
@@ -417,6 +418,16 @@ def update_fp64(n: int, i: int, V, ldv: int, w, beta: float, h, sumsq, stream=No
                                     stream))
 
 
+def grid_barrier_test(rounds: int, missing: int = 0, spin_limit: int = 1 << 20) -> tuple:
+    """(barriers completed summed over blocks, status) of nsamg_grid_barrier_test: one block per
+    SM runs `rounds` bounded grid barriers, each expecting `missing` arrivals more than the grid
+    has (missing > 0: every wait gives up after `spin_limit` polls, status NSAMG_ERR_TIMEOUT)."""
+    passed, status = ctypes.c_int(), ctypes.c_int()
+    _check(load().nsamg_grid_barrier_test(int(rounds), int(missing), int(spin_limit), ctypes.byref(passed),
+                                          ctypes.byref(status)))
+    return passed.value, status.value
+
+
 def fma_rate(fp64: bool, iters: int = 1 << 16, blocks_per_sm: int = 8, reps: int = 5) -> float:
     """FMA/s of the current device in FP64 or FP32 (nsamg_fma_probe, best of `reps` launches
     timed with CUDA events after one warm-up launch)."""
@@ -589,6 +600,7 @@ def status_str(s: int) -> str:
     return load().nsamg_status_str(int(s)).decode()
 
 
+ERR_TIMEOUT = -5
 ERR_ADMISSION = -7
 
 

@@ -669,15 +669,15 @@ def test_fused_tail_equals_separate_launches(name, smoother, fp32):
     A, H = case(name)
     r = np.random.default_rng(7).uniform(-1, 1, A.shape[0])
     outs, launches = [], []
-    for fuse in (0, 1):
+    for fuse in (0, 1, 2):
         p = nsamg.default_params(**params_for(smoother, vcycle_fp32=fp32, fuse_tail=fuse, spmv_group=-1))
         with nsamg.setup_hierarchy(H, p) as h:
             z = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
             nsamg.apply_vcycle(h, dev(r), z)
             outs.append(host(z))
             launches.append(nsamg.launches_per_step(h))
-    assert np.array_equal(outs[0], outs[1])
-    assert launches[1] < launches[0]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert launches[1] < launches[0] and launches[2] < launches[0]
 
 
 @pytest.mark.parametrize("fp32", [0, 1])
@@ -685,13 +685,36 @@ def test_fused_tail_solve_is_bitwise_unchanged(fp32):
     A, H = case("p23")
     b = rhs_uniform(A.shape[0], 4)
     res = []
-    for fuse in (0, 1):
+    for fuse in (0, 1, 2):
         p = nsamg.default_params(smoother=nsamg.HYBRID_ILU0, vcycle_fp32=fp32, fuse_tail=fuse, spmv_group=-1)
         with nsamg.setup_hierarchy(H, p) as h:
             x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
             st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=300)
+            assert st["status"] == 0
             res.append((st["iters"], host(x)))
-    assert res[0][0] == res[1][0] and np.array_equal(res[0][1], res[1][1])
+    for k in (1, 2):
+        assert res[0][0] == res[k][0] and np.array_equal(res[0][1], res[k][1])
+
+
+def test_grid_barrier_completes_every_round():
+    """The grid tail's barrier: one block per SM, 7 rounds, every block passes every round."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    passed, status = nsamg.grid_barrier_test(7)
+    assert (passed, status) == (7 * sms, 0)
+
+
+def test_grid_barrier_wait_runs_out_and_the_context_survives():
+    """A barrier that waits for an arrival nothing makes: every block gives up after its poll limit
+    (a few ms here), the kernel returns NSAMG_ERR_TIMEOUT instead of hanging, and the context then
+    runs a solve as usual."""
+    passed, status = nsamg.grid_barrier_test(3, missing=1, spin_limit=20000)
+    assert passed == 0 and status == nsamg.ERR_TIMEOUT
+    A, H = case("p23")
+    b = rhs_uniform(A.shape[0], 4)
+    with nsamg.setup_hierarchy(H, nsamg.default_params(fuse_tail=2)) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=300)
+    assert st["status"] == 0 and st["converged"] == 1
 
 
 def test_fp32_vcycle_on_unaligned_caller_arrays():
