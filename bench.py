@@ -965,6 +965,29 @@ def run_profile_kernel(args):
     h.close()
 
 
+def run_profile_batch(args):
+    """One batched solve of the 256-system C4 batch (FP32 or FP64 V-cycle, no graph) inside an
+    NVTX range 'timed_solve' after one warm-up solve, for an ncu launch list (per-level shares)."""
+    batch_sys, _ = build_pools(BATCH_COUNT, 0)
+    import torch
+    from paper_2112_14681_b300 import nsamg
+    nsamg.load()
+    fp32 = int(args.smoother.endswith("fp32v"))
+    p = nsamg.default_params(restart=BATCH_RESTART, vcycle_fp32=fp32, use_graph=0)
+    b = torch.from_numpy(np.concatenate([bb for _, _, bb in batch_sys])).cuda()
+    with nsamg.batch_setup([H for _, H, _ in batch_sys], p) as h:
+        x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+        nsamg.batch_solve(h, b, x, RTOL, MAXIT)
+        x.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_solve")
+        st = nsamg.batch_solve(h, b, x, RTOL, MAXIT)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_batch": len(batch_sys), "fp32v": fp32, "iters_max": max(q["iters"] for q in st),
+                      "all_converged": all(q["converged"] == 1 for q in st)}))
+
+
 C3_EDGE = 192
 
 
@@ -1071,6 +1094,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="skip the 256-system batched comparison")
     ap.add_argument("--skip-serving", action="store_true", help="skip the Poisson-arrival serving comparison")
     ap.add_argument("--profile", action="store_true", help="one solve in an NVTX range, for ncu")
+    ap.add_argument("--profile-batch", action="store_true", help="one C4 batched solve in an NVTX range, for ncu")
     ap.add_argument("--profile-setup", action="store_true", help="one GPU AMG setup in an NVTX range, for ncu")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--smoother", default="hybrid_ilu0", choices=list(SMOOTHERS))
@@ -1089,6 +1113,8 @@ def main():
         run_profile_kernel(args)
     elif args.profile_setup:
         run_profile_setup(args)
+    elif args.profile_batch:
+        run_profile_batch(args)
     elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
