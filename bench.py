@@ -532,6 +532,7 @@ def run_gpu(args):
                   "launches timed with CUDA events"} if rank == 0 else {}
     kern = time_kernels(nsamg, torch, h, A, H, stream, fma["fp64_fma_per_s"]) if rank == 0 else {}
     setup_t = time_gpu_setup(nsamg, torch, A, H) if rank == 0 and extras else None
+    tail_ab = time_fused_tail(nsamg, torch, H, d_rhs[0]) if rank == 0 and extras else None
     for hh in handles.values():
         hh.close()
     batched = run_batched(nsamg, torch, batch_sys) if batch_sys else None
@@ -583,6 +584,8 @@ def run_gpu(args):
         }
         if setup_t:
             line["setup"] = setup_t
+        if tail_ab:
+            line["fused_tail"] = tail_ab
         if batched:
             line["batched"] = batched
         if served:
@@ -606,6 +609,40 @@ def _single_thread():
         import contextlib
         pinned = os.environ.get("OPENBLAS_NUM_THREADS") == "1"
         return contextlib.nullcontext(), 1 if pinned else (os.cpu_count() or 1)
+
+
+def time_fused_tail(nsamg, torch, H, b, reps=8):
+    """The main configuration with the V-cycle below 32768 rows as one cooperative grid kernel
+    (fuse_tail = 2, a bounded grid barrier between passes) against one launch per pass: median
+    solve time of `reps` solves each (graph launches, synchronised), whether the solutions are
+    bitwise equal, and the cost of one grid barrier (nsamg_grid_barrier_test with 1 and 2001
+    rounds, wall-clock difference / 2000)."""
+    out = {}
+    xs = {}
+    for fuse in (0, 2):
+        p = nsamg.default_params(restart=RESTART, fuse_tail=fuse, **SMOOTHERS["hybrid_ilu0"])
+        with nsamg.setup_hierarchy(H, p) as h:
+            x = torch.zeros(b.shape[0], dtype=torch.float64, device="cuda")
+            nsamg.solve(h, b, x, RTOL, MAXIT)
+            ts = []
+            for _ in range(reps):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                nsamg.solve(h, b, x, RTOL, MAXIT)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            xs[fuse] = x.cpu().numpy()
+            out[f"fuse_tail_{fuse}"] = {"ms_median": statistics.median(ts) * 1e3,
+                                        "launches_per_step": nsamg.launches_per_step(h)}
+    out["bitwise_equal"] = bool(np.array_equal(xs[0], xs[2]))
+    tb = []
+    for rounds in (1, 2001):
+        t0 = time.perf_counter()
+        passed, status = nsamg.grid_barrier_test(rounds)
+        tb.append(time.perf_counter() - t0)
+    out["grid_barrier_us"] = (tb[1] - tb[0]) / 2000 * 1e6
+    return out
 
 
 def run_batched(nsamg, torch, systems):

@@ -100,7 +100,7 @@ typedef struct {
                             0 (default): one launch per pass. Batches ignore it.                  */
   int32_t sell_shape;    /* with spmv_group = -1: the SELL launch shape 10 K + U, K chunks of 32
                             rows per warp and U entries of each chunk staged per round: 11, 21,
-                            41, 14 or 22 (0 = 11). Every shape sums each row in the same order, so
+                            41, 14, 18 or 22 (0 = 11). Every shape sums each row in the same order, so
                             the results do not depend on it. Ignored otherwise (the autotuner
                             picks the shape).                                                     */
   int32_t krylov_fp64;   /* 0 (default): the Gram and update kernels (Algorithm 1 steps 6 and 12)
@@ -119,6 +119,14 @@ typedef struct {
                             rtol (||b|| + ||A||_inf ||x_0||) with x_0 the cycle's start (the only
                             norm of x known before the x-update); the true residual at the cycle's
                             end then decides with the exact beta(x), restarting if it fails.      */
+  int32_t ranks;         /* 1 (default): smoothers couple all rows of a level. P > 1: the hybrid
+                            block-Jacobi smoothing of a P-rank run (Sec. 5.2): each level's rows
+                            are dealt to P contiguous blocks of ceil(n_l / P) rows, and the
+                            polynomial Gauss-Seidel triangular parts keep only the couplings
+                            inside a block (Jacobi across blocks); residuals use the whole level
+                            operator. ILU factors are taken from the hierarchy as given (build
+                            them from the block diagonal for a P-rank run). One GPU computes every
+                            block; 1 <= P <= 2^20. Not with nsamg_amg_setup_solver.                */
 } nsamg_params;
 
 typedef struct {

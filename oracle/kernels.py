@@ -25,6 +25,11 @@ class SmootherParams:
     (ILU on the finest level only, polynomial Gauss-Seidel below; Sec. 6.2).
     neumann_terms: k terms of the truncated series for (D+L)^-1 (k = 1 is Jacobi).
     ilu_terms_L / ilu_terms_U: terms of the series for (I+L_s)^-1 and (I+U_s)^-1.
+    ranks: the rows of every level are dealt to this many contiguous blocks (MPI ranks in the
+    paper's runs); the polynomial Gauss-Seidel triangular parts keep only the couplings inside a
+    block (hybrid block-Jacobi: Gauss-Seidel within a rank, Jacobi across ranks), while every
+    residual uses the whole level operator. ILU factors come with the hierarchy (those of the
+    block diagonal when it was built for ranks > 1).
     pre_sweeps / post_sweeps: sweeps per level (forward before, backward after the coarse
     correction for polynomial Gauss-Seidel).
     coarse_sweeps: sweeps on the coarsest level when it has no dense direct solve.
@@ -38,6 +43,7 @@ class SmootherParams:
     post_sweeps: int = 1
     coarse_sweeps: int = 4
     mode: str = "definition"
+    ranks: int = 1  # hybrid block-Jacobi across this many row blocks per level (Sec. 5.2, Sec. 6)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -68,6 +74,38 @@ def split_ldu(A: sp.csr_matrix):
     return cached
 
 
+def row_blocks(n: int, ranks: int) -> np.ndarray:
+    """Offsets of `ranks` contiguous row blocks of ceil(n / ranks) rows (the last may be short or
+    empty): block q holds rows off[q] .. off[q+1]-1."""
+    if ranks < 1:
+        raise ValueError("ranks must be >= 1")
+    size = -(-n // ranks)
+    return np.minimum(np.arange(ranks + 1, dtype=np.int64) * size, n)
+
+
+def local_block(A: sp.csr_matrix, ranks: int) -> sp.csr_matrix:
+    """The block-diagonal part of A over the row blocks of row_blocks(n, ranks) (the same split of
+    the columns): a_ij kept when rows i and j lie in the same block, the local matrix each rank
+    relaxes with in a hybrid smoother (Sec. 5.2). ranks = 1 returns A itself."""
+    if ranks == 1:
+        return A
+    cache = getattr(A, "_oracle_blocks", None)
+    if cache is None:
+        cache = {}
+        try:
+            A._oracle_blocks = cache
+        except AttributeError:
+            pass
+    if ranks not in cache:
+        C = sp.coo_matrix(A)
+        off = row_blocks(A.shape[0], ranks)
+        bi = np.searchsorted(off, C.row, side="right")
+        bj = np.searchsorted(off, C.col, side="right")
+        keep = bi == bj
+        cache[ranks] = sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=A.shape)
+    return cache[ranks]
+
+
 def l1_diagonal(A: sp.csr_matrix) -> np.ndarray:
     """d_ii = sum_j |a_ij|, the pointwise l1-Jacobi diagonal (Sec. 6.1 comparison smoother)."""
     cached = getattr(A, "_oracle_l1", None)
@@ -84,7 +122,7 @@ def l1_diagonal(A: sp.csr_matrix) -> np.ndarray:
 # Smoother sweeps. Each returns the updated x; b and x are not modified.
 # ---------------------------------------------------------------------------------------------
 
-def poly_gs_sweep(A, b, x, terms: int, backward: bool = False, mode: str = "definition"):
+def poly_gs_sweep(A, b, x, terms: int, backward: bool = False, mode: str = "definition", ranks: int = 1):
     """One polynomial Gauss-Seidel sweep (Sec. 5.2, eqs. polynomial / jr-initial-guess / jr).
 
     x <- x + M^-1 r with r = b - A x and M = D + L (forward) or D + U (backward).
@@ -92,8 +130,10 @@ def poly_gs_sweep(A, b, x, terms: int, backward: bool = False, mode: str = "defi
         sum_{j=0}^{terms-1} (-D^-1 T)^j D^-1,  T = L (forward) or U (backward),
     evaluated as explicit terms t_0 = D^-1 r, t_{j+1} = -D^-1 (T t_j), g = sum_j t_j.
     direct: g = M^-1 r by forward (or backward) substitution, the classical GS sweep (eq. one-stage).
+    ranks > 1 (hybrid block-Jacobi, Sec. 5.2): L and U are those of local_block(A, ranks), the
+    couplings inside each rank's block; r still uses the whole A.
     """
-    L, d, U = split_ldu(A)
+    L, d, U = split_ldu(local_block(A, ranks))
     T = U if backward else L
     r = residual(A, b, x)
     if mode == "direct":

@@ -37,7 +37,7 @@ def smooth(H, l: int, b, x, p: K.SmootherParams, backward: bool):
                             p.mode)
     if kind == "jacobi":
         return K.l1_jacobi_sweep(lev.A, b, x)
-    return K.poly_gs_sweep(lev.A, b, x, p.neumann_terms, backward=backward, mode=p.mode)
+    return K.poly_gs_sweep(lev.A, b, x, p.neumann_terms, backward=backward, mode=p.mode, ranks=p.ranks)
 
 
 def vcycle(H, b: np.ndarray, p: K.SmootherParams, l: int = 0) -> np.ndarray:

@@ -364,8 +364,12 @@ int upload_vec(const std::vector<double>& h, T** d) {
 }
 
 // Triangular part of A (strict lower if lower, else strict upper), rows scaled by rs (if given)
-// and columns scaled by cs (if given).
-HostCSR tri_part(const nsamg_csr& A, bool lower, const std::vector<double>* rs, const std::vector<double>* cs) {
+// and columns scaled by cs (if given). ranks > 1: only the couplings whose row and column lie in
+// the same one of `ranks` contiguous row blocks of ceil(n / ranks) rows (a hybrid smoother's
+// local triangle, Sec. 5.2).
+HostCSR tri_part(const nsamg_csr& A, bool lower, const std::vector<double>* rs, const std::vector<double>* cs,
+                 int ranks = 1) {
+  const int64_t bsz = ranks > 1 ? ((int64_t)A.nrows + ranks - 1) / ranks : (int64_t)A.nrows + 1;
   HostCSR h;
   h.n = A.nrows;
   h.m = A.ncols;
@@ -373,7 +377,7 @@ HostCSR tri_part(const nsamg_csr& A, bool lower, const std::vector<double>* rs, 
   for (int i = 0; i < A.nrows; ++i) {
     for (int p = A.rowptr[i]; p < A.rowptr[i + 1]; ++p) {
       const int c = A.col[p];
-      if (lower ? c < i : c > i) {
+      if ((lower ? c < i : c > i) && c / bsz == i / bsz) {
         double v = A.val[p];
         if (rs) v *= (*rs)[i];
         if (cs) v *= (*cs)[c];
@@ -447,11 +451,14 @@ void launch_sell_k(const RowOp<TM, TX, TY>& op, cudaStream_t s) {
   launch_sell_one<E_RUNTIME, K, U>(op, s);
 }
 
-// SELL shapes (chunks per warp K, entries staged per chunk U): (1,1), (2,1), (4,1), (1,4), (2,2).
+// SELL shapes (chunks per warp K, entries staged per chunk U): (1,1), (2,1), (4,1), (1,4), (2,2),
+// (1,8). Eight entries a round suit matrices with few chunks and long rows (the coarse levels'
+// Galerkin operators), where each warp otherwise walks its rows in many dependent rounds.
 template <typename TM, typename TX, typename TY>
 void launch_sell(const RowOp<TM, TX, TY>& op, int K, int U, cudaStream_t s) {
   if (K >= 4) launch_sell_k<4, 1>(op, s);
   else if (K == 2) U > 1 ? launch_sell_k<2, 2>(op, s) : launch_sell_k<2, 1>(op, s);
+  else if (U >= 8) launch_sell_k<1, 8>(op, s);
   else U > 1 ? launch_sell_k<1, 4>(op, s) : launch_sell_k<1, 1>(op, s);
 }
 
@@ -1008,7 +1015,7 @@ int tune(DCSR<T>& M, T* x, T* y, cudaStream_t s, const TuneScratch& fl) {
     cands[nc++] = {G, 0, 1, 1e30f};
   }
   if (M.nchunks > 0)
-    for (const auto& ku : {std::pair<int, int>{1, 1}, {2, 1}, {4, 1}, {1, 4}, {2, 2}})
+    for (const auto& ku : {std::pair<int, int>{1, 1}, {2, 1}, {4, 1}, {1, 4}, {2, 2}, {1, 8}})
       cands[nc++] = {1, ku.first, ku.second, 1e30f};
   auto apply = [&M](const Cand& c) {
     M.use_sell = c.K > 0;
@@ -1349,11 +1356,12 @@ int check_params(const nsamg_params& p) {
   if (p.spmv_group < -1 || p.spmv_group > 32 || (p.spmv_group > 0 && (p.spmv_group & (p.spmv_group - 1))))
     return fail(NSAMG_ERR_INVALID_ARG, "spmv_group must be -1, 0 or a power of two <= 32");
   if (p.sell_shape != 0 && p.sell_shape != 11 && p.sell_shape != 21 && p.sell_shape != 41 && p.sell_shape != 14 &&
-      p.sell_shape != 22)
-    return fail(NSAMG_ERR_INVALID_ARG, "sell_shape must be 0, 11, 21, 41, 14 or 22");
+      p.sell_shape != 22 && p.sell_shape != 18)
+    return fail(NSAMG_ERR_INVALID_ARG, "sell_shape must be 0, 11, 21, 41, 14, 18 or 22");
   if (p.fuse_tail < 0 || p.fuse_tail > 2) return fail(NSAMG_ERR_INVALID_ARG, "fuse_tail must be 0, 1 or 2");
   if (p.krylov_fp64 != 0 && p.krylov_fp64 != 1) return fail(NSAMG_ERR_INVALID_ARG, "krylov_fp64 must be 0 or 1");
   if (p.stop_nrbe != 0 && p.stop_nrbe != 1) return fail(NSAMG_ERR_INVALID_ARG, "stop_nrbe must be 0 or 1");
+  if (p.ranks < 1 || p.ranks > (1 << 20)) return fail(NSAMG_ERR_INVALID_ARG, "ranks must be in 1..2^20");
   return NSAMG_OK;
 }
 
@@ -1415,10 +1423,11 @@ int build_levels(const nsamg_hierarchy_desc* H, const nsamg_params& p, std::vect
     // uploads run in parallel host threads
     std::vector<std::function<int()>> jobs;
     jobs.push_back([&] { return upload(D.A, L.A); });
-    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, &dinv), L.L2); });
-    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, &dinv), L.U2); });
-    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, nullptr), L.L1); });
-    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, nullptr), L.U1); });
+    const int rk = p.ranks;
+    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, &dinv, rk), L.L2); });
+    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, &dinv, rk), L.U2); });
+    jobs.push_back([&] { return upload(tri_part(D.A, true, &dinv, nullptr, rk), L.L1); });
+    jobs.push_back([&] { return upload(tri_part(D.A, false, &dinv, nullptr, rk), L.U1); });
     if (l < nl - 1) {
       jobs.push_back([&] { return upload(D.P, L.P); });
       jobs.push_back([&] { return upload(D.R, L.R); });
@@ -2370,6 +2379,7 @@ void nsamg_default_params(nsamg_params* p) {
   p->fuse_tail = 0;
   p->krylov_fp64 = 0;
   p->stop_nrbe = 0;
+  p->ranks = 1;
 }
 
 int nsamg_setup_hierarchy(const nsamg_hierarchy_desc* H, const nsamg_params* p, void* cuda_stream, nsamg_handle** out) {
@@ -2676,6 +2686,7 @@ int nsamg_batch_setup(const nsamg_hierarchy_desc* hs, int count, const nsamg_par
   if (!out) return fail(NSAMG_ERR_INVALID_ARG, "null output handle pointer");
   *out = nullptr;
   if (!hs || count < 1) return fail(NSAMG_ERR_INVALID_ARG, "empty batch");
+  if (p && p->ranks != 1) return fail(NSAMG_ERR_INVALID_ARG, "batch: ranks must be 1 (one block per system)");
   const int nl = hs[0].nlevels;
   int with_inv = 0;
   for (int sI = 0; sI < count; ++sI) {

@@ -1487,6 +1487,8 @@ int dev_setup_impl(nsamg_amg* g, const nsamg_params* pp, void* stream, nsamg_han
   if (pp) p = *pp;
   int rc = check_params(p);
   if (rc) return rc;
+  if (p.ranks != 1)
+    return fail(NSAMG_ERR_INVALID_ARG, "nsamg_amg_setup_solver: ranks > 1 needs a host hierarchy (block-diagonal ILU factors)");
   h->p = p;
   CK(cudaGetDevice(&h->device));
   if (stream) {

@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("smoother", "neumann_terms", "ilu_terms_L", "ilu_terms_U", "pre_sweeps",
                                                "post_sweeps", "coarse_sweeps", "restart", "vcycle_fp32", "t_exact",
                                                "use_graph", "spmv_group", "fuse_tail", "sell_shape", "krylov_fp64",
-                                               "stop_nrbe")]
+                                               "stop_nrbe", "ranks")]
 
 
 class AmgOptions(ctypes.Structure):

@@ -39,7 +39,7 @@ def params_for(smoother, **kw):
 def oracle_params(p: nsamg.Params):
     return K.SmootherParams(smoother=p.smoother, neumann_terms=p.neumann_terms, ilu_terms_L=p.ilu_terms_L,
                             ilu_terms_U=p.ilu_terms_U, pre_sweeps=p.pre_sweeps, post_sweeps=p.post_sweeps,
-                            coarse_sweeps=p.coarse_sweeps)
+                            coarse_sweeps=p.coarse_sweeps, ranks=p.ranks)
 
 
 CASES = {
@@ -764,3 +764,52 @@ def test_fp32_casts_round_to_nearest_even():
     with np.errstate(over="ignore"):
         want = vals.astype(np.float32).astype(np.float64)
     np.testing.assert_array_equal(got, want)
+
+
+_rank_cache = {}
+
+
+def ranked_case(ranks):
+    """p23 with the ILU factors of every level taken from the block diagonal over `ranks` row
+    blocks (the local matrices of a `ranks`-rank run)."""
+    if ranks not in _rank_cache:
+        A, kw = CASES["p23"]()
+        _rank_cache[ranks] = (A, build_hierarchy(A, ilu_levels=None, ranks=ranks, **kw))
+    return _rank_cache[ranks]
+
+
+@pytest.mark.parametrize("ranks", [2, 5, 64])
+@pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0, K.ILU0])
+def test_vcycle_with_emulated_ranks(ranks, smoother):
+    """Hybrid block-Jacobi smoothing of a multi-rank run (Sec. 5.2) computed on one GPU: the
+    V-cycle against the oracle's with the same row blocks, componentwise."""
+    A, H = ranked_case(ranks)
+    p = nsamg.default_params(**params_for(smoother), ranks=ranks)
+    with nsamg.setup_hierarchy(H, p) as h:
+        r = rhs_uniform(A.shape[0], 12)
+        z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h, dev(r), z)
+    want = ovcycle(H, r, oracle_params(p))
+    assert np.max(np.abs(host(z) - want)) <= 1e-11 * np.max(np.abs(want))
+    if smoother == K.ILU0:  # ILU on every smoothed level: the blocks live in the factors alone
+        return
+    # the blocks change the polynomial Gauss-Seidel levels: the same V-cycle without them differs
+    with nsamg.setup_hierarchy(H, nsamg.default_params(**params_for(smoother))) as h1:
+        z1 = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+        nsamg.apply_vcycle(h1, dev(r), z1)
+    assert np.max(np.abs(host(z1) - want)) > 1e-6 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("ranks", [1, 4, 16])
+def test_solve_with_emulated_ranks_matches_oracle(ranks):
+    """GMRES with the hybrid V-cycle of a `ranks`-rank run: iterations and solution as the FP64
+    oracle with the same blocks; more ranks never take fewer iterations here."""
+    A, H = ranked_case(ranks) if ranks > 1 else case("p23")
+    p = nsamg.default_params(smoother=K.HYBRID_ILU0, restart=30, ranks=ranks)
+    b = rhs_uniform(A.shape[0], 13)
+    ref = gmres_onereduce(A, b, lambda v: ovcycle(H, v, oracle_params(p)), m=30, rtol=1e-8)
+    with nsamg.setup_hierarchy(H, p) as h:
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+        st = nsamg.solve(h, dev(b), x, rtol=1e-8, maxit=500)
+    assert st["converged"] == 1 and abs(st["iters"] - ref.iters) <= 1
+    assert np.linalg.norm(host(x) - ref.x) <= 1e-6 * np.linalg.norm(ref.x)

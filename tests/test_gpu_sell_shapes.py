@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2112_14681_b300 import nsamg  # noqa: E402
 
-SHAPES = [11, 21, 41, 14, 22]
+SHAPES = [11, 21, 41, 14, 22, 18]
 
 
 def ragged(n=40000, seed=3):

@@ -214,9 +214,26 @@ def ilut(A: sp.csr_matrix, droptol: float = 1e-2, lfil: int = 5, ruiz: bool = Tr
     return L, U, dr, dc
 
 
+def block_diagonal(A: sp.csr_matrix, ranks: int) -> sp.csr_matrix:
+    """A with every coupling between different row blocks dropped; the blocks are `ranks`
+    contiguous ranges of ceil(n / ranks) rows (columns split the same way): the local matrices
+    of `ranks` MPI ranks that each own one range."""
+    A = _csr(A)
+    if ranks <= 1:
+        return A
+    n = A.shape[0]
+    size = -(-n // ranks)
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    keep = (rows // size) == (A.indices // size)
+    B = sp.csr_matrix((A.data[keep], A.indices[keep], np.concatenate([[0], np.cumsum(
+        np.bincount(rows[keep], minlength=n))])), shape=A.shape)
+    return _csr(B)
+
+
 def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: int = 512, seed: int = 0,
                     ilu_levels=(0,), min_coarse: int = 1, direct_max: int = 512, strength: str = "abs",
-                    ilu: str = "ilu0", droptol: float = 1e-2, lfil: int = 5, ruiz_stop: str = "tol") -> Hierarchy:
+                    ilu: str = "ilu0", droptol: float = 1e-2, lfil: int = 5, ruiz_stop: str = "tol",
+                    ranks: int = 1) -> Hierarchy:
     """Build the Ruge-Stuben hierarchy of A (strength theta, PMIS, BAMG-direct, Galerkin RAP).
 
     Coarsening stops when a level has at most `coarse_max` rows, when `max_levels` levels exist,
@@ -224,7 +241,10 @@ def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: in
     the levels listed in `ilu_levels` (None for every non-coarsest level); ilu="ilut" attaches
     ILUT(droptol, lfil) factors with Ruiz scalings of U instead (Algorithm 2; ruiz_stop="dep" for the
     dep(U)-based early termination of Sec. 5.3). The coarsest level
-    gets a dense inverse when it has at most `direct_max` rows. strength="abs" compares |a_ij|
+    gets a dense inverse when it has at most `direct_max` rows. ranks > 1: the ILU factors are
+    those of the block diagonal over `ranks` contiguous row blocks (block_diagonal), as each rank
+    of a hybrid smoother factors its local matrix (Sec. 5.2); the operators stay whole.
+    strength="abs" compares |a_ij|
     (Sec. 5.1 as printed); strength="neg" compares -a_ij (classical Ruge-Stuben, for matrices
     with positive off-diagonal entries such as Q1 stiffness on high-aspect elements).
     """
@@ -244,12 +264,13 @@ def build_hierarchy(A, theta: float = 0.25, max_levels: int = 25, coarse_max: in
     want = range(len(levels) - 1) if ilu_levels is None else ilu_levels
     for l in want:
         if 0 <= l < len(levels) - 1:
+            Al = block_diagonal(levels[l].A, ranks)
             if ilu == "ilut":
                 lev = levels[l]
-                lev.ilu_L, lev.ilu_U, lev.ilu_dr, lev.ilu_dc = ilut(lev.A, droptol, lfil, ruiz_stop=ruiz_stop)
+                lev.ilu_L, lev.ilu_U, lev.ilu_dr, lev.ilu_dc = ilut(Al, droptol, lfil, ruiz_stop=ruiz_stop)
                 lev.ilu_form = 1
             else:
-                levels[l].ilu_L, levels[l].ilu_U, levels[l].ilu_dinv = ilu0(levels[l].A)
+                levels[l].ilu_L, levels[l].ilu_U, levels[l].ilu_dinv = ilu0(Al)
     H = Hierarchy(levels=levels, theta=theta, seed=seed)
     if levels[-1].n <= direct_max:
         H.coarse_inv = np.ascontiguousarray(np.linalg.inv(levels[-1].A.toarray()))
