@@ -115,6 +115,41 @@ def ilut_variant(H, droptol: float = 1e-2, lfil: int = 5):
     return Hierarchy(levels=[l0] + H.levels[1:], coarse_inv=H.coarse_inv, theta=H.theta, seed=H.seed, info=H.info)
 
 
+def ranks_variant(H, ranks: int):
+    """The same hierarchy with the finest level's ILU(0) factors taken from its block diagonal
+    over `ranks` row blocks (the local matrices of a `ranks`-rank run; the hybrid ILU(0) V-cycle
+    factors only the finest level)."""
+    import copy
+    from workloads.hierarchy import Hierarchy, block_diagonal, ilu0
+    l0 = copy.copy(H.levels[0])
+    l0.ilu_L, l0.ilu_U, l0.ilu_dinv = ilu0(block_diagonal(l0.A, ranks))
+    return Hierarchy(levels=[l0] + H.levels[1:], coarse_inv=H.coarse_inv, theta=H.theta, seed=H.seed, info=H.info)
+
+
+def time_emulated_ranks(nsamg, torch, H, b, ranks_list=(1, 8, 64, 512), reps=4):
+    """The main configuration with the hybrid block-Jacobi smoothing of a P-rank run (Sec. 5.2)
+    computed on this one GPU: iterations to 1e-8 and solve time per P (the paper's strong-scaling
+    runs see iteration counts grow mildly with the rank count)."""
+    out = {}
+    for P in ranks_list:
+        HP = ranks_variant(H, P) if P > 1 else H
+        p = nsamg.default_params(restart=RESTART, ranks=P, **SMOOTHERS["hybrid_ilu0"])
+        with nsamg.setup_hierarchy(HP, p) as h:
+            x = torch.zeros(b.shape[0], dtype=torch.float64, device="cuda")
+            st = nsamg.solve(h, b, x, RTOL, MAXIT)
+            ts = []
+            for _ in range(reps):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = nsamg.solve(h, b, x, RTOL, MAXIT)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+        out[str(P)] = {"iters": st["iters"], "converged": st["converged"] == 1, "relres_true": st["relres_true"],
+                       "ms_median": statistics.median(ts) * 1e3}
+    return out
+
+
 # Batched workload (C4): 256 independent 7-point systems, cube edge ~ U{16..64}, 4 levels each.
 BATCH_COUNT = 256
 BATCH_EDGES = (16, 64)
@@ -533,6 +568,7 @@ def run_gpu(args):
     kern = time_kernels(nsamg, torch, h, A, H, stream, fma["fp64_fma_per_s"]) if rank == 0 else {}
     setup_t = time_gpu_setup(nsamg, torch, A, H) if rank == 0 and extras else None
     tail_ab = time_fused_tail(nsamg, torch, H, d_rhs[0]) if rank == 0 and extras else None
+    ranks_ab = time_emulated_ranks(nsamg, torch, H, d_rhs[0]) if rank == 0 and extras else None
     for hh in handles.values():
         hh.close()
     batched = run_batched(nsamg, torch, batch_sys) if batch_sys else None
@@ -586,6 +622,8 @@ def run_gpu(args):
             line["setup"] = setup_t
         if tail_ab:
             line["fused_tail"] = tail_ab
+        if ranks_ab:
+            line["emulated_ranks"] = ranks_ab
         if batched:
             line["batched"] = batched
         if served:
