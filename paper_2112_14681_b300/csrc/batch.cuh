@@ -68,16 +68,25 @@ __device__ __forceinline__ bool last_of_system(unsigned* tk, int nb) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Gram for every active system (Algorithm 1 steps 6-11 per system).
+// Gram for every active system (Algorithm 1 steps 6-11 per system), in double-FP32 like the
+// single-system kernels (the FP64 pipe would bound it at ~0.25 of HBM): per tile, vt and w are
+// split once into shared memory; warps form C column groups x 16/C row groups over columns
+// 0..i (column i is vt itself, taken from the staged split); each column entry is split on the
+// fly and multiplied by TwoProduct + TwoSum (Dot2) into (sum, error) pairs; a warp reduce-scatter
+// combines them, FP64 takes over for the block and system sums (fixed order). A block whose vt
+// or w leaves the double-FP32 window recomputes its rows in FP64.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
   pdl_enter();
-  __shared__ double s_vt[kGramTile];
-  __shared__ double s_w[kGramTile];
+  __shared__ float4 s_sp[kDfTile];  // per row of the tile: (vt_hi, vt_lo, w_hi, w_lo)
   __shared__ double red[2 * (kMaxM + 1)];
   __shared__ double s_part[kGramWarps][2 * (kMaxM + 1)];
+  __shared__ unsigned s_max;
   __shared__ int s_sys;
-  if (threadIdx.x == 0) s_sys = find_system(a.bstart, a.nsys, blockIdx.x);
+  if (threadIdx.x == 0) {
+    s_sys = find_system(a.bstart, a.nsys, blockIdx.x);
+    s_max = 0u;
+  }
   __syncthreads();
   const int sys = s_sys;
   GState* st = a.st + sys;
@@ -88,56 +97,93 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
   const int stride = 2 * (kMaxM + 1);
   if (active) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int C = ncol <= 1 ? 1 : ncol <= 2 ? 2 : ncol <= 4 ? 4 : ncol <= 8 ? 8 : 16;
+    const int C = df_groups(ncol);
     const int R = kGramWarps / C;
+    const int S = (ncol + C - 1) / C;
     const int cg = warp % C, rg = warp / C;
+    const int rows_w = kDfTile / R;
     const int64_t r0 = a.off[sys] + (int64_t)(blockIdx.x - a.bstart[sys]) * a.rpb;
     const int64_t r1 = min(a.off[sys + 1], r0 + a.rpb);
     const double* vt = a.V + (int64_t)i * a.ldv;
-    double acc_a[kGramSlots], acc_s[kGramSlots];
+    float sa[kDfSlots], ca[kDfSlots], sw[kDfSlots], cw[kDfSlots];
 #pragma unroll
-    for (int s = 0; s < kGramSlots; ++s) acc_a[s] = acc_s[s] = 0.0;
-    for (int64_t t0 = r0; t0 < r1; t0 += kGramTile) {
-      const int tn = (int)((r1 - t0) < (int64_t)kGramTile ? (r1 - t0) : (int64_t)kGramTile);
+    for (int q = 0; q < kDfSlots; ++q) sa[q] = ca[q] = sw[q] = cw[q] = 0.f;
+    unsigned mx = 0u;
+    for (int64_t t0 = r0; t0 < r1; t0 += kDfTile) {
+      const int tn = (int)((r1 - t0) < (int64_t)kDfTile ? (r1 - t0) : (int64_t)kDfTile);
       __syncthreads();
-      for (int r = threadIdx.x; r < tn; r += kGramThreads) {
-        s_vt[r] = __ldcs(vt + t0 + r);
-        s_w[r] = __ldcs(a.w + t0 + r);
+      for (int r = threadIdx.x; r < kDfTile; r += kGramThreads) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < tn) {
+          const double x = __ldcs(vt + t0 + r), y = __ldcs(a.w + t0 + r);
+          mx = max(mx, max(abs_hiword(x), abs_hiword(y)));
+          split_df(x, q.x, q.y);
+          split_df(y, q.z, q.w);
+        }
+        s_sp[r] = q;
       }
       __syncthreads();
+      for (int k = 0; k < rows_w; k += 32) {
+        const int r = rg * rows_w + k + lane;
+        if (r >= tn) break;
+        const float4 q = s_sp[r];
+        double xv[kDfSlots];
 #pragma unroll
-      for (int s = 0; s < kGramSlots; ++s) {
-        const int j = cg + s * C;
-        if (j > i) break;
-        if (j < i) {
-          const double* vj = a.V + (int64_t)j * a.ldv + t0;
-          for (int r = lane + 32 * rg; r < tn; r += 32 * R) {
-            const double x = __ldcs(vj + r);
-            acc_a[s] = fma(x, s_vt[r], acc_a[s]);
-            acc_s[s] = fma(x, s_w[r], acc_s[s]);
-          }
-        } else {
-          for (int r = lane + 32 * rg; r < tn; r += 32 * R) {
-            const double x = s_vt[r];
-            acc_a[s] = fma(x, x, acc_a[s]);
-            acc_s[s] = fma(x, s_w[r], acc_s[s]);
+        for (int sl = 0; sl < kDfSlots; ++sl) {
+          const int j = cg + sl * C;
+          xv[sl] = (sl < S && j < i) ? __ldcs(a.V + (int64_t)j * a.ldv + t0 + r) : 0.0;
+        }
+#pragma unroll
+        for (int sl = 0; sl < kDfSlots; ++sl) {
+          const int j = cg + sl * C;
+          if (sl < S && j <= i) {
+            float xh = q.x, xl = q.y;  // column i: vt, already split
+            if (j < i) split_df(xv[sl], xh, xl);
+            dot2_step(sa[sl], ca[sl], xh, xl, q.x, q.y);
+            dot2_step(sw[sl], cw[sl], xh, xl, q.z, q.w);
           }
         }
       }
     }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) atomicMax(&s_max, mx);
+    __syncthreads();
+    if (df_window(s_max)) {
+      float as[16], ac[16];
 #pragma unroll
-    for (int s = 0; s < kGramSlots; ++s) {
-      const int j = cg + s * C;
-      if (j > i) break;
-      double va = acc_a[s], vs = acc_s[s];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        va += __shfl_xor_sync(0xffffffffu, va, o);
-        vs += __shfl_xor_sync(0xffffffffu, vs, o);
+      for (int sl = 0; sl < kDfSlots; ++sl) {
+        as[2 * sl] = sa[sl];
+        ac[2 * sl] = ca[sl];
+        as[2 * sl + 1] = sw[sl];
+        ac[2 * sl + 1] = cw[sl];
       }
-      if (lane == 0) {
-        s_part[rg][j] = va;
-        s_part[rg][kMaxM + 1 + j] = vs;
+      df_warp_reduce16(as, ac);
+      const int qd = lane >> 1, sl = qd >> 1, j = cg + sl * C;
+      if ((lane & 1) == 0 && sl < S && j <= i)
+        s_part[rg][(qd & 1) ? (kMaxM + 1 + j) : j] = widen_normal(as[0]) + widen_normal(ac[0]);
+    } else {  // FP64 recomputation of this block's rows (vt or w outside the double-FP32 window)
+#pragma unroll 1
+      for (int sl = 0; sl < S; ++sl) {
+        const int j = cg + sl * C;
+        double fa = 0.0, fw = 0.0;
+        if (j <= i) {
+          const double* vj = a.V + (int64_t)j * a.ldv;
+          for (int64_t t0 = r0; t0 < r1; t0 += kDfTile)
+            for (int r = rg * rows_w + lane; r < (rg + 1) * rows_w && t0 + r < r1; r += 32) {
+              const double x = vj[t0 + r];
+              fa = fma(x, vt[t0 + r], fa);
+              fw = fma(x, a.w[t0 + r], fw);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          fa += __shfl_xor_sync(0xffffffffu, fa, o);
+          fw += __shfl_xor_sync(0xffffffffu, fw, o);
+        }
+        if (lane == 0 && j <= i) {
+          s_part[rg][j] = fa;
+          s_part[rg][kMaxM + 1 + j] = fw;
+        }
       }
     }
     __syncthreads();
@@ -222,11 +268,17 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Update + Givens per active system; the last block of the launch advances the batch step.
+// Update + Givens per active system; the last block of the launch advances the batch step. The
+// new vector vt_{i+1} = w / beta_i - sum_j h_j v_j is formed in double-FP32 (w / beta_i and
+// v_i = vt_i / beta_i by one FP64 multiply each, every entry split on the fly, the -h_j split
+// once per block; four (sum, error) pairs) and stored as FP64; rows whose w / beta_i, and every
+// row when the coefficients, leave the double-FP32 window are computed in FP64.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads) k_bupdate(BatchArgs a) {
   pdl_enter();
   __shared__ double s_h[kMaxM + 1];
+  __shared__ float2 s_hs[kMaxM + 1];  // -h_j split
+  __shared__ unsigned s_cmax;
   __shared__ double s_red[kRedThreads / 32];
   __shared__ int s_sys;
   if (threadIdx.x == 0) s_sys = find_system(a.bstart, a.nsys, blockIdx.x);
@@ -239,25 +291,77 @@ __global__ void __launch_bounds__(kRedThreads) k_bupdate(BatchArgs a) {
   const int lane = threadIdx.x & 31;
   if (active) {
     const double invb = st->invbeta[i];
-    for (int j = threadIdx.x; j <= i; j += blockDim.x) s_h[j] = st->h[j];
+    if (threadIdx.x == 0) s_cmax = 0u;
     __syncthreads();
+    for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+      s_h[j] = st->h[j];
+      s_hs[j] = split2(-st->h[j]);
+      atomicMax(&s_cmax, abs_hiword(st->h[j]));
+    }
+    __syncthreads();
+    const bool cok = df_window(s_cmax);
     double* vi = a.V + (int64_t)i * a.ldv;
     double* vn = a.V + (int64_t)(i + 1) * a.ldv;
-    const double hi = s_h[i];
     const int64_t r0 = a.off[sys] + (int64_t)(blockIdx.x - a.bstart[sys]) * a.rpb;
     const int64_t r1 = min(a.off[sys + 1], r0 + a.rpb);
     double ss = 0.0;
+    float qs = 0.f, qc = 0.f;
     for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
       const double v = __ldcs(vi + r) * invb;
       vi[r] = v;
-      double acc = fma(-hi, v, __ldcs(a.w + r) * invb);
-#pragma unroll 8
-      for (int j = 0; j < i; ++j) acc = fma(-s_h[j], __ldcs(a.V + (int64_t)j * a.ldv + r), acc);
+      const double wb = __ldcs(a.w + r) * invb;
+      double acc;
+      if (cok && df_window(abs_hiword(wb))) {
+        // w / beta_i - sum_j h_j v_j in four (sum, error) pairs, columns four at a time
+        float ps[4] = {0.f, 0.f, 0.f, 0.f}, pc[4] = {0.f, 0.f, 0.f, 0.f};
+        split_df(wb, ps[0], pc[0]);
+        for (int j0 = 0; j0 < i; j0 += 4) {
+          double x[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) x[k] = j0 + k < i ? __ldcs(a.V + (int64_t)(j0 + k) * a.ldv + r) : 0.0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float xh, xl;
+            split_df(x[k], xh, xl);
+            const float2 hh = j0 + k < i ? s_hs[j0 + k] : make_float2(0.f, 0.f);
+            dot2_step(ps[k], pc[k], hh.x, hh.y, xh, xl);
+          }
+        }
+        {  // column i: v_i = vt_i / beta_i
+          float xh, xl;
+          split_df(v, xh, xl);
+          dot2_step(ps[1], pc[1], s_hs[i].x, s_hs[i].y, xh, xl);
+        }
+        df_add(ps[0], pc[0], ps[1], pc[1]);
+        df_add(ps[2], pc[2], ps[3], pc[3]);
+        df_add(ps[0], pc[0], ps[2], pc[2]);
+        const float tt = __fadd_rn(ps[0], pc[0]);
+        const float z = __fsub_rn(tt, ps[0]);
+        const float e = __fadd_rn(__fsub_rn(ps[0], __fsub_rn(tt, z)), __fsub_rn(pc[0], z));
+        acc = widen_normal(tt) + widen_normal(e);
+        dot2_step(qs, qc, tt, e, tt, e);
+      } else {  // outside the double-FP32 window: FP64
+        acc = fma(-s_h[i], v, wb);
+        for (int j = 0; j < i; ++j) acc = fma(-s_h[j], __ldcs(a.V + (int64_t)j * a.ldv + r), acc);
+        ss = fma(acc, acc, ss);
+      }
       vn[r] = acc;
-      ss = fma(acc, acc, ss);
+    }
+    // block sum of the squares: double-FP32 part per warp, FP64 part
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float rs = __shfl_xor_sync(0xffffffffu, qs, o), rc = __shfl_xor_sync(0xffffffffu, qc, o);
+      if (lane & o) {
+        df_add(rs, rc, qs, qc);
+        qs = rs;
+        qc = rc;
+      } else {
+        df_add(qs, qc, rs, rc);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    ss += widen_normal(qs) + widen_normal(qc);  // every lane holds the warp's double-FP32 total
     if (lane == 0) s_red[threadIdx.x >> 5] = ss;
     __syncthreads();
     if (threadIdx.x == 0) {
