@@ -208,6 +208,9 @@ SMOOTHERS = {
     "poly_gs_fp32v": dict(smoother=0, neumann_terms=2, pre_sweeps=1, post_sweeps=1, vcycle_fp32=1),
     # ILUT(1e-2, 5) with Ruiz-scaled U and 3 + 3 Jacobi terms on the finest level (Alg. 2)
     "hybrid_ilut": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1, post_sweeps=1),
+    # the main configuration with every Gram / update product and sum in FP64 (krylov_fp64 = 1)
+    "hybrid_ilu0_krylov_fp64": dict(smoother=3, ilu_terms_L=3, ilu_terms_U=3, neumann_terms=2, pre_sweeps=1,
+                                    post_sweeps=1, krylov_fp64=1),
 }
 
 

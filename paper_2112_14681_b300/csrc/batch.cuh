@@ -76,7 +76,10 @@ __device__ __forceinline__ bool last_of_system(unsigned* tk, int nb) {
 // combines them, FP64 takes over for the block and system sums (fixed order). A block whose vt
 // or w leaves the double-FP32 window recomputes its rows in FP64.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
+// Columns per warp of k_bgram: few enough that two blocks fit an SM (64 registers a thread).
+constexpr int kBGramSlots = 4;
+
+__global__ void __launch_bounds__(kGramThreads, 2) k_bgram(BatchArgs a) {
   pdl_enter();
   __shared__ float4 s_sp[kDfTile];  // per row of the tile: (vt_hi, vt_lo, w_hi, w_lo)
   __shared__ double red[2 * (kMaxM + 1)];
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
   const int stride = 2 * (kMaxM + 1);
   if (active) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int C = df_groups(ncol);
+    const int C = df_groups(ncol, kBGramSlots);
     const int R = kGramWarps / C;
     const int S = (ncol + C - 1) / C;
     const int cg = warp % C, rg = warp / C;
@@ -105,9 +108,9 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
     const int64_t r0 = a.off[sys] + (int64_t)(blockIdx.x - a.bstart[sys]) * a.rpb;
     const int64_t r1 = min(a.off[sys + 1], r0 + a.rpb);
     const double* vt = a.V + (int64_t)i * a.ldv;
-    float sa[kDfSlots], ca[kDfSlots], sw[kDfSlots], cw[kDfSlots];
+    float sa[kBGramSlots], ca[kBGramSlots], sw[kBGramSlots], cw[kBGramSlots];
 #pragma unroll
-    for (int q = 0; q < kDfSlots; ++q) sa[q] = ca[q] = sw[q] = cw[q] = 0.f;
+    for (int q = 0; q < kBGramSlots; ++q) sa[q] = ca[q] = sw[q] = cw[q] = 0.f;
     unsigned mx = 0u;
     for (int64_t t0 = r0; t0 < r1; t0 += kDfTile) {
       const int tn = (int)((r1 - t0) < (int64_t)kDfTile ? (r1 - t0) : (int64_t)kDfTile);
@@ -127,14 +130,14 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
         const int r = rg * rows_w + k + lane;
         if (r >= tn) break;
         const float4 q = s_sp[r];
-        double xv[kDfSlots];
+        double xv[kBGramSlots];
 #pragma unroll
-        for (int sl = 0; sl < kDfSlots; ++sl) {
+        for (int sl = 0; sl < kBGramSlots; ++sl) {
           const int j = cg + sl * C;
           xv[sl] = (sl < S && j < i) ? __ldcs(a.V + (int64_t)j * a.ldv + t0 + r) : 0.0;
         }
 #pragma unroll
-        for (int sl = 0; sl < kDfSlots; ++sl) {
+        for (int sl = 0; sl < kBGramSlots; ++sl) {
           const int j = cg + sl * C;
           if (sl < S && j <= i) {
             float xh = q.x, xl = q.y;  // column i: vt, already split
@@ -152,10 +155,10 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram(BatchArgs a) {
       float as[16], ac[16];
 #pragma unroll
       for (int sl = 0; sl < kDfSlots; ++sl) {
-        as[2 * sl] = sa[sl];
-        ac[2 * sl] = ca[sl];
-        as[2 * sl + 1] = sw[sl];
-        ac[2 * sl + 1] = cw[sl];
+        as[2 * sl] = sl < kBGramSlots ? sa[sl < kBGramSlots ? sl : 0] : 0.f;
+        ac[2 * sl] = sl < kBGramSlots ? ca[sl < kBGramSlots ? sl : 0] : 0.f;
+        as[2 * sl + 1] = sl < kBGramSlots ? sw[sl < kBGramSlots ? sl : 0] : 0.f;
+        ac[2 * sl + 1] = sl < kBGramSlots ? cw[sl < kBGramSlots ? sl : 0] : 0.f;
       }
       df_warp_reduce16(as, ac);
       const int qd = lane >> 1, sl = qd >> 1, j = cg + sl * C;
