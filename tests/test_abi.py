@@ -68,7 +68,7 @@ def test_binding_structs_match_the_header(cname, pyname):
                                  dict(pre_sweeps=-1), dict(post_sweeps=-1), dict(coarse_sweeps=0), dict(restart=0),
                                  dict(restart=65), dict(vcycle_fp32=2), dict(t_exact=2), dict(use_graph=2),
                                  dict(spmv_group=3), dict(spmv_group=64), dict(spmv_group=-2), dict(sell_shape=12),
-                                 dict(fuse_tail=3), dict(fuse_tail=-1), dict(krylov_fp64=2), dict(krylov_fp64=-1),
+                                 dict(fuse_tail=3), dict(fuse_tail=-1), dict(ranks=0), dict(ranks=-2), dict(ranks=(1 << 20) + 1), dict(krylov_fp64=2), dict(krylov_fp64=-1),
                                  dict(stop_nrbe=2)])
 def test_params_are_rejected_before_any_device_work(bad):
     """nsamg_setup_hierarchy validates every parameter first: INVALID_ARG with a message, no device
