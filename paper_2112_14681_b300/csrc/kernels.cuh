@@ -182,19 +182,25 @@ __device__ __forceinline__ T ld_entry(const T* p, uint64_t pol) {
 
 // Entries b + lane, b + lane + G, ... of one CSR row, UR per round: the UR column and value loads
 // are issued before the gathers and the gathers before the FMAs, which keep the order of p (so
-// the lane's sum is the one of the plain loop).
+// the lane's sum is the one of the plain loop). csr_round_loads issues one round's loads; the
+// caller issues the first round before it waits for the previous kernel (the matrix does not
+// depend on it, only the gathers do).
+template <bool ST, int G, int UR, typename TM>
+__device__ __forceinline__ void csr_round_loads(const int* __restrict__ ci, const TM* __restrict__ v, int p0, int e,
+                                                int (&cj)[UR], TM (&vj)[UR], uint64_t pol) {
+#pragma unroll
+  for (int u = 0; u < UR; ++u) {
+    const int p = p0 + u * G;
+    cj[u] = p < e ? ld_entry<ST>(ci + p, pol) : 0;
+    vj[u] = p < e ? ld_entry<ST>(v + p, pol) : TM(0);
+  }
+}
+
 template <bool ST, int G, int UR, typename TM, typename TX, typename TY>
 __device__ __forceinline__ TY csr_accumulate(const int* __restrict__ ci, const TM* __restrict__ v, const TX* __restrict__ src,
-                                             int b, int e, int lane, TY acc, uint64_t pol) {
+                                             int b, int e, int lane, TY acc, uint64_t pol, int (&cj)[UR], TM (&vj)[UR]) {
   for (int p0 = b + lane; p0 < e; p0 += UR * G) {
-    int cj[UR];
-    TM vj[UR];
-#pragma unroll
-    for (int u = 0; u < UR; ++u) {
-      const int p = p0 + u * G;
-      cj[u] = p < e ? ld_entry<ST>(ci + p, pol) : 0;
-      vj[u] = p < e ? ld_entry<ST>(v + p, pol) : TM(0);
-    }
+    if (p0 != b + lane) csr_round_loads<ST, G, UR>(ci, v, p0, e, cj, vj, pol);  // round 0: loaded by the caller
     TX xj[UR];
 #pragma unroll
     for (int u = 0; u < UR; ++u) xj[u] = p0 + u * G < e ? __ldg(src + cj[u]) : TX(0);
@@ -207,24 +213,38 @@ __device__ __forceinline__ TY csr_accumulate(const int* __restrict__ ci, const T
 
 template <int G, int EPI, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
-  pdl_enter();
-  if (op.skip && *op.skip) return;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int row = (int)(gid / G);
-  if (row >= op.n) return;  // uniform over the G lanes of a row
+  if (row >= op.n) {  // uniform over the G lanes of a row
+    pdl_enter();
+    return;
+  }
+  constexpr int UR = 4;
+  const int lane = (int)(gid & (G - 1));
+  int b = 0, e = 0;
+  int cj[UR];
+  TM vj[UR];
+  bool stream = false;
+  if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+  if (op.v) {  // row bounds and the first round of entries: static data, before the wait
+    b = __ldg(op.rp + row);
+    e = __ldg(op.rp + row + 1);
+    if (stream) {
+      if constexpr (sizeof(TM) == sizeof(double)) csr_round_loads<true, G, UR>(op.ci, op.v, b + lane, e, cj, vj, l2_evict_first());
+    } else {
+      csr_round_loads<false, G, UR>(op.ci, op.v, b + lane, e, cj, vj, 0ull);
+    }
+  }
+  pdl_enter();  // the source vector, epilogue vectors and the skip flag may come from the previous kernel
+  if (op.skip && *op.skip) return;
   TY acc = TY(0);
   if (op.v) {
     const TX* __restrict__ src = op.src.get();
-    const int lane = (int)(gid & (G - 1));
-    const int b = __ldg(op.rp + row), e = __ldg(op.rp + row + 1);
-    bool stream = false;
-    if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
-    constexpr int UR = 4;
     if (stream) {
       if constexpr (sizeof(TM) == sizeof(double))
-        acc = csr_accumulate<true, G, UR>(op.ci, op.v, src, b, e, lane, acc, l2_evict_first());
+        acc = csr_accumulate<true, G, UR>(op.ci, op.v, src, b, e, lane, acc, l2_evict_first(), cj, vj);
     } else {
-      acc = csr_accumulate<false, G, UR>(op.ci, op.v, src, b, e, lane, acc, 0ull);
+      acc = csr_accumulate<false, G, UR>(op.ci, op.v, src, b, e, lane, acc, 0ull, cj, vj);
     }
     if constexpr (G > 1) {
       const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -242,22 +262,29 @@ __global__ void __launch_bounds__(256) k_row(RowOp<TM, TX, TY> op) {
 // rows prefer U = 1, which needs fewer registers and keeps more warps resident). Every lane runs
 // to its chunk's width (uniform over the warp); padded entries hold zero values and a column of
 // their own row, so they add exact zeros. Each row's FMAs keep the order j = 0, 1, 2, ...
+// The first round's column and value loads are issued by the caller (sell_round_loads) before
+// it waits for the previous kernel: the matrix does not depend on it, only the gathers do.
+template <bool ST, int K, int U, typename TM>
+__device__ __forceinline__ void sell_round_loads(const SellView<TM>& sv, const int64_t (&off)[K], const int (&len)[K],
+                                                 int j, int (&cj)[K][U], TM (&vj)[K][U], uint64_t pol) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool in = j + u < len[k];
+      const int64_t q = off[k] + 32 * (int64_t)(j + u);
+      cj[k][u] = in ? ld_entry<ST>(sv.col + q, pol) : 0;
+      vj[k][u] = in ? ld_entry<ST>(sv.val + q, pol) : TM(0);
+    }
+}
+
 template <bool ST, int K, int U, typename TM, typename TX, typename TY>
 __device__ __forceinline__ void sell_accumulate(const SellView<TM>& sv, const TX* __restrict__ src, const int64_t (&off)[K],
-                                                const int (&len)[K], int jmax, TY (&acc)[K], uint64_t pol) {
+                                                const int (&len)[K], int jmax, TY (&acc)[K], uint64_t pol,
+                                                int (&cj)[K][U], TM (&vj)[K][U]) {
 #pragma unroll(U == 1 ? 2 : 1)
   for (int j = 0; j < jmax; j += U) {
-    int cj[K][U];
-    TM vj[K][U];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool in = j + u < len[k];
-        const int64_t q = off[k] + 32 * (int64_t)(j + u);
-        cj[k][u] = in ? ld_entry<ST>(sv.col + q, pol) : 0;
-        vj[k][u] = in ? ld_entry<ST>(sv.val + q, pol) : TM(0);
-      }
+    if (j > 0) sell_round_loads<ST, K, U>(sv, off, len, j, cj, vj, pol);  // round 0: loaded by the caller
     TX xj[K][U];
 #pragma unroll
     for (int k = 0; k < K; ++k)
@@ -274,15 +301,16 @@ __device__ __forceinline__ void sell_accumulate(const SellView<TM>& sv, const TX
 // K chunks of 32 rows per warp, each lane one row of each chunk, U entries of each chunk staged
 // per round (sell_accumulate). PLAIN: natural row order (chunk c holds rows 32c..32c+31);
 // otherwise rows sorted by length within windows, with a permutation. Chunk widths come from
-// cptr, or from sell.width when every chunk has the same width.
+// cptr, or from sell.width when every chunk has the same width. The chunk geometry and the first
+// round of matrix entries are loaded before the wait for the previous kernel.
 template <int EPI, int K, int U, bool PLAIN, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
-  pdl_enter();
-  if (op.skip && *op.skip) return;
   const int lane = threadIdx.x & 31;
-  const TX* __restrict__ src = op.src.get();
   const int c0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * K;
-  if (c0 >= op.sell.nchunks) return;
+  if (c0 >= op.sell.nchunks) {
+    pdl_enter();
+    return;
+  }
   int row[K], len[K];
   int64_t off[K];
   TY acc[K];
@@ -310,11 +338,21 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
   }
   bool stream = false;
   if constexpr (sizeof(TM) == sizeof(double)) stream = op.mat_stream != 0;  // uniform over the launch
+  int cj[K][U];
+  TM vj[K][U];
+  if (stream) {
+    if constexpr (sizeof(TM) == sizeof(double)) sell_round_loads<true, K, U>(op.sell, off, len, 0, cj, vj, l2_evict_first());
+  } else {
+    sell_round_loads<false, K, U>(op.sell, off, len, 0, cj, vj, 0ull);
+  }
+  pdl_enter();  // the source vector (and the skip flag) may come from the previous kernel
+  if (op.skip && *op.skip) return;
+  const TX* __restrict__ src = op.src.get();
   if (stream) {
     if constexpr (sizeof(TM) == sizeof(double))
-      sell_accumulate<true, K, U>(op.sell, src, off, len, jmax, acc, l2_evict_first());
+      sell_accumulate<true, K, U>(op.sell, src, off, len, jmax, acc, l2_evict_first(), cj, vj);
   } else {
-    sell_accumulate<false, K, U>(op.sell, src, off, len, jmax, acc, 0ull);
+    sell_accumulate<false, K, U>(op.sell, src, off, len, jmax, acc, 0ull, cj, vj);
   }
 #pragma unroll
   for (int k = 0; k < K; ++k)
