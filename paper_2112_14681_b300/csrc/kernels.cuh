@@ -303,6 +303,8 @@ __device__ __forceinline__ void sell_accumulate(const SellView<TM>& sv, const TX
 // otherwise rows sorted by length within windows, with a permutation. Chunk widths come from
 // cptr, or from sell.width when every chunk has the same width. The chunk geometry and the first
 // round of matrix entries are loaded before the wait for the previous kernel.
+constexpr int kSellPrefetchRounds = 8;
+
 template <int EPI, int K, int U, bool PLAIN, typename TM, typename TX, typename TY>
 __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
   const int lane = threadIdx.x & 31;
@@ -344,6 +346,16 @@ __global__ void __launch_bounds__(256) k_sell(RowOp<TM, TX, TY> op) {
     if constexpr (sizeof(TM) == sizeof(double)) sell_round_loads<true, K, U>(op.sell, off, len, 0, cj, vj, l2_evict_first());
   } else {
     sell_round_loads<false, K, U>(op.sell, off, len, 0, cj, vj, 0ull);
+  }
+  // the later rounds of short chunks into L2 as well (one line request per lane and entry)
+  if (jmax <= kSellPrefetchRounds) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      for (int j = U; j < len[k]; ++j) {
+        const int64_t q = off[k] + 32 * (int64_t)j;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(op.sell.col + q));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(op.sell.val + q));
+      }
   }
   pdl_enter();  // the source vector (and the skip flag) may come from the previous kernel
   if (op.skip && *op.skip) return;
