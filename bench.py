@@ -676,7 +676,9 @@ def time_fused_tail(nsamg, torch, H, b, reps=8):
             xs[fuse] = x.cpu().numpy()
             out[f"fuse_tail_{fuse}"] = {"ms_median": statistics.median(ts) * 1e3,
                                         "launches_per_step": nsamg.launches_per_step(h)}
-    out["bitwise_equal"] = bool(np.array_equal(xs[0], xs[2]))
+    # each handle is autotuned on its own, so their row layouts (and the rounding of rows summed by
+    # several lanes) can differ; with fixed layouts the two are bitwise equal (the GPU tests)
+    out["x_rel_diff"] = float(np.linalg.norm(xs[0] - xs[2]) / np.linalg.norm(xs[0]))
     tb = []
     for rounds in (1, 2001):
         t0 = time.perf_counter()
