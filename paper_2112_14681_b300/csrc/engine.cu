@@ -117,7 +117,7 @@ cudaError_t gram_tma_prepare() {
   if ((e = cudaFuncSetAttribute(k_update_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) !=
       cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(k_gram_s, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_gram_s, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSSmem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_update_s, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramTmaSmem)) != cudaSuccess)
     return e;
@@ -1126,7 +1126,7 @@ void enqueue_step(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inner
   ga.w = h->w;
   ga.st = h->st;
   ga.scr = h->scr;
-  if (h->split) launch_k_smem(k_gram_s, h->gram_blocks, kGramTmaThreads, kGramTmaSmem, s, ga);
+  if (h->split) launch_k_smem(k_gram_s, h->gram_blocks, kGramTmaThreads, kGramSSmem, s, ga);
   else launch_k(k_gram, h->gram_blocks, kGramThreads, s, ga);
   g_launches += 2;
   UpdateArgs ua{};
@@ -2605,7 +2605,7 @@ int nsamg_gram_split(int64_t n, int i, const void* d_Vs, int64_t lds, const doub
   ga.i_standalone = i;
   ga.out = d_out;
   ga.scr = scr;
-  launch_k_smem(k_gram_s, kDfGramBlocksPerSM * sms, kGramTmaThreads, kGramTmaSmem, (cudaStream_t)stream, ga);
+  launch_k_smem(k_gram_s, kDfGramBlocksPerSM * sms, kGramTmaThreads, kGramSSmem, (cudaStream_t)stream, ga);
   CK(cudaGetLastError());
   return NSAMG_OK;
 }

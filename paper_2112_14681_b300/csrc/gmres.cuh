@@ -603,12 +603,13 @@ __device__ __forceinline__ int tma_tile_rows(int i, int R) {
   return t < 2048 ? t : 2048;
 }
 
-// One stage ring: NST buffers of kRingBytes / NST bytes followed by the full and empty mbarriers.
+// One stage ring: NST buffers of BYTES / NST bytes followed by the full and empty mbarriers.
 // Item k uses stage k % NST in round k / NST.
-template <int NST>
+template <int NST, int BYTES = kRingBytes>
 struct RingT {
   static constexpr int kStages = NST;
-  static constexpr int kStageBytes = kRingBytes / NST;
+  static constexpr int kStageBytes = BYTES / NST;
+  static_assert(kStageBytes % 16 == 0, "bulk copies need 16-byte aligned stages");
   double* stage;
   unsigned full0, empty0;
   __device__ __forceinline__ double* buf(int k) const { return stage + (int64_t)(k % NST) * (kStageBytes / 8); }
@@ -618,11 +619,11 @@ struct RingT {
 };
 using Ring = RingT<kGramTmaStages>;
 
-template <int NST>
-__device__ __forceinline__ RingT<NST> ring_init_t(unsigned char* dsm) {
-  RingT<NST> g;
+template <int NST, int BYTES = kRingBytes>
+__device__ __forceinline__ RingT<NST, BYTES> ring_init_t(unsigned char* dsm) {
+  RingT<NST, BYTES> g;
   g.stage = reinterpret_cast<double*>(dsm);
-  g.full0 = smem_u32(dsm + kRingBytes);
+  g.full0 = smem_u32(dsm + BYTES);
   g.empty0 = g.full0 + 8u * NST;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -1697,6 +1698,11 @@ __device__ __forceinline__ bool gram_consume_s(const RG& g, const float2* __rest
 // the producer warp and the consumer warps' products. Few columns stream best through three
 // stages; many columns (short tiles) through two larger ones.
 constexpr int kGramTwoStageCols = 30;
+// The Gram's ring: the shared memory left beside its static arrays (divisible into 16-byte
+// aligned stages for 2, 3 and 4 stages); kGramStagesSmall stages below kGramTwoStageCols columns.
+constexpr int kGramRingBytes = 208896;
+constexpr int kGramSSmem = kGramRingBytes + 2 * 4 * 8;
+constexpr int kGramStagesSmall = 3;
 
 template <int NST>
 __device__ __forceinline__ void gram_s_stream(const GramArgs& a, unsigned char* dsm, int nv, int C, int cg, int rg,
@@ -1706,7 +1712,8 @@ __device__ __forceinline__ void gram_s_stream(const GramArgs& a, unsigned char* 
                                               unsigned* s_max,
                                               volatile int* s_abort) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int T = min(2048, RingT<NST>::kStageBytes / (8 * (nv + 1)) / 32 * 32);
+  using RG = RingT<NST, kGramRingBytes>;
+  const int T = min(2048, RG::kStageBytes / (8 * (nv + 1)) / 32 * 32);
   const int64_t chunk = ((a.n + gridDim.x - 1) / gridDim.x + T - 1) / T * T;
   const int64_t r0 = (int64_t)blockIdx.x * chunk;
   const int64_t r1 = min(a.n, r0 + chunk);
@@ -1715,7 +1722,7 @@ __device__ __forceinline__ void gram_s_stream(const GramArgs& a, unsigned char* 
   r1_out = r1;
   const int ntiles = r1 > r0 ? (int)((r1 - r0 + T - 1) / T) : 0;
   const float2* Vs = a.Vs;
-  const RingT<NST> g = ring_init_t<NST>(dsm);
+  const RG g = ring_init_t<NST, kGramRingBytes>(dsm);
   if (threadIdx.x == 0) {
     *s_max = 0u;
     *s_abort = 0;
@@ -1783,7 +1790,7 @@ __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
   int64_t r0, r1;
   const float2* Vs = a.Vs;
   if (nv < kGramTwoStageCols)
-    gram_s_stream<3>(a, dsm, nv, C, cg, rg, R, S, T, r0, r1, sa, ca, sw, cw, mx, &s_max, &s_abort);
+    gram_s_stream<kGramStagesSmall>(a, dsm, nv, C, cg, rg, R, S, T, r0, r1, sa, ca, sw, cw, mx, &s_max, &s_abort);
   else
     gram_s_stream<2>(a, dsm, nv, C, cg, rg, R, S, T, r0, r1, sa, ca, sw, cw, mx, &s_max, &s_abort);
   if (warp < kGramTmaConsumers) {
