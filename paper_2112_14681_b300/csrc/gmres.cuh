@@ -1698,10 +1698,11 @@ __device__ __forceinline__ bool gram_consume_s(const RG& g, const float2* __rest
 // the producer warp and the consumer warps' products. Few columns stream best through three
 // stages; many columns (short tiles) through two larger ones.
 constexpr int kGramTwoStageCols = 30;
-// The Gram's ring: the shared memory left beside its static arrays (divisible into 16-byte
-// aligned stages for 2, 3 and 4 stages); kGramStagesSmall stages below kGramTwoStageCols columns.
-constexpr int kGramRingBytes = 208896;
+// The Gram's ring: nearly all of the block's shared memory (divisible into 16-byte aligned stages
+// for 2, 3 and 4 stages); kGramStagesSmall stages below kGramTwoStageCols columns.
+constexpr int kGramRingBytes = 227328;
 constexpr int kGramSSmem = kGramRingBytes + 2 * 4 * 8;
+static_assert(kGramRingBytes >= kGramWarps * 2 * (kMaxM + 1) * 8, "the partials fit in the ring");
 constexpr int kGramStagesSmall = 3;
 
 template <int NST>
@@ -1770,7 +1771,8 @@ __device__ __forceinline__ void gram_s_stream(const GramArgs& a, unsigned char* 
 __global__ void __launch_bounds__(kGramTmaThreads, 1) k_gram_s(GramArgs a) {
   pdl_enter();
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ double s_part[kGramWarps][2 * (kMaxM + 1)];
+  // the per-warp partials reuse the ring's stage memory once the stream has drained
+  double (*s_part)[2 * (kMaxM + 1)] = reinterpret_cast<double (*)[2 * (kMaxM + 1)]>(dsm);
   __shared__ unsigned s_max;
   __shared__ volatile int s_abort;
   GState* st = a.st;
