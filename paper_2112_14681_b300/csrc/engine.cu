@@ -570,11 +570,10 @@ struct nsamg_handle {
   // GMRES workspace
   int n = 0, m = 0;
   int64_t ld = 0;
-  double* V = nullptr;  // (m+1) columns (FP64 basis: krylov_fp64 = 1, and batches)
+  double* V = nullptr;  // (m+1) columns (FP64 basis: krylov_fp64 = 1)
   float2* Vs = nullptr; // (m+1) columns of (hi, lo) pairs (split basis: krylov_fp64 = 0)
   double* vin = nullptr;  // split basis: the FP64 residual / next V-cycle input
   bool split = false;     // split basis in use
-  bool no_split = false;  // batches keep the FP64 basis
   double* Z = nullptr;  // m columns (FP64 V-cycle)
   float* Z32 = nullptr; // m columns (FP32 V-cycle)
   double* w = nullptr;
@@ -1282,6 +1281,11 @@ BatchArgs batch_args(nsamg_handle* h, int kind, unsigned long long co, unsigned 
   a.gticket = B->d_gticket + kind;
   a.cond_outer = co;
   a.cond_inner = ci;
+  if (h->split) {
+    a.Vs = h->Vs;
+    a.vin = h->vin;
+    a.v32 = h->fp32 ? h->lv32[0].b : nullptr;
+  }
   return a;
 }
 
@@ -1290,9 +1294,13 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
   const int* sel = &B->d_ctl->gi;
   Ctx c{s, nullptr};
   VRef<const double> b;
-  b.p = h->V;
-  b.sel = sel;
-  b.ld = h->ld;
+  if (h->split) {  // split basis: the V-cycle input vt_i is the FP64 vector vin (FP32: level 0's b)
+    b.p = h->vin;
+  } else {
+    b.p = h->V;
+    b.sel = sel;
+    b.ld = h->ld;
+  }
   if (!h->fp32) {
     VRef<double> z;
     z.p = h->Z;
@@ -1304,8 +1312,10 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     run(op, h->lv[0].A.G, c);
   } else {
     Level<float>& L0 = h->lv32[0];
-    ++g_launches;
-    launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), nullptr);
+    if (!h->split) {  // the split kernels write the FP32 input themselves
+      ++g_launches;
+      launch_k(k_cast<double, float>, 8 * 148, kThreads, s, h->n, b, vref(L0.b), nullptr);
+    }
     VRef<float> z;
     z.p = h->Z32;
     z.sel = sel;
@@ -1319,8 +1329,14 @@ void enqueue_bstep(nsamg_handle* h, cudaStream_t s, unsigned long long cond_inne
     launch_row(op, A.G, s);
   }
   g_launches += 2;
-  launch_k(k_bgram, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
-  launch_k(k_bupdate, B->nblocks[BatchData::kUpdate], kRedThreads, s, batch_args(h, BatchData::kUpdate, 0, cond_inner));
+  if (h->split) {
+    launch_k(k_bgram_s, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
+    launch_k(k_bupdate_s, B->nblocks[BatchData::kUpdate], kRedThreads, s,
+             batch_args(h, BatchData::kUpdate, 0, cond_inner));
+  } else {
+    launch_k(k_bgram, B->nblocks[BatchData::kGram], kGramThreads, s, batch_args(h, BatchData::kGram, 0, 0));
+    launch_k(k_bupdate, B->nblocks[BatchData::kUpdate], kRedThreads, s, batch_args(h, BatchData::kUpdate, 0, cond_inner));
+  }
 }
 
 void enqueue_bxupdate(nsamg_handle* h, cudaStream_t s) {
@@ -1341,8 +1357,13 @@ void enqueue_bresid(nsamg_handle* h, cudaStream_t s, int init, unsigned long lon
   ra.ci = A.ci;
   ra.v = A.v;
   ra.init = init;
+  if (h->split) ra.ba.V = h->vin;  // the residual goes to vin; k_bcol0 scales and splits it
   ++g_launches;
   launch_k(k_bresid, B->nblocks[BatchData::kResid], kRedThreads, s, ra);
+  if (h->split) {
+    ++g_launches;
+    launch_k(k_bcol0, B->nblocks[BatchData::kX], kRedThreads, s, batch_args(h, BatchData::kX, 0, 0));
+  }
 }
 
 int check_params(const nsamg_params& p) {
@@ -1560,7 +1581,7 @@ int alloc_workspace(nsamg_handle* h) {
   h->n = h->lv[0].n;
   h->m = h->p.restart;
   h->ld = ((int64_t)h->n + 63) / 64 * 64;
-  h->split = !h->p.krylov_fp64 && !h->no_split;
+  h->split = !h->p.krylov_fp64;
   if (h->split) {
     if ((rc = alloc_vec(&h->Vs, h->ld * (h->m + 1)))) return rc;
     if ((rc = alloc_vec(&h->vin, h->ld))) return rc;
@@ -1732,7 +1753,6 @@ int setup_impl(const nsamg_hierarchy_desc* H, const nsamg_params* pp, void* stre
   int rc = check_params(p);
   if (rc) return rc;
   h->p = p;
-  h->no_split = bi != nullptr;
   if (!H || H->nlevels < 1 || !H->levels) return fail(NSAMG_ERR_INVALID_ARG, "empty hierarchy");
   CK(cudaGetDevice(&h->device));
   if (stream) {

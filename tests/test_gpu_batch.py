@@ -60,11 +60,15 @@ def test_batch_vcycle_is_per_system_vcycle(fp32, smoother):
 
 @pytest.mark.parametrize("fp32", [0, 1])
 @pytest.mark.parametrize("smoother", [K.POLY_GS, K.HYBRID_ILU0])
-@pytest.mark.parametrize("graph", [1, 0])
-def test_batch_solve_matches_oracle_per_system(fp32, smoother, graph):
+@pytest.mark.parametrize("graph,krylov_fp64", [(1, 0), (0, 0), (1, 1)])
+def test_batch_solve_matches_oracle_per_system(fp32, smoother, graph, krylov_fp64):
+    """Every system against the oracle's one-reduce GMRES with its own V-cycle. The systems' sizes
+    (216, 729, 343, 1728, 512, 1000 rows) put odd first and last rows into the split basis's
+    row pairs (krylov_fp64 = 0); krylov_fp64 = 1 keeps the FP64 basis."""
     S = systems()
     m = 30
-    p = nsamg.default_params(smoother=smoother, vcycle_fp32=fp32, restart=m, use_graph=graph)
+    p = nsamg.default_params(smoother=smoother, vcycle_fp32=fp32, restart=m, use_graph=graph,
+                             krylov_fp64=krylov_fp64)
     with nsamg.batch_setup([H for _, H, _ in S], p) as h:
         off = h.offsets
         b = np.concatenate([bb for _, _, bb in S])
