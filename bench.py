@@ -703,8 +703,9 @@ def run_batched(nsamg, torch, systems):
     out = {"count": len(systems), "n_total": int(sum(A.shape[0] for A, _, _ in systems)),
            "nnz_total": int(sum(A.nnz for A, _, _ in systems))}
     b = torch.from_numpy(np.concatenate([bb for _, _, bb in systems])).cuda()
-    for name, fp32 in (("batched_fp32v", 1), ("batched_fp64", 0)):
-        p = nsamg.default_params(restart=BATCH_RESTART, vcycle_fp32=fp32)
+    # the split basis (default) and, for comparison, the FP64 basis (krylov_fp64 = 1)
+    for name, fp32, kf in (("batched_fp32v", 1, 0), ("batched_fp64", 0, 0), ("batched_fp32v_fp64basis", 1, 1)):
+        p = nsamg.default_params(restart=BATCH_RESTART, vcycle_fp32=fp32, krylov_fp64=kf)
         with nsamg.batch_setup([H for _, H, _ in systems], p) as h:
             x = torch.zeros(h.n, dtype=torch.float64, device="cuda")
             for _ in range(2):

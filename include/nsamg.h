@@ -111,7 +111,9 @@ typedef struct {
                             of its FP32 rate; vectors stay FP64 in memory, the vt . vt and vt . w
                             products and all block/grid sums stay FP64, and blocks whose data
                             leave the [2^-50, 2^60] magnitude window recompute in FP64.
-                            1: every product and sum in FP64.                                     */
+                            Solves and batches keep the basis split (row-pair (hi, lo) columns).
+                            1: every product and sum in FP64 (batches: an FP64 basis, products
+                            in double-FP32 with a split per read).                                */
   int32_t stop_nrbe;     /* 0 (default): stop when ||b - A x|| / ||b|| <= rtol (eq. relres).
                             1: stop when the norm-wise relative backward error
                             beta(x) = ||b - A x|| / (||b|| + ||A||_inf ||x||) <= rtol (Sec. 3). Inside a
